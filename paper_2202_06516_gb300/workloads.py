@@ -1,0 +1,100 @@
+"""Seeded synthetic workloads shared by the oracle tests, the CUDA parity tests and the benchmark.
+
+This module holds parameters and seeded random draws only, none of the method's arithmetic.
+Chemical potentials are given relative to the neutral wall value k^2 * psi'(rho_sat) ("mu_rel");
+each caller resolves them with its own coexistence solver.
+
+Readings (stated with the workloads they affect):
+* Peng-Robinson EOS at Tr = 0.7 (density ratio 145): Tr = 0.6 and 0.65 diverge at tau = 1 with
+  every interface width tried, so the reduced temperature is raised.
+* k^2 = 0.1 and kappa-hat = 0.0126 (Eq. 12 leaves both open); interface 10-90 % width ~4.5 lu.
+* Eq. 16 interface width W = 4 at start (W = 2 diverges within a few hundred steps).
+* The wall surface lies half a link outside the solid disc, at radius R + 1/2; drops start
+  tangent to it.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+# model parameters common to every workload
+MODEL = dict(eos=0, Tr=0.7, k2=0.1, kappa=0.0126, tau=1.0, s_e=1.64, s_eps=1.54, s_q=1.9)
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    circle: tuple | None          # (cx, cy, R) or None for a flat bottom wall
+    drop: tuple                   # (x, y, r, W) of the Eq. 16 initial drop
+    mu_rel_circle: float = 0.0    # wall chemical potential minus the neutral value
+    mu_rel_bottom: float = 0.0
+    mu_rel_top: float = 0.0
+    stripes: tuple | None = None  # (arc length, mu_rel of the odd stripes)
+    g: tuple = (0.0, 0.0)
+    steps: int = 3000
+    measure_every: int = 0
+    model: dict = field(default_factory=lambda: dict(MODEL))
+
+    def as_dict(self):
+        return asdict(self)
+
+
+def tangent_drop(cx, cy, R, r, W=4.0):
+    """Drop of radius r resting on top of the circle (cx, cy, R), tangent to its surface R + 1/2."""
+    return (float(cx), float(cy) + R + 0.5 + r, float(r), float(W))
+
+
+def plain_small() -> Workload:
+    """200 x 120, cylinder R = 40 centred on the bottom boundary, drop r = 25, neutral walls,
+    3000 steps then one measurement."""
+    return Workload("plain-200x120-cyl40-drop25", 200, 120, (100.0, 0.0, 40.0),
+                    tangent_drop(100, 0, 40, 25), steps=3000)
+
+
+def mu_rel_for_angle(theta_deg: float, slope_per_deg: float = 6.0e-4) -> float:
+    """Wall chemical potential offset for a target angle from a linear theta(mu_w) calibration
+    (Sec. 4.1 reports theta linear in mu_w): mu_rel = slope * (theta - 90)."""
+    return slope_per_deg * (theta_deg - 90.0)
+
+
+def plain_large(seed: int = 0, pendent: bool = False) -> Workload:
+    """2048 x 1024, cylinder R = 300 on the bottom boundary, drop r = 150, body force 1e-6 toward
+    the cylinder (sessile) or away from it (pendent), wetting drawn from the seed for a target
+    angle in 40-140 degrees, angle measured every 500 steps."""
+    rng = np.random.default_rng(seed)
+    theta = float(rng.uniform(40.0, 140.0))
+    gy = 1e-6 if pendent else -1e-6
+    return Workload(f"plain-2048x1024-cyl300-drop150-{'pendent' if pendent else 'sessile'}-s{seed}",
+                    2048, 1024, (1024.0, 0.0, 300.0), tangent_drop(1024, 0, 300, 150),
+                    mu_rel_circle=mu_rel_for_angle(theta), g=(0.0, gy), steps=50000,
+                    measure_every=500)
+
+
+def flat_drop(nx=160, ny=80, r=20.0, theta_rel=0.0) -> Workload:
+    """Drop on a flat bottom wall (no cylinder)."""
+    return Workload(f"flat-{nx}x{ny}-drop{r:g}", nx, ny, None, (nx / 2.0, -0.5 + r, r, 4.0),
+                    mu_rel_bottom=theta_rel)
+
+
+def batched(n: int = 256, seed: int = 0) -> list[Workload]:
+    """Independent instances with domain 128..768 x 128..512, cylinder radius 20..200, drop radius
+    15..90 and target angle 30..150 degrees, rejection-resampled until 2 R + 16 <= nx and
+    R + 2 r + 8 <= ny (the drawn ranges otherwise overlap the domain walls)."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng([seed, i])
+        while True:
+            nx = int(rng.integers(128, 769))
+            ny = int(rng.integers(128, 513))
+            R = float(rng.integers(20, 201))
+            r = float(rng.integers(15, 91))
+            if 2 * R + 16 <= nx and R + 2 * r + 8 <= ny:
+                break
+        theta = float(rng.uniform(30.0, 150.0))
+        cx = float(nx // 2)
+        out.append(Workload(f"batch{seed}-{i}", nx, ny, (cx, 0.0, R), tangent_drop(cx, 0, R, r),
+                            mu_rel_circle=mu_rel_for_angle(theta), steps=40000))
+    return out

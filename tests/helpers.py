@@ -1,0 +1,90 @@
+"""Test-side glue: turns a workload description into oracle parameters (and, for the GPU tests,
+into the CUDA library's parameters) with the same resolved numbers on both sides."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def oracle_config(O, w, **over):
+    """oracle.Config for a workload; wall chemical potentials resolved from the oracle's own
+    coexistence value (neutral wall = k^2 psi'(rho_sat))."""
+    m = w.model
+    mx = O.maxwell(m["eos"], m["Tr"])
+    neutral = m["k2"] * mx["mu_sat"]
+    kw = dict(nx=w.nx, ny=w.ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
+              tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"], gx=w.g[0], gy=w.g[1],
+              rho_g=mx["rho_g"], rho_l=mx["rho_l"],
+              mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top,
+              drop_x=w.drop[0], drop_y=w.drop[1], drop_r=w.drop[2], drop_W=w.drop[3])
+    if w.circle is not None:
+        kw.update(has_circle=1, cx=w.circle[0], cy=w.circle[1], R=w.circle[2],
+                  mu_circle=neutral + w.mu_rel_circle)
+    if w.stripes is not None:
+        kw.update(stripes=1, stripe_arc=w.stripes[0], mu_stripe_b=neutral + w.stripes[1])
+    kw.update(over)
+    return O.Config(**kw), mx, neutral
+
+
+def tanh_drop(nx, ny, x0, y0, r, rho_g, rho_l, W):
+    """Density field of a circular drop with a tanh interface (the Eq. 16 profile), built in the
+    test, used as a synthetic input of known geometry."""
+    j, i = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    d = np.sqrt((i - x0) ** 2 + (j - y0) ** 2)
+    return 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * np.tanh(2.0 * (d - r) / W)
+
+
+def cap_angle_on_circle(Rs, r, D):
+    """Contact angle (degrees, through the liquid) of a circular drop of radius r whose centre is
+    at distance D from the centre of a circular substrate of radius Rs: law of cosines in the
+    triangle (substrate centre, drop centre, contact point)."""
+    c = (Rs**2 + r**2 - D**2) / (2.0 * Rs * r)
+    return float(np.degrees(np.arccos(np.clip(c, -1, 1))))
+
+
+def drop_centre_for_angle(Rs, r, theta_deg, cx=0.0, cy=0.0):
+    """Centre of a drop of radius r on top of the circle (cx, cy, Rs) meeting it at theta."""
+    D = np.sqrt(Rs**2 + r**2 - 2.0 * Rs * r * np.cos(np.radians(theta_deg)))
+    return cx, cy + D
+
+
+def exact_secant_angle(substrate, drop_c, r, d1, d2, side):
+    """Closed-form result of the Fig. 1 construction on an exact circular interface: the points
+    of the drop circle (centre drop_c, radius r) at distances d1 and d2 from the substrate, the
+    line through them, its intersection with the substrate and the angle (degrees) between that
+    line and the substrate tangent pointing into the liquid. substrate = ("circle", cx, cy, Rs)
+    or ("flat", y_wall). side 0 = left, 1 = right (as seen from the drop centre)."""
+    qx, qy = drop_c
+
+    def point_at(d):
+        if substrate[0] == "circle":
+            _, cx, cy, Rs = substrate
+            a = Rs + d
+            dx, dy = qx - cx, qy - cy
+            D = np.hypot(dx, dy)
+            l = (a * a - r * r + D * D) / (2 * D)
+            h = np.sqrt(max(a * a - l * l, 0.0))
+            mx, my = cx + l * dx / D, cy + l * dy / D
+            cands = [(mx + h * dy / D, my - h * dx / D), (mx - h * dy / D, my + h * dx / D)]
+            # left = counter-clockwise from the drop-centre direction
+            def cross(p):
+                return dx * (p[1] - cy) - dy * (p[0] - cx)
+            return max(cands, key=cross) if side == 0 else min(cands, key=cross)
+        yw = substrate[1]
+        y = yw + d
+        hx = np.sqrt(max(r * r - (y - qy) ** 2, 0.0))
+        return (qx - hx, y) if side == 0 else (qx + hx, y)
+
+    p1, p2 = np.array(point_at(d1)), np.array(point_at(d2))
+    v = (p2 - p1) / np.linalg.norm(p2 - p1)
+    if substrate[0] == "circle":
+        _, cx, cy, Rs = substrate
+        w = p1 - np.array([cx, cy])
+        wv = w @ v
+        disc = wv * wv - (w @ w - Rs * Rs)
+        s = min([-wv - np.sqrt(disc), -wv + np.sqrt(disc)], key=abs)
+        C = p1 + s * v
+        n = (C - np.array([cx, cy])) / Rs
+        t = np.array([n[1], -n[0]]) if side == 0 else np.array([-n[1], n[0]])
+    else:
+        t = np.array([1.0, 0.0]) if side == 0 else np.array([-1.0, 0.0])
+    return float(np.degrees(np.arccos(np.clip(t @ v, -1, 1))))

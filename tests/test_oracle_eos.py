@@ -1,0 +1,96 @@
+"""Pins for the oracle's equations of state and coexistence (Eq. 8-11, Maxwell construction).
+
+Each check is against something other than the oracle's own formula: thermodynamic identities
+evaluated numerically, the critical point the EOS constants are defined by, and the equal-area
+rule integrated independently with scipy.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("eos,Tr", [(0, 0.6), (0, 0.7), (0, 0.8), (1, 0.7)])
+@pytest.mark.parametrize("rho_frac", [0.01, 0.2, 0.5, 0.8])
+def test_gibbs_duhem(oracle_mod, eos, Tr, rho_frac):
+    """dp0/drho = rho dpsi'/drho (Eq. 8 differentiated): pins psi' (Eq. 11) against p0 (Eq. 10)."""
+    b = oracle_mod.eos_constants(eos, Tr)["b"]
+    rmax = (1.0 if eos == 0 else 4.0) / b
+    rho = rho_frac * rmax
+    h = 1e-5 * rho
+    mu = lambda r: oracle_mod.eos_eval(eos, Tr, r)["mu0"]
+    p = lambda r: oracle_mod.eos_eval(eos, Tr, r)["p0"]
+    dmu = (mu(rho + h) - mu(rho - h)) / (2 * h)
+    dp = (p(rho + h) - p(rho - h)) / (2 * h)
+    assert dp == pytest.approx(rho * dmu, rel=1e-6, abs=1e-12)
+    # the analytic dp0/drho used by the spinodal search
+    assert oracle_mod.eos_eval(eos, Tr, rho)["dp"] == pytest.approx(dp, rel=1e-6, abs=1e-12)
+
+
+@pytest.mark.parametrize("eos", [0, 1])
+def test_free_energy_eq9(oracle_mod, eos):
+    """psi / rho has derivative p0 / rho^2 (Eq. 9)."""
+    Tr = 0.7
+    for rho in [0.05, 0.1, 0.3]:
+        rho = rho * (10.5 if eos == 0 else 1.0)
+        h = 1e-5 * rho
+        g = lambda r: oracle_mod.eos_eval(eos, Tr, r)["psi"] / r
+        d = (g(rho + h) - g(rho - h)) / (2 * h)
+        assert d == pytest.approx(oracle_mod.eos_eval(eos, Tr, rho)["p0"] / rho**2, rel=1e-6)
+
+
+@pytest.mark.parametrize("eos,rho_c_expected", [(0, 0.0778 / (0.3074 * (2.0 / 21.0))), (1, 0.1304)])
+def test_critical_point(oracle_mod, eos, rho_c_expected):
+    """At Tr = 1 the EOS has its critical inflection: min dp0/drho = 0 at rho_c.
+
+    PR: rho_c = p_c / (Z_c R T_c) with b = 0.0778 R T_c / p_c and Z_c = 0.3074 (standard PR
+    critical constants). CS with b = 4: packing fraction 0.1304 at the critical point.
+    """
+    rmax = 10.5 if eos == 0 else 1.0
+    rho = np.linspace(0.02, 0.6, 20001) * rmax
+    dp = np.array([oracle_mod.eos_eval(eos, 1.0, r)["dp"] for r in rho])
+    k = int(np.argmin(dp))
+    scale = oracle_mod.eos_constants(eos, 1.0)["T"]  # R T sets the scale of dp/drho
+    assert abs(dp[k]) < 2e-3 * scale
+    assert rho[k] == pytest.approx(rho_c_expected, rel=0.02)
+    # below Tc the same scan finds a van der Waals loop
+    dp07 = np.array([oracle_mod.eos_eval(eos, 0.7, r)["dp"] for r in rho])
+    assert dp07.min() < 0
+
+
+@pytest.mark.parametrize("eos,Tr", [(0, 0.6), (0, 0.7), (0, 0.8), (1, 0.7)])
+def test_maxwell_equal_area(oracle_mod, eos, Tr):
+    """Coexistence: equal pressure, equal chemical potential, equal areas (scipy quadrature)."""
+    m = oracle_mod.maxwell(eos, Tr)
+    rg, rl, ps = m["rho_g"], m["rho_l"], m["p_sat"]
+    p = lambda r: oracle_mod.eos_eval(eos, Tr, r)["p0"]
+    mu = lambda r: oracle_mod.eos_eval(eos, Tr, r)["mu0"]
+    assert p(rg) == pytest.approx(ps, rel=1e-9)
+    assert p(rl) == pytest.approx(ps, rel=1e-9)
+    assert mu(rg) == pytest.approx(mu(rl), rel=1e-9)
+    # equal areas in the (1/rho, p) plane: int (p0 - p_sat) / rho^2 drho = 0
+    area, _ = quad(lambda r: (p(r) - ps) / r**2, rg, rl, limit=400, epsabs=1e-14)
+    scale, _ = quad(lambda r: abs(p(r) - ps) / r**2, rg, rl, limit=400)
+    assert abs(area) < 1e-7 * scale
+    assert rg < rl
+
+
+def test_maxwell_ordering(oracle_mod):
+    """The coexistence gap closes toward the critical point."""
+    ratios = [oracle_mod.maxwell(0, t)["rho_l"] / oracle_mod.maxwell(0, t)["rho_g"]
+              for t in (0.6, 0.7, 0.8, 0.9)]
+    assert all(a > b for a, b in zip(ratios, ratios[1:]))
+
+
+def test_maxwell_regression(oracle_mod):
+    """Regression pin: values written by tests/golden/make_golden.py from the oracle."""
+    with open(os.path.join(GOLDEN, "maxwell.json")) as f:
+        gold = json.load(f)
+    for row in gold["rows"]:
+        m = oracle_mod.maxwell(row["eos"], row["Tr"])
+        for k in ("rho_g", "rho_l", "p_sat", "mu_sat"):
+            assert m[k] == pytest.approx(row[k], rel=1e-10)
