@@ -1,0 +1,339 @@
+"""Benchmark of the multiphase LBM hot path on GB300.
+
+Workload (N = 1): 2048 x 1024 lattice, cylinder R = 300 centred on the bottom boundary, drop
+r = 150 resting on it, body force 1e-6 toward the cylinder (sessile), wall wetting drawn from
+seed 0, FP32 populations with FP64 reductions; one bench step = one time step (fused step kernel),
+the contact angle measured on the device every 500 steps inside the timed region.
+
+Metric: MLUPS (million lattice-node updates per second, all nx * ny nodes), higher is better.
+The device-timed region uses CUDA events on the library's stream; the working set (2 x 75.5 MB of
+populations + 2 x 8 MB of density + geometry, 170 MB) is larger than the 126 MB L2, so no L2
+flush is inserted between steps. ``e2e`` repeats the run through the C ABI from host buffers:
+geometry and a host initial density in, angles and the final density out.
+
+N > 1 (torchrun): every rank runs an independent instance (seed = rank) with no data-path
+collective; value = all ranks' node updates / the slowest rank's time (weak scaling).
+
+--impl reference: the FP64 CPU oracle on the host cores on the same workload, for a bounded
+number of steps.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURE_EVERY = 500
+STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2202_06516_gb300", "csrc", "lbm_step.cu")
+PROFILE = os.path.join(ROOT, "profiles", "k_step_fp32_2048x1024.md")
+BYTES_PER_FLUID_NODE = 80  # 9 x 4 B populations read + written, 4 B density read + written
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash():
+    with open(STEP_KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken
+    on the current kernel source (None otherwise)."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not b or h.group(1) != _src_hash():
+        return None
+    return float(b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[2 + k]
+                          and "Not" not in r[2 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _resolve(w, lbm_mod):
+    m = w.model
+    co = lbm_mod.lbm_coexistence(m["eos"], m["Tr"])
+    neutral = m["k2"] * co["mu_sat"]
+    return co, neutral
+
+
+def _make_lattice(lbm, w, stream=None):
+    m = w.model
+    co, neutral = _resolve(w, lbm)
+    lat = lbm.Lattice(w.nx, w.ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
+                      tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"], gx=w.g[0],
+                      gy=w.g[1], stream=stream)
+    geo = dict(circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+               mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top, drop=w.drop)
+    return lat, geo
+
+
+def run_cuda(args, rank, world, dist):
+    import torch
+    from paper_2202_06516_gb300 import lbm, workloads as W
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    w = W.plain_large(seed=rank)
+    stream = torch.cuda.Stream(device=dev)
+    lat, geo = _make_lattice(lbm, w, stream=stream)
+    lat.set_geometry(**geo)
+    n_nodes = w.nx * w.ny
+    n_fluid = int(lat.info().n_fluid)
+
+    def run(k):
+        left = k
+        done = 0
+        nmeas = 0
+        while left > 0:
+            chunk = min(left, MEASURE_EVERY - (done % MEASURE_EVERY))
+            lat.step(chunk)
+            done += chunk
+            left -= chunk
+            if done % MEASURE_EVERY == 0:
+                lat.measure()
+                nmeas += 1
+        return nmeas
+
+    run(args.warmup)
+    lat.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        t0.record(stream)
+        nmeas = run(args.steps)
+        t1.record(stream)
+        t1.synchronize()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    # step kernel alone (graph-replayed back-to-back launches) for the roofline
+    k2 = max(256, min(args.steps, 4000))
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    lat.step(k2)
+    k1.record(stream)
+    k1.synchronize()
+    kernel_us = k0.elapsed_time(k1) * 1e3 / k2
+    st, mres = lbm.lbm_mass(lat.ctx, allow_unstable=True)
+    stable = st == lbm.LBM_OK
+    angles = lat.measure()
+    lat.close()
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the C ABI from host buffers (rank-local, not part of the device timing)
+    e2e = None
+    if rank == 0:
+        co, _ = _resolve(w, lbm)
+        j, i = np.mgrid[0:w.ny, 0:w.nx].astype(np.float64)
+        d = np.sqrt((i - w.drop[0]) ** 2 + (j - w.drop[1]) ** 2)
+        rho0 = 0.5 * (co["rho_g"] + co["rho_l"]) + 0.5 * (co["rho_g"] - co["rho_l"]) * \
+            np.tanh(2.0 * (d - w.drop[2]) / w.drop[3])
+        lat2, geo2 = _make_lattice(lbm, w, stream=stream)
+        lat2.set_geometry(**geo2)
+        lat2.step(max(3, args.warmup))
+        lat2.synchronize()
+        ke = args.steps
+        tt = time.perf_counter()
+        lat2.set_geometry(**geo2, rho0=rho0)
+        nm = 0
+        done = 0
+        while done < ke:
+            c = min(ke - done, MEASURE_EVERY - (done % MEASURE_EVERY))
+            lat2.step(c)
+            done += c
+            if done % MEASURE_EVERY == 0:
+                lat2.measure()
+                nm += 1
+        rho_out = lat2.rho()
+        te = time.perf_counter() - tt
+        lat2.close()
+        ang_bytes = 2 * 104
+        e2e = {"value": n_nodes * ke / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": rho0.nbytes / ke,
+               "d2h_bytes_per_step": (rho_out.nbytes + nm * ang_bytes) / ke,
+               "what": "lbm_set_geometry(host rho0) + lbm_step + lbm_measure_contact_angle every "
+                       "500 steps + lbm_read_fields(rho), host wall clock"}
+
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_FLUID_NODE * n_fluid / (kernel_us * 1e-6) / 1e9
+    traffic = _profiled_traffic()
+    line = {
+        "metric": "MLUPS", "value": n_nodes * args.steps * world / (ms * 1e-3) / 1e6,
+        "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name.rsplit("-s", 1)[0], "nx": w.nx, "ny": w.ny,
+                   "fluid_nodes": n_fluid, "measure_every": MEASURE_EVERY,
+                   "precision": "FP32 populations (deviation form), FP64 reductions/angles",
+                   "l2": "working set 170 MB > L2, no flush", "parallelism": f"replicas{world}",
+                   "eos": "Peng-Robinson Tr=0.7", "seed": "rank"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_step<float,32,16>", "kernel_us_per_launch": kernel_us,
+                     "bytes_per_launch": BYTES_PER_FLUID_NODE * n_fluid},
+        "e2e": e2e,
+        "gpu_launches": args.steps + 4 * nmeas,
+        "clocks": clk.summary(),
+        "stable": stable,
+        "angles_deg": [round(angles[0].theta, 3), round(angles[1].theta, 3)],
+    }
+    return line
+
+
+def cpu_baseline(steps: int = 60):
+    """The oracle as it stands on the host cores: the same 2048 x 1024 workload, `steps` time
+    steps (a bounded sample of the 50k-step run)."""
+    import oracle as O
+    from paper_2202_06516_gb300 import workloads as W
+    w = W.plain_large(0)
+    m = w.model
+    mx = O.maxwell(m["eos"], m["Tr"])
+    neutral = m["k2"] * mx["mu_sat"]
+    cfg = O.Config(nx=w.nx, ny=w.ny, **{k: m[k] for k in ("eos", "Tr", "k2", "kappa", "tau", "s_e",
+                                                           "s_eps", "s_q")},
+                   gx=w.g[0], gy=w.g[1], rho_g=mx["rho_g"], rho_l=mx["rho_l"], has_circle=1,
+                   cx=w.circle[0], cy=w.circle[1], R=w.circle[2],
+                   mu_circle=neutral + w.mu_rel_circle, mu_bottom=neutral, mu_top=neutral,
+                   drop_x=w.drop[0], drop_y=w.drop[1], drop_r=w.drop[2], drop_W=w.drop[3])
+    s = O.Sim(cfg)
+    s.step(2)
+    t = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t
+    return {"value": w.nx * w.ny * steps / dt / 1e6, "unit": "MLUPS", "cores": O.threads(),
+            "kind": "oracle", "sample": f"{steps} FP64 oracle steps of the 2048x1024 workload",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, bounded so the run ends in minutes."""
+    from paper_2202_06516_gb300 import workloads as W
+    w = W.plain_large(0)
+    steps = max(1, min(args.steps, 200))
+    warm = max(0, min(args.warmup, 3))
+    cb = cpu_baseline(steps)
+    return {"metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": 0,
+            "steps": steps, "warmup": warm, "ms_per_step": cb["seconds"] * 1e3 / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name.rsplit("-s", 1)[0], "nx": w.nx, "ny": w.ny},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+        dist = td
+    from paper_2202_06516_gb300 import _native
+    if rank == 0:
+        _native.build()
+    if dist:
+        dist.barrier()
+    line = run_cuda(args, rank, world, dist)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

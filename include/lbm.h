@@ -1,0 +1,184 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) multiphase lattice Boltzmann library for contact angles
+ * on curved wetting surfaces (Liu, Yao, Li, Wen, "Contact angle measurement on curved wetting
+ * surface in multiphase lattice Boltzmann method", arXiv:2202.06516).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an lbm_status; nothing aborts, exits or traps. On failure the context
+ *    keeps a message readable with lbm_last_error().
+ *  - Host buffers passed in are borrowed for the duration of the call and never freed. Device
+ *    memory is owned by the context and released by lbm_destroy().
+ *  - Work is issued on the context's stream (lbm_params.stream, or a private non-blocking stream
+ *    when NULL). Calls that return results to the host synchronise that stream.
+ *  - Lattice: fluid-domain nodes (i, j), 0 <= i < nx periodic in x, 0 <= j < ny; rows j = -2, -1
+ *    and j = ny, ny+1 are solid wall rows (the two wetting layers of Sec. 3.1). Node index
+ *    n = j * nx + i. Row-major host arrays of the fluid domain have shape (ny, nx); arrays of the
+ *    extended lattice have shape (ny + 4, nx) with row r holding j = r - 2.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; owns the device state of one lattice */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,        /* invalid argument (message says which) */
+    LBM_ERR_CUDA = 2,       /* a CUDA runtime call failed (message has the CUDA error) */
+    LBM_ERR_STATE = 3,      /* call out of order, e.g. lbm_step before lbm_set_geometry */
+    LBM_ERR_UNSTABLE = 4,   /* non-finite or non-positive density found by a reduction */
+    LBM_ERR_NO_CONTACT = 5, /* a side has no interface points in the band near the substrate */
+    LBM_ERR_TIMEOUT = 6     /* reserved for bounded device-side waits */
+} lbm_status;
+
+enum { LBM_FP32 = 0, LBM_FP64 = 1 };          /* storage and arithmetic type of the step */
+enum { LBM_EOS_PR = 0, LBM_EOS_CS = 1 };      /* Peng-Robinson (Eq. 10) or Carnahan-Starling */
+enum { LBM_MRT = 0, LBM_BGK = 1 };            /* collision of Eq. 1 or Eq. 3 */
+enum { LBM_FLUID = 0, LBM_LAYER1 = 1, LBM_LAYER2 = 2, LBM_SOLID = 3 }; /* node classes */
+
+/* Model parameters (lattice units).
+ *  k2, kappa: k^2 and kappa-hat of the mesh-space chemical potential, Eq. 12.
+ *  tau: s_v = 1/tau (Sec. 2.1) and the BGK relaxation time (Eq. 3).
+ *  s_e, s_eps, s_q: MRT rates of S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_v, s_v) (Sec. 2.1).
+ *  gx, gy: body acceleration; the force rho*g acts on gas and liquid (Sec. 4).
+ *  rho_g, rho_l: coexistence densities; <= 0 selects the library's Maxwell construction.
+ *  tile_x, tile_y: step-kernel tile; 0 selects the default (32 x 16). Supported: 32x8, 32x16,
+ *    64x16, 32x32.
+ *  stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or NULL. */
+typedef struct lbm_params {
+    int32_t nx, ny;
+    int32_t precision; /* LBM_FP32 or LBM_FP64 */
+    int32_t eos;       /* LBM_EOS_PR or LBM_EOS_CS */
+    int32_t collision; /* LBM_MRT or LBM_BGK */
+    int32_t device;    /* CUDA device ordinal */
+    int32_t tile_x, tile_y;
+    double Tr, k2, kappa, tau, s_e, s_eps, s_q;
+    double gx, gy;
+    double rho_g, rho_l;
+    void *stream;
+} lbm_params;
+
+/* Geometry and initial state (Sec. 3.1, Fig. 1, Fig. 9, Eq. 16).
+ *  Circle: solid nodes are those with (i - cx)^2 + (j - cy)^2 <= R^2, evaluated exactly in
+ *    doubled-integer coordinates, so cx, cy, R must be multiples of 1/2. Its wall surface is
+ *    taken at radius R + 1/2 for the measurement.
+ *  Wall chemical potential of a wetting-layer node: mu_circle inside the disc (or, with stripes,
+ *    alternating mu_circle / mu_stripe_b by arc length R*(phi - pi/2) in units of stripe_arc,
+ *    phi = atan2(j - cy, i - cx)); mu_bottom below the domain; mu_top above it.
+ *  Initial density: rho0 (host, (ny, nx), read at fluid nodes) if non-NULL, else the Eq. 16 drop
+ *    (drop_x, drop_y, drop_r, width drop_W); populations start at f = f_eq(rho, 0). */
+typedef struct lbm_geometry {
+    int32_t has_circle;
+    int32_t stripes;
+    double cx, cy, R;
+    double mu_circle, stripe_arc, mu_stripe_b;
+    double mu_bottom, mu_top;
+    double drop_x, drop_y, drop_r, drop_W;
+    const double *rho0;
+} lbm_geometry;
+
+/* One side of the contact-angle measurement (Sec. 3.2, Eq. 15, Fig. 1, Fig. 2). Angles in
+ * degrees. theta is measured through the liquid between the line through p1 and p2 and the
+ * substrate tangent at the contact point; alpha is the tangent's inclination to the horizontal;
+ * beta = theta + alpha on the convex circle (theta on a flat wall). d1, d2: distances of p1, p2
+ * from the substrate. link1, link2: (node index * 4 + slot) of the chosen liquid/gas links, slot
+ * 0..3 = link to (i+1, j), (i, j+1), (i+1, j+1), (i-1, j+1). */
+typedef struct lbm_angle {
+    int32_t status; /* LBM_OK or LBM_ERR_NO_CONTACT */
+    double theta_deg, alpha_deg, beta_deg;
+    double contact_x, contact_y;
+    double p1_x, p1_y, p2_x, p2_y;
+    double d1, d2;
+    int64_t link1, link2;
+} lbm_angle;
+
+typedef struct lbm_info {
+    double rho_g, rho_l, p_sat, mu_sat; /* coexistence in use; mu_sat = psi'(rho_sat), k = 1 */
+    double T;                           /* absolute temperature Tr * Tc */
+    int64_t steps;                      /* time steps taken since lbm_set_geometry */
+    int64_t n_fluid;                    /* fluid nodes */
+    int32_t tile_x, tile_y;
+    int32_t precision;
+} lbm_info;
+
+/* Maxwell equal-area coexistence of an EOS at reduced temperature Tr (Sec. 4, after Eq. 16),
+ * computed on the host in FP64. out[4] = rho_g, rho_l, p_sat, mu_sat (mu at k = 1).
+ * LBM_ERR_ARG above the critical temperature or for an unknown EOS. */
+lbm_status lbm_coexistence(int32_t eos, double Tr, double out[4]);
+
+/* Allocate a lattice on p->device (2 x 9 population planes, 2 density planes, flags, wall
+ * chemical potential, reduction and measurement scratch). *out receives the context; on failure
+ * *out is NULL and nothing is leaked. */
+lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Build the geometry on the device (classification, wetting layers, wall chemical potential,
+ * boundary-link masks) and set the initial state; resets the step counter. Copies g->rho0 from
+ * the host when given. Synchronous. */
+lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g);
+
+/* Advance nsteps time steps (Eq. 1-4 with Eq. 7, 12-14): one fused kernel per step, replayed
+ * from a CUDA graph in chunks when the stream allows capture. Asynchronous; returns LBM_OK once
+ * the work is queued (LBM_ERR_STATE before lbm_set_geometry, LBM_ERR_ARG for nsteps < 0). */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Measure the left (out[0]) and right (out[1]) contact angles on the current density field with
+ * the on-device scheme of Sec. 3.2: liquid/gas links (a node is liquid when rho > rho_m, the
+ * mean of rho_g and rho_l), Eq. 15 points, per side the points nearest to 1 and 2 lattice units
+ * from the substrate within 0.5..2.5 (ties: smaller |d - target|, then smaller link id), the line
+ * through them cut with the substrate (the circle at R + 1/2 if present, else the bottom wall
+ * y = -1/2). Sides split by the liquid centroid. Synchronous. Returns LBM_ERR_NO_CONTACT if
+ * either side failed (its status says so; the other side is still filled). */
+lbm_status lbm_measure_contact_angle(lbm_ctx *ctx, lbm_angle out[2]);
+
+/* Copy fields of the current state to caller buffers of n = nx * ny doubles each ((ny, nx),
+ * zero at solid nodes). which: bit 0 density, bit 1 velocity v = u + F/(2 rho) (Sec. 2.2, below
+ * Eq. 13; computes the force of the current state), bit 2 destinations are device pointers.
+ * Any of rho, ux, uy may be NULL when its bit is clear. Synchronous. */
+#define LBM_FIELD_RHO 1u
+#define LBM_FIELD_VEL 2u
+#define LBM_FIELD_DEVICE_DST 4u
+lbm_status lbm_read_fields(lbm_ctx *ctx, uint32_t which, double *rho, double *ux, double *uy,
+                           size_t n);
+
+/* FP64 sums over fluid nodes (deterministic two-pass reduction): out[0] total mass, out[1]
+ * number of liquid nodes (rho > rho_m), out[2], out[3] their centroid x, y. Returns
+ * LBM_ERR_UNSTABLE if a density is non-finite or non-positive. Synchronous. */
+lbm_status lbm_mass(lbm_ctx *ctx, double out[4]);
+
+/* Geometry as built on the device: flags ((ny+4) x nx node classes), mu_w ((ny+4) x nx wall
+ * chemical potential, 0 off the wetting layers) and the boundary links (fluid node n, direction
+ * q with x + e_q solid) as codes n * 9 + q in ascending order. Any output may be NULL; links
+ * holds at most cap codes, *n_links receives the total. D2Q9 directions q = 0..8: rest, (1,0),
+ * (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1). Synchronous. */
+lbm_status lbm_read_geometry(lbm_ctx *ctx, uint8_t *flags, double *mu_w, int64_t *links,
+                             int64_t cap, int64_t *n_links);
+
+/* Liquid/gas links of the current density field with their Eq. 15 points and substrate
+ * distances, in ascending link id (node * 4 + slot): ids[k], pxyd[3k..3k+2] = px, py, d. Writes
+ * at most cap entries; *n receives the total. Synchronous. */
+lbm_status lbm_read_candidates(lbm_ctx *ctx, int64_t *ids, double *pxyd, int64_t cap,
+                               int64_t *n);
+
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
+
+/* Wait for the context's stream. */
+lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+/* Release all device memory, graphs and the private stream. NULL is ignored. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none); for ctx == NULL, of the last failed
+ * lbm_create or lbm_coexistence in this process. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

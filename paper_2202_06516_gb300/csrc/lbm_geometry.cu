@@ -1,0 +1,214 @@
+// Geometry and initial-state kernels (Sec. 3.1, Fig. 1, Fig. 9, Eq. 16).
+//
+// Classification is integer-exact: a node is solid when it lies in a wall row or inside the
+// closed disc, tested in doubled-integer coordinates. Wetting layers follow Sec. 3.1: layer 1 is
+// a solid node with a fluid node among its 8 neighbours, layer 2 a remaining solid node with a
+// layer-1 node among its 8 neighbours. Both passes update flags in place: layer 1 only reads the
+// fluid/solid distinction, which it never changes, and layer 2 only reads "is layer 1", which it
+// never changes.
+#include <math.h>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int wrap(int i, int nx) {
+    i %= nx;
+    return i < 0 ? i + nx : i;
+}
+
+__global__ void k_classify(uint8_t* flags, GeomArgs g) {
+    const int rows = g.ny + 4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * g.nx;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / g.nx), i = (int)(e % g.nx);
+        const int j = r - 2;
+        bool solid = j < 0 || j >= g.ny;
+        if (!solid && g.has_circle) {
+            const long long dx = 2LL * i - g.cx2, dy = 2LL * j - g.cy2;
+            solid = dx * dx + dy * dy <= g.r2 * g.r2;
+        }
+        flags[(size_t)r * g.P + i] = solid ? kSolid : kFluid;
+    }
+}
+
+// match: class of neighbour that promotes (fluid for layer 1, layer 1 for layer 2)
+__global__ void k_layer(uint8_t* flags, GeomArgs g, uint8_t match, uint8_t promote) {
+    const int rows = g.ny + 4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * g.nx;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / g.nx), i = (int)(e % g.nx);
+        if (flags[(size_t)r * g.P + i] != kSolid) continue;
+        bool hit = false;
+#pragma unroll
+        for (int q = 1; q < 9; ++q) {
+            const int rr = r + qy(q);
+            if (rr < 0 || rr >= rows) continue;
+            hit |= flags[(size_t)rr * g.P + wrap(i + qx(q), g.nx)] == match;
+        }
+        if (hit) flags[(size_t)r * g.P + i] = promote;
+    }
+}
+
+template <typename T>
+__global__ void k_muw(const uint8_t* flags, T* muw, GeomArgs g) {
+    const int rows = g.ny + 4;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * g.nx;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / g.nx), i = (int)(e % g.nx);
+        const int j = r - 2;
+        const uint8_t f = flags[(size_t)r * g.P + i];
+        double mu = 0.0;
+        if (f == kLayer1 || f == kLayer2) {
+            bool in_disc = false;
+            if (g.has_circle) {
+                const long long dx = 2LL * i - g.cx2, dy = 2LL * j - g.cy2;
+                in_disc = dx * dx + dy * dy <= g.r2 * g.r2;
+            }
+            if (in_disc) {
+                mu = g.mu_circle;
+                if (g.stripes) {
+                    const double phi = atan2((double)j - g.cy, (double)i - g.cx);
+                    const double s = g.R * (phi - 0.5 * M_PI);
+                    const long long k = (long long)floor(s / g.stripe_arc);
+                    mu = (k % 2 == 0) ? g.mu_circle : g.mu_stripe_b;
+                }
+            } else {
+                mu = j < 0 ? g.mu_bottom : g.mu_top;
+            }
+        }
+        muw[(size_t)r * g.P + i] = (T)mu;
+    }
+}
+
+// bit (q-1) set when fluid node x has a solid node at x + e_q; counts fluid nodes
+__global__ void k_linkmask(const uint8_t* flags, uint8_t* mask, unsigned long long* n_fluid,
+                           GeomArgs g) {
+    unsigned long long local = 0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)g.ny * g.nx;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(n / g.nx), i = (int)(n % g.nx);
+        uint8_t m = 0;
+        if (flags[(size_t)(j + 2) * g.P + i] == kFluid) {
+            ++local;
+#pragma unroll
+            for (int q = 1; q < 9; ++q)
+                if (flags[(size_t)(j + 2 + qy(q)) * g.P + wrap(i + qx(q), g.nx)] != kFluid)
+                    m |= (uint8_t)(1u << (q - 1));
+        }
+        mask[(size_t)j * g.P + i] = m;
+    }
+    // integer atomics: exact and order-independent
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(n_fluid, local);
+}
+
+// Eq. 16 drop (or a given density) at fluid nodes; zero elsewhere
+template <typename T>
+__global__ void k_init_rho(const uint8_t* flags, T* rho, T* rho_other, const double* rho0,
+                           GeomArgs g, double rg, double rl, double x0, double y0, double r0,
+                           double W) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)g.ny * g.nx;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(n / g.nx), i = (int)(n % g.nx);
+        const size_t o = (size_t)j * g.P + i;
+        double v = 0.0;
+        if (flags[(size_t)(j + 2) * g.P + i] == kFluid) {
+            if (rho0) {
+                v = rho0[n];
+            } else {
+                const double dx = i - x0, dy = j - y0;
+                const double r = sqrt(dx * dx + dy * dy);
+                v = 0.5 * (rg + rl) + 0.5 * (rg - rl) * tanh(2.0 * (r - r0) / W);
+            }
+        }
+        rho[o] = (T)v;
+        rho_other[o] = (T)0;
+    }
+}
+
+// Stored populations are post-collision deviations h_q(z) = f*_q(z) - w_q rho(z). Starting from
+// f(x, 0) = w_q rho0(x) means f*_q(z, -1) = w_q rho0(z + e_q) when z + e_q is fluid (it streams
+// there) and w_q rho0(z) when it is solid (it bounces back to z).
+template <typename T>
+__global__ void k_init_h(const uint8_t* flags, const T* rho, T* h, T* h_other, GeomArgs g,
+                         long long plane) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)g.ny * g.nx;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(n / g.nx), i = (int)(n % g.nx);
+        const size_t o = (size_t)j * g.P + i;
+        const bool fluid = flags[(size_t)(j + 2) * g.P + i] == kFluid;
+        const T r0 = rho[o];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            T v = (T)0;
+            if (fluid && q > 0) {
+                const int ti = wrap(i + qx(q), g.nx), tj = j + qy(q);
+                if (flags[(size_t)(tj + 2) * g.P + ti] == kFluid)
+                    v = qw<T>(q) * (rho[(size_t)tj * g.P + ti] - r0);
+            }
+            h[(size_t)q * plane + o] = v;
+            h_other[(size_t)q * plane + o] = (T)0;
+        }
+    }
+}
+
+int grid_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g) {
+    const long long next = (long long)(c->ny + 4) * c->nx;
+    const long long nf = (long long)c->ny * c->nx;
+    k_classify<<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, g);
+    k_layer<<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, g, kFluid, kLayer1);
+    k_layer<<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, g, kLayer1, kLayer2);
+    if (c->esz == 4)
+        k_muw<float><<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, (float*)c->muw, g);
+    else
+        k_muw<double><<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, (double*)c->muw, g);
+    unsigned long long* d_nf = (unsigned long long*)c->red_out;  // scratch, overwritten later
+    cudaError_t e = cudaMemsetAsync(d_nf, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    k_linkmask<<<grid_for(nf), kThreads, 0, c->stream>>>(c->flags, c->linkmask, d_nf, g);
+    unsigned long long nfl = 0;
+    e = cudaMemcpyAsync(&nfl, d_nf, sizeof nfl, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(c->stream);
+    c->n_fluid = (int64_t)nfl;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& geo, const double* d_rho0) {
+    GeomArgs g{};
+    g.nx = c->nx;
+    g.ny = c->ny;
+    g.P = c->P;
+    const long long nf = (long long)c->ny * c->nx;
+    if (c->esz == 4) {
+        k_init_rho<float><<<grid_for(nf), kThreads, 0, c->stream>>>(
+            c->flags, (float*)c->rho[0], (float*)c->rho[1], d_rho0, g, c->rho_g, c->rho_l,
+            geo.drop_x, geo.drop_y, geo.drop_r, geo.drop_W);
+        k_init_h<float><<<grid_for(nf), kThreads, 0, c->stream>>>(
+            c->flags, (const float*)c->rho[0], (float*)c->h[0], (float*)c->h[1], g,
+            (long long)c->plane);
+    } else {
+        k_init_rho<double><<<grid_for(nf), kThreads, 0, c->stream>>>(
+            c->flags, (double*)c->rho[0], (double*)c->rho[1], d_rho0, g, c->rho_g, c->rho_l,
+            geo.drop_x, geo.drop_y, geo.drop_r, geo.drop_W);
+        k_init_h<double><<<grid_for(nf), kThreads, 0, c->stream>>>(
+            c->flags, (const double*)c->rho[0], (double*)c->h[0], (double*)c->h[1], g,
+            (long long)c->plane);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,131 @@
+// Internal declarations of the GB300 multiphase LBM library: context layout, kernel argument
+// blocks and launcher entry points shared by the translation units of liblbm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// D2Q9 direction order: rest, E, N, W, S, NE, NW, SW, SE (e_q and weights w_q of Eq. 1-2).
+__host__ __device__ constexpr int qx(int q) {
+    return q == 1 || q == 5 || q == 8 ? 1 : (q == 3 || q == 6 || q == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int qy(int q) {
+    return q == 2 || q == 5 || q == 6 ? 1 : (q == 4 || q == 7 || q == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int qopp(int q) {
+    return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 3) % 4) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T qw(int q) {
+    return q == 0 ? T(4) / T(9) : (q <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+
+constexpr uint8_t kFluid = 0, kLayer1 = 1, kLayer2 = 2, kSolid = 3;
+
+// Equation-of-state constants in the form the kernels evaluate psi'(rho) in.
+struct EosConst {
+    int eos;      // LBM_EOS_PR / LBM_EOS_CS
+    double RT;    // R * T
+    double aal;   // a * alpha(T) (PR) or a (CS)
+    double b;
+};
+
+// Arguments of the fused step kernel (one time step, Eq. 1-4, 7, 12-14).
+template <typename T>
+struct StepArgs {
+    const T* h_in;     // 9 planes, post-collision deviations f*_q - w_q rho(t) (see step .cu)
+    T* h_out;
+    const T* rho_in;   // rho(t), fluid domain, pitch P
+    T* rho_out;        // rho(t+1)
+    const uint8_t* flags;  // extended rows -2..ny+1
+    const T* muw;          // extended rows, wall chemical potential
+    T* vx;             // optional velocity output (macroscopic mode), fluid domain
+    T* vy;
+    int nx, ny, P;
+    long long plane;   // ny * P
+    T k2, kappa, gx, gy;
+    T s_e, s_eps, s_q, s_v, inv_tau;
+    int bgk;
+    int eos;
+    T RT, aal, b;
+};
+
+struct GeomArgs {
+    int nx, ny, P;
+    int has_circle, stripes;
+    long long cx2, cy2, r2;  // doubled-integer circle
+    double cx, cy, R, stripe_arc;
+    double mu_circle, mu_stripe_b, mu_bottom, mu_top;
+};
+
+// Device result block of the reductions: sums over fluid nodes.
+struct ReduceOut {
+    double mass, n_liquid, sx, sy, bad, pad0, pad1, pad2;
+};
+
+struct Substrate {
+    int circle;       // 1: circle (cx, cy, Rs), 0: flat bottom wall at y = -1/2
+    double cx, cy, Rs;
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+    lbm_params p;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nx = 0, ny = 0, P = 0;
+    size_t plane = 0, plane_ext = 0;
+    size_t esz = 4;
+    void* h[2] = {nullptr, nullptr};
+    void* rho[2] = {nullptr, nullptr};
+    void* muw = nullptr;
+    uint8_t* flags = nullptr;
+    uint8_t* linkmask = nullptr;   // per fluid-domain node, bit q-1 set when x + e_q is solid
+    int cur = 0;
+    bool has_geometry = false;
+    int64_t steps = 0;
+    int64_t n_fluid = 0;
+    lbm::EosConst eosc{};
+    double rho_g = 0, rho_l = 0, p_sat = 0, mu_sat = 0, T = 0;
+    lbm_geometry geom{};
+    lbm::Substrate sub{};
+    // reduction / measurement scratch
+    double* red_partials = nullptr;
+    lbm::ReduceOut* red_out = nullptr;
+    void* meas_partials = nullptr;
+    lbm_angle* meas_out = nullptr;
+    int red_blocks = 0;
+    // velocity scratch for lbm_read_fields
+    void* vel = nullptr;
+    // graphs of GRAPH_CHUNK steps starting from buffer 0 / buffer 1
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    int tile_x = 32, tile_y = 16;
+    std::string err;
+};
+
+namespace lbm {
+
+constexpr int kGraphChunk = 64;   // steps per captured graph (even: ping-pong parity preserved)
+constexpr int kRedThreads = 256;
+
+// launchers (return the CUDA error of the launch)
+cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g);
+cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& g, const double* d_rho0);
+cudaError_t launch_step(lbm_ctx* c, int src, bool macro);
+size_t step_smem_bytes(int tile_x, int tile_y, size_t esz);
+cudaError_t step_configure(lbm_ctx* c);
+cudaError_t launch_reduce(lbm_ctx* c);
+cudaError_t launch_measure(lbm_ctx* c);
+cudaError_t launch_candidates(lbm_ctx* c, uint8_t* d_mark, double* d_pxyd);
+cudaError_t launch_to_double(lbm_ctx* c, const void* src, double* dst, int src_is_rho_plane);
+
+}  // namespace lbm

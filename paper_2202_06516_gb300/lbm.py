@@ -1,0 +1,291 @@
+"""Python binding of liblbm.so: the C ABI of include/lbm.h with the same names.
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels. The
+library is loaded from the package's ``_build`` folder (built by ``_native.build``); if it is
+missing or cannot be loaded, importing the functions raises — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_STATE = 0, 1, 2, 3
+LBM_ERR_UNSTABLE, LBM_ERR_NO_CONTACT, LBM_ERR_TIMEOUT = 4, 5, 6
+LBM_FP32, LBM_FP64 = 0, 1
+LBM_EOS_PR, LBM_EOS_CS = 0, 1
+LBM_MRT, LBM_BGK = 0, 1
+LBM_FIELD_RHO, LBM_FIELD_VEL, LBM_FIELD_DEVICE_DST = 1, 2, 4
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbm status {status}: {msg}")
+        self.status = status
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32),
+                ("eos", C.c_int32), ("collision", C.c_int32), ("device", C.c_int32),
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32),
+                ("Tr", C.c_double), ("k2", C.c_double), ("kappa", C.c_double),
+                ("tau", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double),
+                ("s_q", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
+                ("rho_g", C.c_double), ("rho_l", C.c_double), ("stream", C.c_void_p)]
+
+
+class lbm_geometry(C.Structure):
+    _fields_ = [("has_circle", C.c_int32), ("stripes", C.c_int32),
+                ("cx", C.c_double), ("cy", C.c_double), ("R", C.c_double),
+                ("mu_circle", C.c_double), ("stripe_arc", C.c_double),
+                ("mu_stripe_b", C.c_double), ("mu_bottom", C.c_double), ("mu_top", C.c_double),
+                ("drop_x", C.c_double), ("drop_y", C.c_double), ("drop_r", C.c_double),
+                ("drop_W", C.c_double), ("rho0", C.POINTER(C.c_double))]
+
+
+class lbm_angle(C.Structure):
+    _fields_ = [("status", C.c_int32), ("theta_deg", C.c_double), ("alpha_deg", C.c_double),
+                ("beta_deg", C.c_double), ("contact_x", C.c_double), ("contact_y", C.c_double),
+                ("p1_x", C.c_double), ("p1_y", C.c_double), ("p2_x", C.c_double),
+                ("p2_y", C.c_double), ("d1", C.c_double), ("d2", C.c_double),
+                ("link1", C.c_int64), ("link2", C.c_int64)]
+
+
+class lbm_info(C.Structure):
+    _fields_ = [("rho_g", C.c_double), ("rho_l", C.c_double), ("p_sat", C.c_double),
+                ("mu_sat", C.c_double), ("T", C.c_double), ("steps", C.c_int64),
+                ("n_fluid", C.c_int64), ("tile_x", C.c_int32), ("tile_y", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+_sig = None
+
+
+def lib() -> C.CDLL:
+    """The loaded library with argument types declared (raises if it cannot be loaded)."""
+    global _sig
+    L = _native.load()
+    if _sig is None:
+        vp, dp, i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)
+        L.lbm_coexistence.argtypes = [C.c_int32, C.c_double, dp]
+        L.lbm_create.argtypes = [C.POINTER(lbm_params), C.POINTER(vp)]
+        L.lbm_set_geometry.argtypes = [vp, C.POINTER(lbm_geometry)]
+        L.lbm_step.argtypes = [vp, C.c_int64]
+        L.lbm_measure_contact_angle.argtypes = [vp, C.POINTER(lbm_angle)]
+        L.lbm_read_fields.argtypes = [vp, C.c_uint32, vp, vp, vp, C.c_size_t]
+        L.lbm_mass.argtypes = [vp, dp]
+        L.lbm_read_geometry.argtypes = [vp, C.POINTER(C.c_uint8), dp, i64p, C.c_int64, i64p]
+        L.lbm_read_candidates.argtypes = [vp, i64p, dp, C.c_int64, i64p]
+        L.lbm_get_info.argtypes = [vp, C.POINTER(lbm_info)]
+        L.lbm_synchronize.argtypes = [vp]
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = C.c_char_p
+        for n in ("lbm_coexistence", "lbm_create", "lbm_set_geometry", "lbm_step",
+                  "lbm_measure_contact_angle", "lbm_read_fields", "lbm_mass", "lbm_read_geometry",
+                  "lbm_read_candidates", "lbm_get_info", "lbm_synchronize"):
+            getattr(L, n).restype = C.c_int
+        _sig = True
+    return L
+
+
+def _check(status: int, ctx=None, allow=()):
+    if status != LBM_OK and status not in allow:
+        msg = lib().lbm_last_error(ctx).decode()
+        raise LbmError(status, msg)
+    return status
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ------------------------------------------------------------------------------ C ABI names
+def lbm_coexistence(eos: int, Tr: float) -> dict:
+    out = np.zeros(4)
+    _check(lib().lbm_coexistence(eos, Tr, _dp(out)))
+    return {"rho_g": out[0], "rho_l": out[1], "p_sat": out[2], "mu_sat": out[3]}
+
+
+def lbm_create(params: lbm_params) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(lib().lbm_create(C.byref(params), C.byref(ctx)))
+    return ctx
+
+
+def lbm_set_geometry(ctx, geom: lbm_geometry, rho0: np.ndarray | None = None):
+    keep = None
+    if rho0 is not None:
+        keep = np.ascontiguousarray(rho0, dtype=np.float64)
+        geom.rho0 = _dp(keep)
+    else:
+        geom.rho0 = None
+    _check(lib().lbm_set_geometry(ctx, C.byref(geom)), ctx)
+
+
+def lbm_step(ctx, nsteps: int):
+    _check(lib().lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_measure_contact_angle(ctx):
+    """(status, [left, right]) with lbm_angle structs; NO_CONTACT is returned, not raised."""
+    out = (lbm_angle * 2)()
+    st = _check(lib().lbm_measure_contact_angle(ctx, out), ctx, allow=(LBM_ERR_NO_CONTACT,))
+    return st, [out[0], out[1]]
+
+
+def lbm_read_fields(ctx, which: int, nx: int, ny: int, device_out=None):
+    """Host arrays (ny, nx) of density / velocity; device_out = (rho, ux, uy) device pointers
+    (e.g. torch tensors' data_ptr()) writes on the device instead and returns None."""
+    n = nx * ny
+    if device_out is not None:
+        r, u, v = device_out
+        _check(lib().lbm_read_fields(ctx, which | LBM_FIELD_DEVICE_DST, r, u, v, n), ctx)
+        return None
+    rho = np.zeros((ny, nx)) if which & LBM_FIELD_RHO else None
+    ux = np.zeros((ny, nx)) if which & LBM_FIELD_VEL else None
+    uy = np.zeros((ny, nx)) if which & LBM_FIELD_VEL else None
+    ptr = lambda a: a.ctypes.data if a is not None else None
+    _check(lib().lbm_read_fields(ctx, which, ptr(rho), ptr(ux), ptr(uy), n), ctx)
+    return rho, ux, uy
+
+
+def lbm_mass(ctx, allow_unstable: bool = False):
+    out = np.zeros(4)
+    st = _check(lib().lbm_mass(ctx, _dp(out)), ctx,
+                allow=(LBM_ERR_UNSTABLE,) if allow_unstable else ())
+    return st, {"mass": out[0], "n_liquid": out[1], "cx": out[2], "cy": out[3]}
+
+
+def lbm_read_geometry(ctx, nx: int, ny: int):
+    flags = np.zeros((ny + 4, nx), dtype=np.uint8)
+    muw = np.zeros((ny + 4, nx))
+    nl = C.c_int64()
+    _check(lib().lbm_read_geometry(ctx, flags.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(muw),
+                                   None, 0, C.byref(nl)), ctx)
+    links = np.zeros(max(nl.value, 1), dtype=np.int64)
+    _check(lib().lbm_read_geometry(ctx, None, None, links.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   nl.value, C.byref(nl)), ctx)
+    return flags, muw, links[:nl.value]
+
+
+def lbm_read_candidates(ctx, nx: int, ny: int):
+    cap = 4 * nx * ny
+    ids = np.zeros(cap, dtype=np.int64)
+    pd = np.zeros((cap, 3))
+    n = C.c_int64()
+    _check(lib().lbm_read_candidates(ctx, ids.ctypes.data_as(C.POINTER(C.c_int64)), _dp(pd),
+                                     cap, C.byref(n)), ctx)
+    return ids[:n.value].copy(), pd[:n.value].copy()
+
+
+def lbm_get_info(ctx) -> lbm_info:
+    out = lbm_info()
+    _check(lib().lbm_get_info(ctx, C.byref(out)), ctx)
+    return out
+
+
+def lbm_synchronize(ctx):
+    _check(lib().lbm_synchronize(ctx), ctx)
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        lib().lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx=None) -> str:
+    return lib().lbm_last_error(ctx).decode()
+
+
+# -------------------------------------------------------------------------- convenience layer
+@dataclass
+class Angle:
+    status: int
+    theta: float
+    alpha: float
+    beta: float
+    contact: tuple
+    p1: tuple
+    p2: tuple
+    d1: float
+    d2: float
+    link1: int
+    link2: int
+
+
+def _angle(a: lbm_angle) -> Angle:
+    return Angle(a.status, a.theta_deg, a.alpha_deg, a.beta_deg, (a.contact_x, a.contact_y),
+                 (a.p1_x, a.p1_y), (a.p2_x, a.p2_y), a.d1, a.d2, a.link1, a.link2)
+
+
+class Lattice:
+    """Owns one lbm_ctx. ``stream`` may be a torch.cuda.Stream (its handle is passed through)."""
+
+    def __init__(self, nx, ny, *, eos=LBM_EOS_PR, Tr=0.7, k2=0.1, kappa=0.0126, tau=1.0,
+                 s_e=1.64, s_eps=1.54, s_q=1.9, gx=0.0, gy=0.0, rho_g=0.0, rho_l=0.0,
+                 precision=LBM_FP32, collision=LBM_MRT, device=0, tile=(0, 0), stream=None):
+        handle = getattr(stream, "cuda_stream", stream)
+        self.params = lbm_params(nx, ny, precision, eos, collision, device, tile[0], tile[1], Tr,
+                                 k2, kappa, tau, s_e, s_eps, s_q, gx, gy, rho_g, rho_l,
+                                 C.c_void_p(handle) if handle else None)
+        self.nx, self.ny = nx, ny
+        self.ctx = lbm_create(self.params)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
+                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None):
+        g = lbm_geometry()
+        if circle is not None:
+            g.has_circle = 1
+            g.cx, g.cy, g.R = circle
+        g.mu_circle = mu_circle
+        if stripes is not None:
+            g.stripes = 1
+            g.stripe_arc, g.mu_stripe_b = stripes
+        g.mu_bottom, g.mu_top = mu_bottom, mu_top
+        g.drop_x, g.drop_y, g.drop_r, g.drop_W = drop
+        lbm_set_geometry(self.ctx, g, rho0)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def synchronize(self):
+        lbm_synchronize(self.ctx)
+
+    def measure(self):
+        st, (l, r) = lbm_measure_contact_angle(self.ctx)
+        return _angle(l), _angle(r)
+
+    def rho(self):
+        return lbm_read_fields(self.ctx, LBM_FIELD_RHO, self.nx, self.ny)[0]
+
+    def velocity(self):
+        _, ux, uy = lbm_read_fields(self.ctx, LBM_FIELD_VEL, self.nx, self.ny)
+        return ux, uy
+
+    def mass(self):
+        return lbm_mass(self.ctx)[1]
+
+    def geometry(self):
+        return lbm_read_geometry(self.ctx, self.nx, self.ny)
+
+    def candidates(self):
+        return lbm_read_candidates(self.ctx, self.nx, self.ny)
+
+    def info(self):
+        return lbm_get_info(self.ctx)

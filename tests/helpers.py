@@ -88,3 +88,21 @@ def exact_secant_angle(substrate, drop_c, r, d1, d2, side):
     else:
         t = np.array([1.0, 0.0]) if side == 0 else np.array([-1.0, 0.0])
     return float(np.degrees(np.arccos(np.clip(t @ v, -1, 1))))
+
+
+MODEL_KEYS = ("eos", "Tr", "k2", "kappa", "tau", "s_e", "s_eps", "s_q")
+
+
+def gpu_lattice(lbm, cfg, precision=0, tile=(0, 0), rho0=None, stream=None):
+    """CUDA-library lattice with exactly the numbers of an oracle Config (same coexistence
+    densities, wall chemical potentials and initial drop)."""
+    lat = lbm.Lattice(cfg.nx, cfg.ny, eos=cfg.eos, Tr=cfg.Tr, k2=cfg.k2, kappa=cfg.kappa,
+                      tau=cfg.tau, s_e=cfg.s_e, s_eps=cfg.s_eps, s_q=cfg.s_q, gx=cfg.gx,
+                      gy=cfg.gy, rho_g=cfg.rho_g, rho_l=cfg.rho_l, precision=precision,
+                      collision=cfg.collision, tile=tile, stream=stream)
+    lat.set_geometry(circle=(cfg.cx, cfg.cy, cfg.R) if cfg.has_circle else None,
+                     mu_circle=cfg.mu_circle,
+                     stripes=(cfg.stripe_arc, cfg.mu_stripe_b) if cfg.stripes else None,
+                     mu_bottom=cfg.mu_bottom, mu_top=cfg.mu_top,
+                     drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W), rho0=rho0)
+    return lat

@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports every entry point that
+include/lbm.h declares, and its host-only parts behave (no kernel is launched here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_measure_contact_angle",
+              "lbm_read_fields", "lbm_destroy", "lbm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2202_06516_gb300 import _native
+    lib = _native.load()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_coexistence_agrees_with_oracle(oracle_mod):
+    """The library's host Maxwell solver (parametrised by mu) and the oracle's (bisection on p)
+    are independent; they must agree to near round-off."""
+    from paper_2202_06516_gb300 import lbm
+    for eos, Tr in [(0, 0.6), (0, 0.7), (0, 0.8), (1, 0.7)]:
+        a = lbm.lbm_coexistence(eos, Tr)
+        b = oracle_mod.maxwell(eos, Tr)
+        for k in ("rho_g", "rho_l", "p_sat", "mu_sat"):
+            assert a[k] == pytest.approx(b[k], rel=1e-9), (eos, Tr, k)
+
+
+def test_coexistence_rejects_supercritical():
+    from paper_2202_06516_gb300 import lbm
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_coexistence(0, 1.2)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_coexistence(7, 0.7)
+
+
+def test_create_validates_arguments():
+    """Argument errors are reported before any device work, with a message."""
+    from paper_2202_06516_gb300 import lbm
+    p = lbm.lbm_params(4, 64, 0, 0, 0, 0, 0, 0, 0.7, 0.1, 0.0126, 1.0, 1.64, 1.54, 1.9, 0, 0, 0,
+                       0, None)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(p)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    assert "nx" in lbm.lbm_last_error(None)
+    p.nx, p.tile_x, p.tile_y = 64, 48, 48
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(p)
+    assert e.value.status == lbm.LBM_ERR_ARG
+
+
+def test_null_context_is_an_error_not_a_crash():
+    from paper_2202_06516_gb300 import lbm
+    L = lbm.lib()
+    assert L.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert L.lbm_measure_contact_angle(None, None) == lbm.LBM_ERR_ARG
+    L.lbm_destroy(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The CUDA path's package never reaches the oracle."""
+    pkg = os.path.join(ROOT, "paper_2202_06516_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "lbm_oracle" not in txt, f

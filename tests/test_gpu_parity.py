@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA library against the FP64 oracle, through the C ABI.
+
+Tolerances: geometry, boundary links, candidate links and chosen contact-line links bit-exact;
+FP64 fields to 1e-9 of rho_l after hundreds of steps; FP32 fields max|drho| <= 1e-4 rho_l after
+the 200 x 120 workload's 3000 steps; contact angles within 0.5 degrees on independently evolved
+fields and within 1e-6 degrees on identical fields.
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_lattice, oracle_config, tanh_drop
+from paper_2202_06516_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2202_06516_gb300 import lbm as L
+    L.lib()
+    return L
+
+
+def _cfg(O, w=None, **over):
+    return oracle_config(O, w or W.plain_small(), **over)[0]
+
+
+# --------------------------------------------------------------------------------- geometry
+@pytest.mark.parametrize("case", ["cyl", "stripes", "flat", "halfint", "wrap"])
+def test_geometry_bit_exact(lbm, oracle_mod, case):
+    O = oracle_mod
+    over = {}
+    if case == "stripes":
+        over = dict(stripes=1, stripe_arc=7.0, mu_stripe_b=0.5)
+    if case == "flat":
+        over = dict(has_circle=0)
+    if case == "halfint":
+        over = dict(nx=77, ny=53, cx=38.5, cy=-0.5, R=20.5, drop_x=38.5, drop_y=40, drop_r=8)
+    if case == "wrap":
+        over = dict(nx=40, ny=30, cx=2.0, cy=3.0, R=9.0, drop_x=20, drop_y=22, drop_r=5)
+    cfg = _cfg(O, **over)
+    ref = O.Sim(cfg)
+    lat = gpu_lattice(lbm, cfg)
+    flags, muw, links = lat.geometry()
+    _, _, oflag, omuw = ref.ext()
+    assert np.array_equal(flags, oflag)
+    assert np.array_equal(muw.astype(np.float32), omuw.astype(np.float32))
+    assert np.array_equal(links, ref.links())
+    assert lat.info().n_fluid == int((oflag[2:-2] == 0).sum())
+
+
+# -------------------------------------------------------------------------------- time steps
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16)])
+def test_fp64_matches_oracle(lbm, oracle_mod, tile):
+    """FP64 kernel vs FP64 oracle: same arithmetic up to operation order."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=77, ny=53, cx=38.5, R=20.0, drop_x=38.5, drop_y=20.5 + 14, drop_r=14,
+               gy=-1e-5)
+    ref = O.Sim(cfg)
+    lat = gpu_lattice(lbm, cfg, precision=1, tile=tile)
+    for n in (1, 9, 290):
+        ref.step(n)
+        lat.step(n)
+        err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+        assert err < 1e-9, (n, err)
+    ux, uy = lat.velocity()
+    oux, ouy, _, _ = ref.velocity_force()
+    # the oracle reports the velocity of the state before its last step; step once more
+    ref2 = O.Sim(cfg)
+    ref2.step(301)
+    oux, ouy, _, _ = ref2.velocity_force()
+    assert np.abs(ux - oux).max() < 1e-9
+    assert np.abs(uy - ouy).max() < 1e-9
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 16), (32, 32)])
+def test_fp32_matches_oracle_ragged(lbm, oracle_mod, tile):
+    """FP32 path on a domain that is not a multiple of any tile (ragged tails in x and y)."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=77, ny=53, cx=38.5, R=20.0, drop_x=38.5, drop_y=20.5 + 14, drop_r=14)
+    ref = O.Sim(cfg)
+    ref.step(500)
+    lat = gpu_lattice(lbm, cfg, tile=tile)
+    lat.step(500)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < 2e-5, err
+
+
+def test_fp32_plain_workload_3000_steps(lbm, oracle_mod):
+    """The 200 x 120 workload (cylinder R = 40, drop r = 25, neutral walls): after 3000 steps
+    max |drho| <= 1e-4 rho_l, mass conserved, angles within 0.5 degrees of the oracle's."""
+    O = oracle_mod
+    cfg = _cfg(O)
+    ref = O.Sim(cfg)
+    ref.step(3000)
+    lat = gpu_lattice(lbm, cfg)
+    m0 = lat.mass()["mass"]
+    lat.step(3000)
+    rho, oref = lat.rho(), ref.rho()
+    err = np.abs(rho - oref).max() / cfg.rho_l
+    gas = oref < 0.5 * (cfg.rho_g + cfg.rho_l)
+    gas_err = np.abs(rho - oref)[gas & (oref > 0)].max() / cfg.rho_g
+    print(f"max |drho|/rho_l = {err:.3e}, gas max rel = {gas_err:.3e}")
+    assert err <= 1e-4
+    m1 = lat.mass()["mass"]
+    assert abs(m1 - m0) / m0 < 1e-5
+    gl, gr = lat.measure()
+    ol, orr, _ = ref.measure()
+    assert gl.status == 0 and gr.status == 0
+    assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
+
+
+def test_fp64_plain_workload(lbm, oracle_mod):
+    """FP64 variant of the 200 x 120 workload, 1000 steps: agreement to 1e-9 of rho_l."""
+    O = oracle_mod
+    cfg = _cfg(O)
+    ref = O.Sim(cfg)
+    ref.step(1000)
+    lat = gpu_lattice(lbm, cfg, precision=1)
+    lat.step(1000)
+    assert np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l < 1e-9
+
+
+def test_small_periodic_domain(lbm, oracle_mod):
+    """nx = 8 (the tile and its halo wrap the periodic axis several times)."""
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    nx, ny = 8, 40
+    j = np.arange(ny)[:, None] * np.ones((1, nx))
+    rho0 = mx["rho_g"] + (mx["rho_l"] - mx["rho_g"]) * 0.5 * (np.tanh((j - 12) / 2.) -
+                                                              np.tanh((j - 28) / 2.))
+    cfg = _cfg(O, nx=nx, ny=ny, has_circle=0)
+    ref = O.Sim(cfg, rho0)
+    ref.step(400)
+    lat = gpu_lattice(lbm, cfg, precision=1, rho0=rho0)
+    lat.step(400)
+    assert np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l < 1e-9
+
+
+def test_graph_chunks_equal_single_launches(lbm, oracle_mod):
+    """Steps replayed from the captured graph equal steps launched one by one (bitwise)."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=96, ny=64, cx=48, R=20, drop_x=48, drop_y=34.5, drop_r=14)
+    a = gpu_lattice(lbm, cfg)
+    b = gpu_lattice(lbm, cfg)
+    a.step(128 + 3)           # two graph chunks + 3 single launches
+    for _ in range(131):
+        b.step(1)
+    assert np.array_equal(a.rho(), b.rho())
+
+
+# ------------------------------------------------------------------------------ measurement
+def test_measure_identical_field_bit_exact(lbm, oracle_mod):
+    """On the same (FP32-rounded) density field the GPU finds the same liquid/gas links, points
+    and distances bit for bit, picks the same contact-line links and the same angles."""
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    for k, (R, r, yc, dx) in enumerate([(40.0, 25.0, 58.3, 0.3), (30.5, 18.0, 38.0, -1.2),
+                                        (45.0, 30.0, 75.0, 0.0)]):
+        nx, ny = 200, 120
+        rho = tanh_drop(nx, ny, 100.0 + dx, yc, r, rg, rl, 5.0).astype(np.float32).astype(np.float64)
+        cfg = _cfg(O, nx=nx, ny=ny, cx=100.0, R=R)
+        lat = gpu_lattice(lbm, cfg, rho0=rho)
+        ids, pd = lat.candidates()
+        oids, opd = O.candidates(cfg, rho, 0.5 * (rg + rl))
+        assert np.array_equal(ids, oids)
+        assert np.array_equal(pd, opd)
+        gl, gr = lat.measure()
+        ol, orr, _ = O.measure(cfg, rho, 0.5 * (rg + rl))
+        for g, o in ((gl, ol), (gr, orr)):
+            assert g.status == o.status == 0
+            assert (g.link1, g.link2) == (o.link1, o.link2)
+            assert g.d1 == o.d1 and g.d2 == o.d2
+            assert g.theta == pytest.approx(o.theta, abs=1e-6)
+            assert g.alpha == pytest.approx(o.alpha, abs=1e-6)
+            assert g.contact[0] == pytest.approx(o.contact[0], abs=1e-9)
+
+
+def test_measure_flat_wall(lbm, oracle_mod):
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    nx, ny = 160, 80
+    rho = tanh_drop(nx, ny, 80.2, 8.0, 30.0, rg, rl, 6.0).astype(np.float32).astype(np.float64)
+    cfg = _cfg(O, nx=nx, ny=ny, has_circle=0)
+    lat = gpu_lattice(lbm, cfg, rho0=rho)
+    gl, gr = lat.measure()
+    ol, orr, _ = O.measure(cfg, rho, 0.5 * (rg + rl))
+    assert (gl.link1, gl.link2, gr.link1, gr.link2) == (ol.link1, ol.link2, orr.link1, orr.link2)
+    assert gl.theta == pytest.approx(ol.theta, abs=1e-6)
+    assert gr.theta == pytest.approx(orr.theta, abs=1e-6)
+
+
+def test_measure_no_contact(lbm, oracle_mod):
+    """A drop far from the substrate has no interface points in the band: NO_CONTACT status."""
+    O = oracle_mod
+    cfg = _cfg(O, drop_y=95.0, drop_r=12.0)
+    lat = gpu_lattice(lbm, cfg)
+    st, (l, r) = lbm.lbm_measure_contact_angle(lat.ctx)
+    assert st == lbm.LBM_ERR_NO_CONTACT
+    assert l.status == lbm.LBM_ERR_NO_CONTACT and r.status == lbm.LBM_ERR_NO_CONTACT
+
+
+# ---------------------------------------------------------------------------- full size
+def test_full_size_sampled(lbm, oracle_mod):
+    """2048 x 1024 (cylinder R = 300, drop r = 150, sessile body force), bench launch config:
+    50 FP32 steps vs the oracle on every node, mass to FP32 round-off."""
+    O = oracle_mod
+    w = W.plain_large(0)
+    cfg = oracle_config(O, w)[0]
+    ref = O.Sim(cfg)
+    ref.step(50)
+    lat = gpu_lattice(lbm, cfg)
+    m0 = lat.mass()["mass"]
+    lat.step(50)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < 2e-5, err
+    m1 = lat.mass()["mass"]
+    assert abs(m1 - m0) / m0 < 1e-6
+
+
+def test_stream_from_torch(lbm, oracle_mod):
+    """The library runs on a caller's torch stream."""
+    import torch
+    O = oracle_mod
+    cfg = _cfg(O, nx=96, ny=64, cx=48, R=20, drop_x=48, drop_y=34.5, drop_r=14)
+    s = torch.cuda.Stream()
+    a = gpu_lattice(lbm, cfg, stream=s)
+    b = gpu_lattice(lbm, cfg)
+    a.step(100)
+    b.step(100)
+    assert np.array_equal(a.rho(), b.rho())
+    # device-pointer read into torch tensors
+    r = torch.zeros(64 * 96, dtype=torch.float64, device="cuda")
+    lbm.lbm_read_fields(a.ctx, lbm.LBM_FIELD_RHO, 96, 64, device_out=(r.data_ptr(), None, None))
+    torch.cuda.synchronize()
+    assert np.array_equal(r.cpu().numpy().reshape(64, 96), a.rho())
