@@ -167,6 +167,30 @@ lbm_status lbm_read_candidates(lbm_ctx *ctx, int64_t *ids, double *pxyd, int64_t
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 
+/* Allocation-free variant of lbm_mass for a caller-owned FP32 density field.
+ * For callers that must not allocate device memory at this point: a framework that owns every
+ * device byte through its own pool, code that cannot afford the implicit device synchronisation
+ * of cudaMalloc/cudaFree, or a process that has budgeted the whole GPU. The paper has no
+ * counterpart; this is a deployment convenience, not part of the method.
+ *  rho:   device, rho[j * pitch + i] for 0 <= j < ny, 0 <= i < nx (fluid-domain rows).
+ *  flags: device, same layout; a node is summed when its flag is 0 (LBM_FLUID).
+ *  out:   device, 5 doubles: total mass, number of liquid nodes (rho > rho_m), their centroid
+ *         x and y, and the number of non-finite or non-positive densities.
+ *  stream: cudaStream_t or NULL; work is queued asynchronously on the calling thread's current
+ *         device, which must hold the three arrays.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. Its scratch is a fixed device
+ * array inside the library image of LBM_NOALLOC_MAX_ROWS x 8 doubles (256 KiB), which every GPU
+ * that loads the library holds until the process exits; ny > LBM_NOALLOC_MAX_ROWS is rejected
+ * with LBM_ERR_ARG. The first call on a device looks up the array's device address (a one-time
+ * set-up per device); make that first call before any stream capture. Calls overwrite every
+ * scratch entry they read, so no clearing is needed, but calls that overlap on the GPU share the
+ * array and race. Errors: LBM_ERR_ARG (NULL pointer, nx or ny <= 0, pitch < nx, ny too large),
+ * LBM_ERR_CUDA (no current device, set-up or launch failure); the message is available from
+ * lbm_last_error(NULL). */
+#define LBM_NOALLOC_MAX_ROWS 4096
+lbm_status lbm_mass_noalloc(const float *rho, const uint8_t *flags, int32_t nx, int32_t ny,
+                            int32_t pitch, double rho_m, double *out, void *stream);
+
 /* Wait for the context's stream. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
 

@@ -232,6 +232,11 @@ lbm_status capture_graph(lbm_ctx* c, int start) {
 
 }  // namespace
 
+namespace lbm {
+// message for lbm_last_error(NULL) from entry points outside this file
+void set_global_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace lbm
+
 extern "C" {
 
 lbm_status lbm_coexistence(int32_t eos, double Tr, double out[4]) {
