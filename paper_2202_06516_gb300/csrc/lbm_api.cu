@@ -269,6 +269,11 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const size_t esz = p->precision == LBM_FP32 ? 4 : 8;
     if (lbm::step_smem_bytes(tx, ty, esz) == 0)
         return fail(nullptr, LBM_ERR_ARG, "lbm_create: unsupported tile shape for this precision");
+    {
+        const long long P = (p->nx + 2 * lbm::kPadX + 31) / 32 * 32;
+        if (9 * P * (p->ny + 2 * lbm::kPadY + 1) >= (1LL << 31))
+            return fail(nullptr, LBM_ERR_ARG, "lbm_create: lattice too large (plane >= 2^31 nodes)");
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -284,9 +289,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->device = p->device;
     c->nx = p->nx;
     c->ny = p->ny;
-    c->P = (p->nx + 31) / 32 * 32;
-    c->plane = (size_t)c->ny * c->P;
-    c->plane_ext = (size_t)(c->ny + 4) * c->P;
+    c->P = (p->nx + 2 * lbm::kPadX + 31) / 32 * 32;
+    // one slack row past the last pad row: the step kernel's 4-wide halo loads may start up to
+    // 3 columns before the end of a padded row
+    c->plane = (size_t)(c->ny + 2 * lbm::kPadY + 1) * c->P;
     c->esz = esz;
     c->tile_x = tx;
     c->tile_y = ty;
@@ -322,8 +328,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         e = cudaMalloc(&c->h[k], hbytes);
         if (e == cudaSuccess) e = cudaMalloc(&c->rho[k], c->plane * esz);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&c->muw, c->plane_ext * esz);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->flags, c->plane_ext);
+    if (e == cudaSuccess) e = cudaMalloc(&c->muw, c->plane * esz);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->flags, c->plane);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->linkmask, c->plane);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->red_partials, sizeof(double) * 8 * c->red_blocks);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->red_out, sizeof(lbm::ReduceOut));
@@ -351,6 +357,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     a.nx = c->nx;
     a.ny = c->ny;
     a.P = c->P;
+    a.plane = (int)c->plane;
     a.has_circle = g->has_circle;
     a.stripes = g->stripes;
     a.cx2 = llround(2.0 * g->cx);
@@ -364,8 +371,9 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     a.mu_stripe_b = g->mu_stripe_b;
     a.mu_bottom = g->mu_bottom;
     a.mu_top = g->mu_top;
-    LBM_CUDA(c, cudaMemsetAsync(c->flags, lbm::kSolid, c->plane_ext, c->stream));
-    LBM_CUDA(c, cudaMemsetAsync(c->muw, 0, c->plane_ext * c->esz, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->flags, lbm::kSolid, c->plane, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->muw, 0, c->plane * c->esz, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->linkmask, 0, c->plane, c->stream));
     LBM_CUDA(c, lbm::launch_geometry(c, a));
     double* d_rho0 = nullptr;
     if (g->rho0) {
@@ -485,19 +493,21 @@ lbm_status lbm_read_geometry(lbm_ctx* c, uint8_t* flags, double* mu_w, int64_t* 
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_read_geometry: no geometry");
     DeviceGuard dg(c->device);
     const int nx = c->nx, rows = c->ny + 4;
+    const size_t o_ext = (size_t)lbm::lidx(c->P, 0, -2), o_dom = (size_t)lbm::lidx(c->P, 0, 0);
     if (flags)
-        LBM_CUDA(c, cudaMemcpy2DAsync(flags, nx, c->flags, c->P, nx, rows, cudaMemcpyDeviceToHost,
-                                      c->stream));
+        LBM_CUDA(c, cudaMemcpy2DAsync(flags, nx, c->flags + o_ext, c->P, nx, rows,
+                                      cudaMemcpyDeviceToHost, c->stream));
     std::vector<unsigned char> mw;
     if (mu_w) {
         mw.resize((size_t)rows * nx * c->esz);
-        LBM_CUDA(c, cudaMemcpy2DAsync(mw.data(), nx * c->esz, c->muw, c->P * c->esz, nx * c->esz,
-                                      rows, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaMemcpy2DAsync(mw.data(), nx * c->esz, (const char*)c->muw + o_ext * c->esz,
+                                      c->P * c->esz, nx * c->esz, rows, cudaMemcpyDeviceToHost,
+                                      c->stream));
     }
     std::vector<uint8_t> lm;
     if (links || n_links) {
         lm.resize((size_t)c->ny * nx);
-        LBM_CUDA(c, cudaMemcpy2DAsync(lm.data(), nx, c->linkmask, c->P, nx, c->ny,
+        LBM_CUDA(c, cudaMemcpy2DAsync(lm.data(), nx, c->linkmask + o_dom, c->P, nx, c->ny,
                                       cudaMemcpyDeviceToHost, c->stream));
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -20,6 +20,8 @@ __device__ __forceinline__ int wrap(int i, int nx) {
     return i < 0 ? i + nx : i;
 }
 
+// Classification on the canonical nodes (0 <= x < nx, -2 <= j < ny + 2); the remaining pad rows
+// stay inner solid (memset by the caller) and the pad columns are filled afterwards.
 __global__ void k_classify(uint8_t* flags, GeomArgs g) {
     const int rows = g.ny + 4;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * g.nx;
@@ -31,7 +33,7 @@ __global__ void k_classify(uint8_t* flags, GeomArgs g) {
             const long long dx = 2LL * i - g.cx2, dy = 2LL * j - g.cy2;
             solid = dx * dx + dy * dy <= g.r2 * g.r2;
         }
-        flags[(size_t)r * g.P + i] = solid ? kSolid : kFluid;
+        flags[lidx(g.P, i, j)] = solid ? kSolid : kFluid;
     }
 }
 
@@ -41,15 +43,16 @@ __global__ void k_layer(uint8_t* flags, GeomArgs g, uint8_t match, uint8_t promo
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * g.nx;
          e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e / g.nx), i = (int)(e % g.nx);
-        if (flags[(size_t)r * g.P + i] != kSolid) continue;
+        const int j = r - 2;
+        if (flags[lidx(g.P, i, j)] != kSolid) continue;
         bool hit = false;
 #pragma unroll
         for (int q = 1; q < 9; ++q) {
             const int rr = r + qy(q);
             if (rr < 0 || rr >= rows) continue;
-            hit |= flags[(size_t)rr * g.P + wrap(i + qx(q), g.nx)] == match;
+            hit |= flags[lidx(g.P, wrap(i + qx(q), g.nx), j + qy(q))] == match;
         }
-        if (hit) flags[(size_t)r * g.P + i] = promote;
+        if (hit) flags[lidx(g.P, i, j)] = promote;
     }
 }
 
@@ -60,7 +63,7 @@ __global__ void k_muw(const uint8_t* flags, T* muw, GeomArgs g) {
          e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e / g.nx), i = (int)(e % g.nx);
         const int j = r - 2;
-        const uint8_t f = flags[(size_t)r * g.P + i];
+        const uint8_t f = flags[lidx(g.P, i, j)];
         double mu = 0.0;
         if (f == kLayer1 || f == kLayer2) {
             bool in_disc = false;
@@ -80,7 +83,7 @@ __global__ void k_muw(const uint8_t* flags, T* muw, GeomArgs g) {
                 mu = j < 0 ? g.mu_bottom : g.mu_top;
             }
         }
-        muw[(size_t)r * g.P + i] = (T)mu;
+        muw[lidx(g.P, i, j)] = (T)mu;
     }
 }
 
@@ -92,14 +95,14 @@ __global__ void k_linkmask(const uint8_t* flags, uint8_t* mask, unsigned long lo
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / g.nx), i = (int)(n % g.nx);
         uint8_t m = 0;
-        if (flags[(size_t)(j + 2) * g.P + i] == kFluid) {
+        if (flags[lidx(g.P, i, j)] == kFluid) {
             ++local;
 #pragma unroll
             for (int q = 1; q < 9; ++q)
-                if (flags[(size_t)(j + 2 + qy(q)) * g.P + wrap(i + qx(q), g.nx)] != kFluid)
+                if (flags[lidx(g.P, wrap(i + qx(q), g.nx), j + qy(q))] != kFluid)
                     m |= (uint8_t)(1u << (q - 1));
         }
-        mask[(size_t)j * g.P + i] = m;
+        mask[lidx(g.P, i, j)] = m;
     }
     // integer atomics: exact and order-independent
     for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
@@ -114,9 +117,9 @@ __global__ void k_init_rho(const uint8_t* flags, T* rho, T* rho_other, const dou
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)g.ny * g.nx;
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / g.nx), i = (int)(n % g.nx);
-        const size_t o = (size_t)j * g.P + i;
+        const int o = lidx(g.P, i, j);
         double v = 0.0;
-        if (flags[(size_t)(j + 2) * g.P + i] == kFluid) {
+        if (flags[o] == kFluid) {
             if (rho0) {
                 v = rho0[n];
             } else {
@@ -134,25 +137,36 @@ __global__ void k_init_rho(const uint8_t* flags, T* rho, T* rho_other, const dou
 // f(x, 0) = w_q rho0(x) means f*_q(z, -1) = w_q rho0(z + e_q) when z + e_q is fluid (it streams
 // there) and w_q rho0(z) when it is solid (it bounces back to z).
 template <typename T>
-__global__ void k_init_h(const uint8_t* flags, const T* rho, T* h, T* h_other, GeomArgs g,
-                         long long plane) {
+__global__ void k_init_h(const uint8_t* flags, const T* rho, T* h, GeomArgs g) {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)g.ny * g.nx;
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / g.nx), i = (int)(n % g.nx);
-        const size_t o = (size_t)j * g.P + i;
-        const bool fluid = flags[(size_t)(j + 2) * g.P + i] == kFluid;
+        const int o = lidx(g.P, i, j);
+        const bool fluid = flags[o] == kFluid;
         const T r0 = rho[o];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             T v = (T)0;
             if (fluid && q > 0) {
-                const int ti = wrap(i + qx(q), g.nx), tj = j + qy(q);
-                if (flags[(size_t)(tj + 2) * g.P + ti] == kFluid)
-                    v = qw<T>(q) * (rho[(size_t)tj * g.P + ti] - r0);
+                const int t = lidx(g.P, wrap(i + qx(q), g.nx), j + qy(q));
+                if (flags[t] == kFluid) v = qw<T>(q) * (rho[t] - r0);
             }
-            h[(size_t)q * plane + o] = v;
-            h_other[(size_t)q * plane + o] = (T)0;
+            h[(size_t)q * g.plane + o] = v;
         }
+    }
+}
+
+// Periodic images: columns -kPadX..-1 copy nx-kPadX..nx-1 and nx..nx+kPadX-1 copy 0..kPadX-1,
+// on every row of the padded plane.
+template <typename T>
+__global__ void k_fill_pads(T* a, int nx, int P, int rows) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * 2 * kPadX;
+         e += gridDim.x * blockDim.x) {
+        const int r = e / (2 * kPadX), k = e % (2 * kPadX);
+        const int j = r - kPadY;
+        const int x = k < kPadX ? k - kPadX : nx + (k - kPadX);
+        const int src = k < kPadX ? x + nx : x - nx;
+        a[lidx(P, x, j)] = a[lidx(P, src, j)];
     }
 }
 
@@ -174,6 +188,15 @@ cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g) {
         k_muw<float><<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, (float*)c->muw, g);
     else
         k_muw<double><<<grid_for(next), kThreads, 0, c->stream>>>(c->flags, (double*)c->muw, g);
+    const int rows = c->ny + 2 * kPadY;
+    k_fill_pads<uint8_t><<<grid_for(rows * 2 * kPadX), kThreads, 0, c->stream>>>(c->flags, c->nx,
+                                                                                  c->P, rows);
+    if (c->esz == 4)
+        k_fill_pads<float><<<grid_for(rows * 2 * kPadX), kThreads, 0, c->stream>>>(
+            (float*)c->muw, c->nx, c->P, rows);
+    else
+        k_fill_pads<double><<<grid_for(rows * 2 * kPadX), kThreads, 0, c->stream>>>(
+            (double*)c->muw, c->nx, c->P, rows);
     unsigned long long* d_nf = (unsigned long long*)c->red_out;  // scratch, overwritten later
     cudaError_t e = cudaMemsetAsync(d_nf, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
@@ -192,22 +215,45 @@ cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& geo, const double*
     g.nx = c->nx;
     g.ny = c->ny;
     g.P = c->P;
+    g.plane = (int)c->plane;
     const long long nf = (long long)c->ny * c->nx;
+    // both buffers start at zero (pads and solid nodes included)
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(c->h[k], 0, 9 * c->plane * c->esz, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->rho[k], 0, c->plane * c->esz, c->stream);
+    }
+    if (e != cudaSuccess) return e;
     if (c->esz == 4) {
         k_init_rho<float><<<grid_for(nf), kThreads, 0, c->stream>>>(
             c->flags, (float*)c->rho[0], (float*)c->rho[1], d_rho0, g, c->rho_g, c->rho_l,
             geo.drop_x, geo.drop_y, geo.drop_r, geo.drop_W);
-        k_init_h<float><<<grid_for(nf), kThreads, 0, c->stream>>>(
-            c->flags, (const float*)c->rho[0], (float*)c->h[0], (float*)c->h[1], g,
-            (long long)c->plane);
+        k_init_h<float><<<grid_for(nf), kThreads, 0, c->stream>>>(c->flags, (const float*)c->rho[0],
+                                                                 (float*)c->h[0], g);
     } else {
         k_init_rho<double><<<grid_for(nf), kThreads, 0, c->stream>>>(
             c->flags, (double*)c->rho[0], (double*)c->rho[1], d_rho0, g, c->rho_g, c->rho_l,
             geo.drop_x, geo.drop_y, geo.drop_r, geo.drop_W);
         k_init_h<double><<<grid_for(nf), kThreads, 0, c->stream>>>(
-            c->flags, (const double*)c->rho[0], (double*)c->h[0], (double*)c->h[1], g,
-            (long long)c->plane);
+            c->flags, (const double*)c->rho[0], (double*)c->h[0], g);
     }
+    e = launch_fill_pads(c, c->rho[0], c->esz);
+    for (int q = 0; q < 9 && e == cudaSuccess; ++q)
+        e = launch_fill_pads(c, (char*)c->h[0] + (size_t)q * c->plane * c->esz, c->esz);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_pads(lbm_ctx* c, void* plane, size_t esz) {
+    const int rows = c->ny + 2 * kPadY;
+    const int n = rows * 2 * kPadX;
+    if (esz == 4)
+        k_fill_pads<float><<<grid_for(n), kThreads, 0, c->stream>>>((float*)plane, c->nx, c->P, rows);
+    else if (esz == 8)
+        k_fill_pads<double><<<grid_for(n), kThreads, 0, c->stream>>>((double*)plane, c->nx, c->P, rows);
+    else
+        k_fill_pads<uint8_t><<<grid_for(n), kThreads, 0, c->stream>>>((uint8_t*)plane, c->nx, c->P,
+                                                                      rows);
     return cudaGetLastError();
 }
 

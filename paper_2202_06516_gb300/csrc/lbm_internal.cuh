@@ -28,6 +28,17 @@ __host__ __device__ constexpr T qw(int q) {
 
 constexpr uint8_t kFluid = 0, kLayer1 = 1, kLayer2 = 2, kSolid = 3;
 
+// Device layout shared by every plane (populations, density, flags, wall chemical potential):
+// node (x, j) of the fluid domain lives at (j + kPadY) * P + kPadX + x. Columns -kPadX..-1 and
+// nx..nx+kPadX-1 hold copies of the periodic images (x + nx, x - nx); rows -2, -1, ny, ny+1 are
+// the solid wall rows, and the remaining pad rows are inner solid. With the pads in place the
+// step kernel reads any node within 8 columns and 7 rows of the domain without wrapping. Every
+// plane ends with one more (slack) row.
+constexpr int kPadX = 8, kPadY = 8;
+__host__ __device__ __forceinline__ int lidx(int P, int x, int j) {
+    return (j + kPadY) * P + kPadX + x;
+}
+
 // Equation-of-state constants in the form the kernels evaluate psi'(rho) in.
 struct EosConst {
     int eos;      // LBM_EOS_PR / LBM_EOS_CS
@@ -39,16 +50,16 @@ struct EosConst {
 // Arguments of the fused step kernel (one time step, Eq. 1-4, 7, 12-14).
 template <typename T>
 struct StepArgs {
-    const T* h_in;     // 9 planes, post-collision deviations f*_q - w_q rho(t) (see step .cu)
+    const T* h_in;     // 9 planes, post-collision deviations f*_q - w_q rho (see step .cu)
     T* h_out;
-    const T* rho_in;   // rho(t), fluid domain, pitch P
+    const T* rho_in;   // rho(t)
     T* rho_out;        // rho(t+1)
-    const uint8_t* flags;  // extended rows -2..ny+1
-    const T* muw;          // extended rows, wall chemical potential
-    T* vx;             // optional velocity output (macroscopic mode), fluid domain
+    const uint8_t* flags;
+    const T* muw;      // wall chemical potential on the wetting layers
+    T* vx;             // optional velocity output (macroscopic mode)
     T* vy;
     int nx, ny, P;
-    long long plane;   // ny * P
+    int plane;         // elements per plane: (ny + 2 kPadY + 1) * P
     T k2, kappa, gx, gy;
     T s_e, s_eps, s_q, s_v, inv_tau;
     int bgk;
@@ -57,7 +68,7 @@ struct StepArgs {
 };
 
 struct GeomArgs {
-    int nx, ny, P;
+    int nx, ny, P, plane;
     int has_circle, stripes;
     long long cx2, cy2, r2;  // doubled-integer circle
     double cx, cy, R, stripe_arc;
@@ -82,13 +93,13 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nx = 0, ny = 0, P = 0;
-    size_t plane = 0, plane_ext = 0;
+    size_t plane = 0;  // elements per padded plane
     size_t esz = 4;
     void* h[2] = {nullptr, nullptr};
     void* rho[2] = {nullptr, nullptr};
     void* muw = nullptr;
     uint8_t* flags = nullptr;
-    uint8_t* linkmask = nullptr;   // per fluid-domain node, bit q-1 set when x + e_q is solid
+    uint8_t* linkmask = nullptr;   // per node, bit q-1 set when fluid x has a solid x + e_q
     int cur = 0;
     bool has_geometry = false;
     int64_t steps = 0;
@@ -127,5 +138,6 @@ cudaError_t launch_reduce(lbm_ctx* c);
 cudaError_t launch_measure(lbm_ctx* c);
 cudaError_t launch_candidates(lbm_ctx* c, uint8_t* d_mark, double* d_pxyd);
 cudaError_t launch_to_double(lbm_ctx* c, const void* src, double* dst, int src_is_rho_plane);
+cudaError_t launch_fill_pads(lbm_ctx* c, void* plane, size_t esz);
 
 }  // namespace lbm

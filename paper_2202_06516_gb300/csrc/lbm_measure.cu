@@ -49,8 +49,8 @@ __global__ void k_reduce(const T* rho, const uint8_t* flags, int nx, int ny, int
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)nx * ny;
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / nx), i = (int)(n % nx);
-        if (flags[(size_t)(j + 2) * P + i] != kFluid) continue;
-        const double r = (double)rho[(size_t)j * P + i];
+        if (flags[lidx(P, i, j)] != kFluid) continue;
+        const double r = (double)rho[lidx(P, i, j)];
         acc[0] += r;
         if (!(r > 0.0) || !isfinite(r)) acc[4] += 1.0;
         if (r > rho_m) {
@@ -99,8 +99,8 @@ __device__ __forceinline__ bool link_point(const T* rho, const uint8_t* flags, i
     const int ti = i + slot_x(sl), tj = j + slot_y(sl);
     if (tj >= ny) return false;
     const int wi = ti < 0 ? ti + nx : (ti >= nx ? ti - nx : ti);
-    if (flags[(size_t)(tj + 2) * P + wi] != kFluid) return false;
-    const double ra = (double)rho[(size_t)j * P + i], rb = (double)rho[(size_t)tj * P + wi];
+    if (flags[lidx(P, wi, tj)] != kFluid) return false;
+    const double ra = (double)rho[lidx(P, i, j)], rb = (double)rho[lidx(P, wi, tj)];
     const bool la = ra > rho_m, lb = rb > rho_m;
     if (la == lb) return false;
     double xg, yg, rg, rl, ex, ey;
@@ -133,7 +133,7 @@ __global__ void k_meas_cand(const T* rho, const uint8_t* flags, int nx, int ny, 
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)nx * ny;
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / nx), i = (int)(n % nx);
-        if (flags[(size_t)(j + 2) * P + i] != kFluid) continue;
+        if (flags[lidx(P, i, j)] != kFluid) continue;
         for (int sl = 0; sl < 4; ++sl) {
             double px, py;
             if (!link_point<T>(rho, flags, nx, ny, P, rho_m, i, j, sl, px, py)) continue;
@@ -269,7 +269,7 @@ __global__ void k_cand_dense(const T* rho, const uint8_t* flags, int nx, int ny,
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)nx * ny;
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / nx), i = (int)(n % nx);
-        const bool fl = flags[(size_t)(j + 2) * P + i] == kFluid;
+        const bool fl = flags[lidx(P, i, j)] == kFluid;
         for (int sl = 0; sl < 4; ++sl) {
             double px = 0, py = 0;
             const bool ok = fl && link_point<T>(rho, flags, nx, ny, P, rho_m, i, j, sl, px, py);
@@ -289,7 +289,7 @@ __global__ void k_to_double(const T* src, const uint8_t* flags, int nx, int ny, 
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)nx * ny;
          n += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(n / nx), i = (int)(n % nx);
-        dst[n] = flags[(size_t)(j + 2) * P + i] == kFluid ? (double)src[(size_t)j * P + i] : 0.0;
+        dst[n] = flags[lidx(P, i, j)] == kFluid ? (double)src[lidx(P, i, j)] : 0.0;
     }
 }
 
