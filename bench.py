@@ -124,12 +124,12 @@ def _resolve(w, lbm_mod):
     return co, neutral
 
 
-def _make_lattice(lbm, w, stream=None):
+def _make_lattice(lbm, w, stream=None, tile=(0, 0), min_blocks=0):
     m = w.model
     co, neutral = _resolve(w, lbm)
     lat = lbm.Lattice(w.nx, w.ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
                       tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"], gx=w.g[0],
-                      gy=w.g[1], stream=stream)
+                      gy=w.g[1], stream=stream, tile=tile, min_blocks=min_blocks)
     geo = dict(circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
                mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top, drop=w.drop)
     return lat, geo
@@ -143,8 +143,9 @@ def run_cuda(args, rank, world, dist):
     torch.cuda.set_device(dev)
     w = W.plain_large(seed=rank)
     stream = torch.cuda.Stream(device=dev)
-    lat, geo = _make_lattice(lbm, w, stream=stream)
+    lat, geo = _make_lattice(lbm, w, stream=stream, tile=args.tile, min_blocks=args.min_blocks)
     lat.set_geometry(**geo)
+    tile = (lat.info().tile_x, lat.info().tile_y, lat.info().min_blocks)
     n_nodes = w.nx * w.ny
     n_fluid = int(lat.info().n_fluid)
 
@@ -201,7 +202,8 @@ def run_cuda(args, rank, world, dist):
         d = np.sqrt((i - w.drop[0]) ** 2 + (j - w.drop[1]) ** 2)
         rho0 = 0.5 * (co["rho_g"] + co["rho_l"]) + 0.5 * (co["rho_g"] - co["rho_l"]) * \
             np.tanh(2.0 * (d - w.drop[2]) / w.drop[3])
-        lat2, geo2 = _make_lattice(lbm, w, stream=stream)
+        lat2, geo2 = _make_lattice(lbm, w, stream=stream, tile=args.tile,
+                                   min_blocks=args.min_blocks)
         lat2.set_geometry(**geo2)
         lat2.step(max(3, args.warmup))
         lat2.synchronize()
@@ -242,7 +244,8 @@ def run_cuda(args, rank, world, dist):
                    "eos": "Peng-Robinson Tr=0.7", "seed": "rank"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_step<float,32,16>", "kernel_us_per_launch": kernel_us,
+                     "kernel": f"k_step<float,{tile[0]},{tile[1]}> min_blocks={tile[2]}",
+                     "kernel_us_per_launch": kernel_us,
                      "bytes_per_launch": BYTES_PER_FLUID_NODE * n_fluid},
         "e2e": e2e,
         "gpu_launches": args.steps + 4 * nmeas,
@@ -303,6 +306,10 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
+                    help="step-kernel tile, e.g. 32x16 (default: the library's)")
+    ap.add_argument("--min-blocks", type=int, default=0,
+                    help="step-kernel CTAs per SM to fit registers to (0: none)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

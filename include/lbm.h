@@ -48,8 +48,10 @@ enum { LBM_FLUID = 0, LBM_LAYER1 = 1, LBM_LAYER2 = 2, LBM_SOLID = 3 }; /* node c
  *  s_e, s_eps, s_q: MRT rates of S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_v, s_v) (Sec. 2.1).
  *  gx, gy: body acceleration; the force rho*g acts on gas and liquid (Sec. 4).
  *  rho_g, rho_l: coexistence densities; <= 0 selects the library's Maxwell construction.
- *  tile_x, tile_y: step-kernel tile; 0 selects the default (32 x 16). Supported: 32x8, 32x16,
- *    64x16, 32x32.
+ *  tile_x, tile_y, min_blocks: step-kernel variant: tile shape and the CTAs per SM the register
+ *    budget is fitted to (0 = no constraint); all three 0 selects 32x16/5 in FP32 and 32x16/0 in
+ *    FP64. Supported (tile/min_blocks):
+ *    FP32 32x8/0, 32x8/6, 32x16/0, 32x16/5, 32x16/6, 64x16/0, 32x32/0; FP64 32x8/0, 32x16/0.
  *  stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or NULL. */
 typedef struct lbm_params {
     int32_t nx, ny;
@@ -58,6 +60,7 @@ typedef struct lbm_params {
     int32_t collision; /* LBM_MRT or LBM_BGK */
     int32_t device;    /* CUDA device ordinal */
     int32_t tile_x, tile_y;
+    int32_t min_blocks;
     double Tr, k2, kappa, tau, s_e, s_eps, s_q;
     double gx, gy;
     double rho_g, rho_l;
@@ -105,6 +108,7 @@ typedef struct lbm_info {
     int64_t n_fluid;                    /* fluid nodes */
     int32_t tile_x, tile_y;
     int32_t precision;
+    int32_t min_blocks;
 } lbm_info;
 
 /* Maxwell equal-area coexistence of an EOS at reduced temperature Tr (Sec. 4, after Eq. 16),

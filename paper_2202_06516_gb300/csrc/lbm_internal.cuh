@@ -119,7 +119,7 @@ struct lbm_ctx {
     // graphs of GRAPH_CHUNK steps starting from buffer 0 / buffer 1
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
-    int tile_x = 32, tile_y = 16;
+    int tile_x = 32, tile_y = 16, min_blocks = 0;
     std::string err;
 };
 
@@ -132,7 +132,7 @@ constexpr int kRedThreads = 256;
 cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g);
 cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& g, const double* d_rho0);
 cudaError_t launch_step(lbm_ctx* c, int src, bool macro);
-size_t step_smem_bytes(int tile_x, int tile_y, size_t esz);
+size_t step_smem_bytes(int tile_x, int tile_y, size_t esz, int min_blocks);
 cudaError_t step_configure(lbm_ctx* c);
 cudaError_t launch_reduce(lbm_ctx* c);
 cudaError_t launch_measure(lbm_ctx* c);

@@ -311,8 +311,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
     }
 }
 
-template <typename T, int TX, int TY, int NT, bool MACRO>
-__global__ void __launch_bounds__(NT) k_step(const StepArgs<T> a, const T rho_mid) {
+template <typename T, int TX, int TY, int NT, bool MACRO, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs<T> a, const T rho_mid) {
     using L = Layout<T, TX, TY>;
     constexpr int RW = L::RW, RH = L::RH, MW = L::MW, MH = L::MH, CW = L::CW, CH = L::CH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -347,25 +347,25 @@ __global__ void __launch_bounds__(NT) k_step(const StepArgs<T> a, const T rho_mi
         step_body<T, TX, TY, NT, MACRO, false>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int MINB>
 cudaError_t configure_one() {
     using L = Layout<T, TX, TY>;
-    cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, 256, false>,
+    cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, 256, false, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step<T, TX, TY, 256, true>,
+    return cudaFuncSetAttribute(k_step<T, TX, TY, 256, true, MINB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int MINB>
 cudaError_t launch_one(lbm_ctx* c, const StepArgs<T>& a, bool macro) {
     using L = Layout<T, TX, TY>;
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY);
     const T rho_mid = (T)(0.5 * (c->rho_g + c->rho_l));
     if (macro)
-        k_step<T, TX, TY, 256, true><<<grid, 256, L::bytes, c->stream>>>(a, rho_mid);
+        k_step<T, TX, TY, 256, true, MINB><<<grid, 256, L::bytes, c->stream>>>(a, rho_mid);
     else
-        k_step<T, TX, TY, 256, false><<<grid, 256, L::bytes, c->stream>>>(a, rho_mid);
+        k_step<T, TX, TY, 256, false, MINB><<<grid, 256, L::bytes, c->stream>>>(a, rho_mid);
     return cudaGetLastError();
 }
 
@@ -403,43 +403,48 @@ StepArgs<T> make_args(lbm_ctx* c, int src) {
 
 }  // namespace
 
-size_t step_smem_bytes(int tx, int ty, size_t esz) {
-    if (esz == 4) {
-        if (tx == 32 && ty == 8) return Layout<float, 32, 8>::bytes;
-        if (tx == 32 && ty == 16) return Layout<float, 32, 16>::bytes;
-        if (tx == 64 && ty == 16) return Layout<float, 64, 16>::bytes;
-        if (tx == 32 && ty == 32) return Layout<float, 32, 32>::bytes;
-    } else {
-        if (tx == 32 && ty == 8) return Layout<double, 32, 8>::bytes;
-        if (tx == 32 && ty == 16) return Layout<double, 32, 16>::bytes;
-    }
+// Supported step-kernel variants: tile (TX, TY) and the minimum resident CTAs per SM the
+// compiler is asked to fit (register budget); min_blocks 0 = no constraint.
+#define LBM_STEP_VARIANTS(X)                                     \
+    X(float, 32, 8, 1) X(float, 32, 8, 6) X(float, 32, 16, 1)    \
+    X(float, 32, 16, 5) X(float, 32, 16, 6) X(float, 64, 16, 1)  \
+    X(float, 32, 32, 1) X(double, 32, 8, 1) X(double, 32, 16, 1)
+
+static int minb_of(lbm_ctx* c) { return c->min_blocks > 0 ? c->min_blocks : 1; }
+
+size_t step_smem_bytes(int tx, int ty, size_t esz, int min_blocks) {
+    const int mb = min_blocks > 0 ? min_blocks : 1;
+#define X(T, A, B, M) \
+    if (esz == sizeof(T) && tx == A && ty == B && mb == M) return Layout<T, A, B>::bytes;
+    LBM_STEP_VARIANTS(X)
+#undef X
     return 0;
 }
 
 cudaError_t step_configure(lbm_ctx* c) {
-    if (c->esz == 4) {
-        if (c->tile_x == 32 && c->tile_y == 8) return configure_one<float, 32, 8>();
-        if (c->tile_x == 32 && c->tile_y == 16) return configure_one<float, 32, 16>();
-        if (c->tile_x == 64 && c->tile_y == 16) return configure_one<float, 64, 16>();
-        if (c->tile_x == 32 && c->tile_y == 32) return configure_one<float, 32, 32>();
-    } else {
-        if (c->tile_x == 32 && c->tile_y == 8) return configure_one<double, 32, 8>();
-        if (c->tile_x == 32 && c->tile_y == 16) return configure_one<double, 32, 16>();
-    }
+#define X(T, A, B, M) \
+    if (c->esz == sizeof(T) && c->tile_x == A && c->tile_y == B && minb_of(c) == M) \
+        return configure_one<T, A, B, M>();
+    LBM_STEP_VARIANTS(X)
+#undef X
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step(lbm_ctx* c, int src, bool macro) {
     if (c->esz == 4) {
         const StepArgs<float> a = make_args<float>(c, src);
-        if (c->tile_x == 32 && c->tile_y == 8) return launch_one<float, 32, 8>(c, a, macro);
-        if (c->tile_x == 32 && c->tile_y == 16) return launch_one<float, 32, 16>(c, a, macro);
-        if (c->tile_x == 64 && c->tile_y == 16) return launch_one<float, 64, 16>(c, a, macro);
-        if (c->tile_x == 32 && c->tile_y == 32) return launch_one<float, 32, 32>(c, a, macro);
+#define X(T, A, B, M)                                                                 \
+    if (sizeof(T) == 4 && c->tile_x == A && c->tile_y == B && minb_of(c) == M) \
+        return launch_one<float, A, B, M>(c, a, macro);
+        LBM_STEP_VARIANTS(X)
+#undef X
     } else {
         const StepArgs<double> a = make_args<double>(c, src);
-        if (c->tile_x == 32 && c->tile_y == 8) return launch_one<double, 32, 8>(c, a, macro);
-        if (c->tile_x == 32 && c->tile_y == 16) return launch_one<double, 32, 16>(c, a, macro);
+#define X(T, A, B, M)                                                                 \
+    if (sizeof(T) == 8 && c->tile_x == A && c->tile_y == B && minb_of(c) == M) \
+        return launch_one<double, A, B, M>(c, a, macro);
+        LBM_STEP_VARIANTS(X)
+#undef X
     }
     return cudaErrorInvalidValue;
 }

@@ -30,7 +30,7 @@ class LbmError(RuntimeError):
 class lbm_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32),
                 ("eos", C.c_int32), ("collision", C.c_int32), ("device", C.c_int32),
-                ("tile_x", C.c_int32), ("tile_y", C.c_int32),
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("min_blocks", C.c_int32),
                 ("Tr", C.c_double), ("k2", C.c_double), ("kappa", C.c_double),
                 ("tau", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double),
                 ("s_q", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
@@ -58,7 +58,7 @@ class lbm_info(C.Structure):
     _fields_ = [("rho_g", C.c_double), ("rho_l", C.c_double), ("p_sat", C.c_double),
                 ("mu_sat", C.c_double), ("T", C.c_double), ("steps", C.c_int64),
                 ("n_fluid", C.c_int64), ("tile_x", C.c_int32), ("tile_y", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("min_blocks", C.c_int32)]
 
 
 _sig = None
@@ -228,11 +228,12 @@ class Lattice:
 
     def __init__(self, nx, ny, *, eos=LBM_EOS_PR, Tr=0.7, k2=0.1, kappa=0.0126, tau=1.0,
                  s_e=1.64, s_eps=1.54, s_q=1.9, gx=0.0, gy=0.0, rho_g=0.0, rho_l=0.0,
-                 precision=LBM_FP32, collision=LBM_MRT, device=0, tile=(0, 0), stream=None):
+                 precision=LBM_FP32, collision=LBM_MRT, device=0, tile=(0, 0), min_blocks=0,
+                 stream=None):
         handle = getattr(stream, "cuda_stream", stream)
-        self.params = lbm_params(nx, ny, precision, eos, collision, device, tile[0], tile[1], Tr,
-                                 k2, kappa, tau, s_e, s_eps, s_q, gx, gy, rho_g, rho_l,
-                                 C.c_void_p(handle) if handle else None)
+        self.params = lbm_params(nx, ny, precision, eos, collision, device, tile[0], tile[1],
+                                 min_blocks, Tr, k2, kappa, tau, s_e, s_eps, s_q, gx, gy, rho_g,
+                                 rho_l, C.c_void_p(handle) if handle else None)
         self.nx, self.ny = nx, ny
         self.ctx = lbm_create(self.params)
 

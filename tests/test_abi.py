@@ -51,8 +51,8 @@ def test_coexistence_rejects_supercritical():
 def test_create_validates_arguments():
     """Argument errors are reported before any device work, with a message."""
     from paper_2202_06516_gb300 import lbm
-    p = lbm.lbm_params(4, 64, 0, 0, 0, 0, 0, 0, 0.7, 0.1, 0.0126, 1.0, 1.64, 1.54, 1.9, 0, 0, 0,
-                       0, None)
+    p = lbm.lbm_params(4, 64, 0, 0, 0, 0, 0, 0, 0, 0.7, 0.1, 0.0126, 1.0, 1.64, 1.54, 1.9, 0, 0,
+                       0, 0, None)
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(p)
     assert e.value.status == lbm.LBM_ERR_ARG
