@@ -298,6 +298,56 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_batched(args):
+    """256-instance sweep (domains 128..768 x 128..512, R 20..200, r 15..90, target angle 30..150
+    degrees): all instances advance together in the persistent batched kernel; value = all
+    instances' node updates per second over args.steps steps (no early exit in the timed run),
+    then a convergence run (residual < 1e-6 per 500 steps or 40k steps) reports steps and
+    angles per instance."""
+    import torch
+    from paper_2202_06516_gb300 import lbm, workloads as W
+    ws = W.batched(args.instances, seed=0)
+    m = ws[0].model
+    co = lbm.lbm_coexistence(m["eos"], m["Tr"])
+    neutral = m["k2"] * co["mu_sat"]
+    b = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
+                  kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"])
+    for i, w in enumerate(ws):
+        b.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+                       mu_bottom=neutral, mu_top=neutral, drop=w.drop)
+    nodes = sum(w.nx * w.ny for w in ws)
+    b.run(max(4, args.warmup // 2 * 2), check_every=max(2, args.warmup // 2 * 2), tol=0.0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    steps, conv, res = b.run(args.steps, check_every=500, tol=0.0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    line = {"metric": "MLUPS", "value": nodes * args.steps / dt / 1e6, "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched-{args.instances}-instances", "total_nodes": nodes,
+                       "timing": "host wall clock around the synchronous batch run"}}
+    if args.converge:
+        b2 = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
+                       kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"],
+                       s_q=m["s_q"])
+        for i, w in enumerate(ws):
+            b2.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+                            mu_bottom=neutral, mu_top=neutral, drop=w.drop)
+        t = time.perf_counter()
+        steps, conv, res = b2.run(40000, check_every=500, tol=1e-6)
+        dt2 = time.perf_counter() - t
+        ang = b2.measure()
+        line["converge"] = {"seconds": dt2, "converged": int(conv.sum()),
+                            "steps_mean": float(steps.mean()), "steps_max": int(steps.max()),
+                            "angles_ok": int(sum(a[0].status == 0 and a[1].status == 0
+                                                 for a in ang))}
+        b2.close()
+    b.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,6 +358,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--converge", action="store_true")
     ap.add_argument("--min-blocks", type=int, default=0,
                     help="step-kernel CTAs per SM to fit registers to (0: none)")
     args = ap.parse_args()
@@ -330,6 +383,10 @@ def main():
     from paper_2202_06516_gb300 import _native
     if rank == 0:
         _native.build()
+    if args.workload == "batched":
+        if rank == 0:
+            print(json.dumps(run_batched(args)), flush=True)
+        return
     if dist:
         dist.barrier()
     line = run_cuda(args, rank, world, dist)

@@ -195,6 +195,40 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 lbm_status lbm_mass_noalloc(const float *rho, const uint8_t *flags, int32_t nx, int32_t ny,
                             int32_t pitch, double rho_m, double *out, void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched sweeps: independent lattices of uneven size (drop radius, cylinder curvature and
+ * wettability sweeps, Sec. 4.1-4.2) advanced together by one persistent kernel over a device
+ * table of (instance, tile) pairs, replayed from a CUDA graph, with per-instance convergence.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque; owns n lattices, their stream and tile tables */
+
+/* Create n lattices of sizes nx[i] x ny[i] sharing the model parameters (model->nx, ny, tile_x,
+ * tile_y, min_blocks and stream are ignored; precision must be LBM_FP32). Every instance is an
+ * lbm_ctx on the batch's private stream. On failure *out is NULL and nothing is leaked. */
+lbm_status lbm_batch_create(const lbm_params *model, int32_t n, const int32_t *nx,
+                            const int32_t *ny, lbm_batch **out);
+
+/* Geometry and initial state of instance i (as lbm_set_geometry); marks it runnable. */
+lbm_status lbm_batch_set_geometry(lbm_batch *b, int32_t i, const lbm_geometry *g);
+
+/* Advance every runnable instance, check_every steps per graph replay (even, >= 2), until its
+ * residual sum|rho(t) - rho(t - check_every)| / sum rho over fluid nodes (FP64, deterministic)
+ * falls below tol or max_steps have been taken; converged or unstable instances leave the tile
+ * table at the check. Outputs (each n entries, may be NULL): steps taken, converged flag, last
+ * residual (-1 if never checked). Synchronous. */
+lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int32_t check_every, double tol,
+                         int64_t *steps_out, int32_t *converged_out, double *residual_out);
+
+/* Contact angles of every instance (out[2 i], out[2 i + 1] = left, right), as
+ * lbm_measure_contact_angle. Returns LBM_ERR_NO_CONTACT if any side of any instance failed. */
+lbm_status lbm_batch_measure(lbm_batch *b, lbm_angle *out);
+
+/* Borrow the context of instance i (read fields, mass, geometry); owned by the batch. */
+lbm_status lbm_batch_instance(lbm_batch *b, int32_t i, lbm_ctx **ctx);
+
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Wait for the context's stream. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
 

@@ -1,0 +1,475 @@
+// Batched sweep: many independent lattices of uneven size advanced together (the parameter
+// sweeps over drop radius, cylinder curvature and wettability of Sec. 4.1-4.2).
+//
+// Every instance is an ordinary lbm_ctx (its own planes, geometry and measurement scratch, all
+// on the batch's stream). A device tile table lists (instance, tile) pairs of the instances still
+// running; one persistent kernel, one CTA per resident slot, walks the table and advances each
+// tile one time step with the same device code as the single-lattice kernel. A CUDA graph holds
+// `check_every` such launches. After each graph the FP64 residual sum |rho(t) - rho(t - check)| /
+// sum rho of every running instance is computed (one block per instance, fixed order), converged
+// instances leave the table, and the graph is replayed on the shorter table without recapture
+// (the kernels read the table length from device memory).
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "lbm_step_body.cuh"
+
+namespace lbm {
+void set_global_error(const std::string& msg);
+}
+
+struct lbm_batch {
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<lbm_ctx*> inst;
+    std::vector<int> cur;         // buffer parity of each instance
+    std::vector<int64_t> steps;   // steps taken by each instance
+    std::vector<int> running;     // 1 while the instance is in the tile table
+    std::vector<int> has_geom;
+    void* d_desc = nullptr;       // BatchInst[n]
+    int2* d_tiles = nullptr;      // (instance, tile index)
+    int* d_ntiles = nullptr;
+    int* d_active = nullptr;      // running instance ids (residual kernel)
+    double* d_res = nullptr;      // per instance: residual sum, mass
+    float* snap = nullptr;        // one density snapshot plane per instance
+    std::vector<size_t> snap_off;
+    int max_tiles = 0;
+    int grid = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    int graph_parity = -1;
+    lbm::StepArgs<float> model{};
+    std::string err;
+};
+
+namespace lbm {
+namespace {
+
+using namespace stepdev;
+
+constexpr int TXB = 32, TYB = 16, NTB = 256, MINBB = 5;
+
+struct BatchInst {
+    float* h[2];
+    float* rho[2];
+    const uint8_t* flags;
+    const float* muw;
+    float* snap;
+    int nx, ny, P, plane, tiles_x;
+    float rho_mid;
+};
+
+__global__ void __launch_bounds__(NTB, MINBB)
+    k_batch_step(const StepArgs<float> model, const BatchInst* inst, const int2* tiles,
+                 const int* n_tiles, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nt = *n_tiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 e = tiles[t];
+        const BatchInst& I = inst[e.x];
+        StepArgs<float> a = model;
+        a.h_in = I.h[parity];
+        a.h_out = I.h[parity ^ 1];
+        a.rho_in = I.rho[parity];
+        a.rho_out = I.rho[parity ^ 1];
+        a.flags = I.flags;
+        a.muw = I.muw;
+        a.nx = I.nx;
+        a.ny = I.ny;
+        a.P = I.P;
+        a.plane = I.plane;
+        const int ty = e.y / I.tiles_x, tx = e.y - ty * I.tiles_x;
+        step_tile<float, TXB, TYB, NTB, false>(a, I.rho_mid, smem_raw, tx * TXB, ty * TYB);
+        __syncthreads();  // the next tile reuses shared memory
+    }
+}
+
+// One block per running instance: sum |rho - snapshot| and sum rho over fluid nodes in a fixed
+// order, then refresh the snapshot. res[2 i] = sum |drho|, res[2 i + 1] = sum rho.
+__global__ void k_batch_residual(const BatchInst* inst, const int* active, int parity, double* res,
+                                 int refresh) {
+    const int id = active[blockIdx.x];
+    const BatchInst& I = inst[id];
+    const float* rho = I.rho[parity];
+    double dsum = 0, msum = 0;
+    const int n = I.nx * I.ny;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int j = k / I.nx, i = k - j * I.nx;
+        const int o = lidx(I.P, i, j);
+        if (I.flags[o] != kFluid) continue;
+        const float r = rho[o];
+        dsum += fabs((double)r - (double)I.snap[o]);
+        msum += (double)r;
+        if (refresh) I.snap[o] = r;
+    }
+    __shared__ double s[2][NTB / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+        msum += __shfl_down_sync(0xffffffffu, msum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s[0][threadIdx.x >> 5] = dsum;
+        s[1][threadIdx.x >> 5] = msum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += s[0][w];
+            b += s[1][w];
+        }
+        res[2 * id] = a;
+        res[2 * id + 1] = b;
+    }
+}
+
+lbm_status bfail(lbm_batch* b, lbm_status st, const std::string& msg) {
+    if (b)
+        b->err = msg;
+    else
+        set_global_error(msg);
+    return st;
+}
+
+#define BCUDA(b, expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail((b), LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int tiles_of(const lbm_ctx* c) { return ((c->nx + TXB - 1) / TXB) * ((c->ny + TYB - 1) / TYB); }
+
+lbm_status upload_desc(lbm_batch* b) {
+    std::vector<BatchInst> d(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        lbm_ctx* c = b->inst[i];
+        BatchInst& I = d[i];
+        I.h[0] = (float*)c->h[0];
+        I.h[1] = (float*)c->h[1];
+        I.rho[0] = (float*)c->rho[0];
+        I.rho[1] = (float*)c->rho[1];
+        I.flags = c->flags;
+        I.muw = (const float*)c->muw;
+        I.snap = b->snap + b->snap_off[i];
+        I.nx = c->nx;
+        I.ny = c->ny;
+        I.P = c->P;
+        I.plane = (int)c->plane;
+        I.tiles_x = (c->nx + TXB - 1) / TXB;
+        I.rho_mid = (float)(0.5 * (c->rho_g + c->rho_l));
+    }
+    BCUDA(b, cudaMemcpyAsync(b->d_desc, d.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice,
+                             b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+// tile table of the running instances that share parity p; returns the number of tiles
+lbm_status upload_tiles(lbm_batch* b, int p, int* ntiles, std::vector<int>* act) {
+    std::vector<int2> t;
+    act->clear();
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->running[i] || b->cur[i] != p) continue;
+        act->push_back(i);
+        const int k = tiles_of(b->inst[i]);
+        for (int q = 0; q < k; ++q) t.push_back(make_int2(i, q));
+    }
+    *ntiles = (int)t.size();
+    if (!t.empty())
+        BCUDA(b, cudaMemcpyAsync(b->d_tiles, t.data(), sizeof(int2) * t.size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+    BCUDA(b, cudaMemcpyAsync(b->d_ntiles, ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    if (!act->empty())
+        BCUDA(b, cudaMemcpyAsync(b->d_active, act->data(), sizeof(int) * act->size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+    // the pageable sources must stay valid until the copies ran
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+cudaError_t launch_batch_step(lbm_batch* b, int parity) {
+    k_batch_step<<<b->grid, NTB, Layout<float, TXB, TYB>::bytes, b->stream>>>(
+        b->model, (const BatchInst*)b->d_desc, b->d_tiles, b->d_ntiles, parity);
+    return cudaGetLastError();
+}
+
+lbm_status capture(lbm_batch* b, int chunk, int parity) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_OK;  // plain launches
+    }
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < chunk; ++s) {
+        cudaError_t e = launch_batch_step(b, parity ^ (s & 1));
+        if (e != cudaSuccess && le == cudaSuccess) le = e;
+    }
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (le != cudaSuccess || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LBM_OK;
+    }
+    if (cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+    }
+    cudaGraphDestroy(g);
+    b->graph_chunk = chunk;
+    b->graph_parity = parity;
+    return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+lbm_status lbm_batch_create(const lbm_params* model, int32_t n, const int32_t* nx,
+                            const int32_t* ny, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_create: out is NULL");
+    *out = nullptr;
+    if (!model || !nx || !ny || n <= 0)
+        return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_create: need model, n > 0, nx[], ny[]");
+    if (model->precision != LBM_FP32)
+        return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_create: batches run in LBM_FP32");
+    lbm_batch* b = new lbm_batch();
+    b->n = n;
+    auto cleanup = [&](lbm_status st, const std::string& msg) {
+        for (lbm_ctx* c : b->inst) lbm_destroy(c);
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        cudaFree(b->d_desc);
+        cudaFree(b->d_tiles);
+        cudaFree(b->d_ntiles);
+        cudaFree(b->d_active);
+        cudaFree(b->d_res);
+        cudaFree(b->snap);
+        if (b->stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return bfail(nullptr, st, msg);
+    };
+    int dev = model->device;
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bfail(nullptr, LBM_ERR_CUDA, "lbm_batch_create: cannot select the device");
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(LBM_ERR_CUDA, "lbm_batch_create: stream");
+    size_t snap_total = 0;
+    for (int i = 0; i < n; ++i) {
+        lbm_params p = *model;
+        p.nx = nx[i];
+        p.ny = ny[i];
+        p.tile_x = TXB;
+        p.tile_y = TYB;
+        p.min_blocks = MINBB;
+        p.stream = b->stream;
+        lbm_ctx* c = nullptr;
+        lbm_status st = lbm_create(&p, &c);
+        if (st != LBM_OK)
+            return cleanup(st, std::string("lbm_batch_create: instance ") + std::to_string(i) +
+                                   ": " + lbm_last_error(nullptr));
+        b->inst.push_back(c);
+        b->snap_off.push_back(snap_total);
+        snap_total += c->plane;
+        b->max_tiles += tiles_of(c);
+    }
+    b->cur.assign(n, 0);
+    b->steps.assign(n, 0);
+    b->running.assign(n, 0);
+    b->has_geom.assign(n, 0);
+    e = cudaMalloc(&b->d_desc, sizeof(BatchInst) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int2) * b->max_tiles);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ntiles, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_active, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_res, sizeof(double) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->snap, sizeof(float) * snap_total);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->snap, 0, sizeof(float) * snap_total, b->stream);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Layout<float, TXB, TYB>::bytes);
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step, NTB,
+                                                          Layout<float, TXB, TYB>::bytes);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return cleanup(LBM_ERR_CUDA, std::string("lbm_batch_create: ") + cudaGetErrorString(e));
+    b->grid = (per_sm > 0 ? per_sm : 1) * sms;
+    // model part of the step arguments (per-instance fields are filled in the kernel)
+    lbm_ctx* c0 = b->inst[0];
+    StepArgs<float>& a = b->model;
+    a.k2 = (float)c0->p.k2;
+    a.kappa = (float)c0->p.kappa;
+    a.gx = (float)c0->p.gx;
+    a.gy = (float)c0->p.gy;
+    a.s_e = (float)c0->p.s_e;
+    a.s_eps = (float)c0->p.s_eps;
+    a.s_q = (float)c0->p.s_q;
+    a.s_v = (float)(1.0 / c0->p.tau);
+    a.inv_tau = (float)(1.0 / c0->p.tau);
+    a.bgk = c0->p.collision == LBM_BGK;
+    a.eos = c0->eosc.eos;
+    a.RT = (float)c0->eosc.RT;
+    a.aal = (float)c0->eosc.aal;
+    a.b = (float)c0->eosc.b;
+    lbm_status st = upload_desc(b);
+    if (st != LBM_OK) return cleanup(st, b->err);
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_geometry(lbm_batch* b, int32_t i, const lbm_geometry* g) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_set_geometry: batch is NULL");
+    if (i < 0 || i >= b->n) return bfail(b, LBM_ERR_ARG, "lbm_batch_set_geometry: bad index");
+    lbm_status st = lbm_set_geometry(b->inst[i], g);
+    if (st != LBM_OK) return bfail(b, st, lbm_last_error(b->inst[i]));
+    b->cur[i] = 0;
+    b->steps[i] = 0;
+    b->has_geom[i] = 1;
+    b->running[i] = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, double tol,
+                         int64_t* steps_out, int32_t* converged_out, double* residual_out) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_run: batch is NULL");
+    if (max_steps < 0 || check_every < 2 || (check_every & 1))
+        return bfail(b, LBM_ERR_ARG, "lbm_batch_run: need max_steps >= 0 and an even check_every >= 2");
+    BCUDA(b, cudaSetDevice(b->inst[0]->device));
+    std::vector<int> conv(b->n, 0);
+    std::vector<double> resid(b->n, -1.0);
+    // every instance with geometry starts at parity 0 (set_geometry) or where it stopped
+    for (int i = 0; i < b->n; ++i) b->running[i] = b->has_geom[i];
+    std::vector<int> act;
+    int ntiles = 0;
+    int64_t done = 0;
+    // the running set must share one parity; group by the parity of the first running instance
+    int parity = -1;
+    for (int i = 0; i < b->n; ++i)
+        if (b->running[i]) {
+            if (parity < 0) parity = b->cur[i];
+            if (b->cur[i] != parity) b->running[i] = 0;  // run them in a later call
+        }
+    if (parity < 0) parity = 0;
+    lbm_status st = upload_tiles(b, parity, &ntiles, &act);
+    if (st != LBM_OK) return st;
+    if (!act.empty()) {
+        k_batch_residual<<<(int)act.size(), NTB, 0, b->stream>>>((const BatchInst*)b->d_desc,
+                                                                 b->d_active, parity, b->d_res, 1);
+        BCUDA(b, cudaGetLastError());
+    }
+    while (done < max_steps && !act.empty()) {
+        const int chunk = (int)std::min<int64_t>(check_every, max_steps - done);
+        if (chunk == check_every) {
+            if (!b->graph || b->graph_chunk != chunk || b->graph_parity != parity)
+                capture(b, chunk, parity);
+            if (b->graph) {
+                BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+            } else {
+                for (int s = 0; s < chunk; ++s) BCUDA(b, launch_batch_step(b, parity ^ (s & 1)));
+            }
+        } else {
+            for (int s = 0; s < chunk; ++s) BCUDA(b, launch_batch_step(b, parity ^ (s & 1)));
+        }
+        parity ^= (chunk & 1);
+        done += chunk;
+        for (int i : act) {
+            b->steps[i] += chunk;
+            b->cur[i] = parity;
+        }
+        k_batch_residual<<<(int)act.size(), NTB, 0, b->stream>>>((const BatchInst*)b->d_desc,
+                                                                 b->d_active, parity, b->d_res, 1);
+        BCUDA(b, cudaGetLastError());
+        std::vector<double> res(2 * b->n);
+        BCUDA(b, cudaMemcpyAsync(res.data(), b->d_res, sizeof(double) * 2 * b->n,
+                                 cudaMemcpyDeviceToHost, b->stream));
+        BCUDA(b, cudaStreamSynchronize(b->stream));
+        bool changed = false;
+        for (int i : act) {
+            const double r = res[2 * i + 1] > 0 ? res[2 * i] / res[2 * i + 1] : 0.0;
+            resid[i] = r;
+            if (!(res[2 * i + 1] > 0) || !std::isfinite(res[2 * i + 1])) {
+                b->running[i] = 0;  // unstable: stop it, report not converged
+                changed = true;
+            } else if (r < tol) {
+                conv[i] = 1;
+                b->running[i] = 0;
+                changed = true;
+            }
+        }
+        if (changed) {
+            st = upload_tiles(b, parity, &ntiles, &act);
+            if (st != LBM_OK) return st;
+        }
+    }
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        b->inst[i]->cur = b->cur[i];
+        b->inst[i]->steps = b->steps[i];
+        if (steps_out) steps_out[i] = b->steps[i];
+        if (converged_out) converged_out[i] = conv[i];
+        if (residual_out) residual_out[i] = resid[i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_measure(lbm_batch* b, lbm_angle* out) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_measure: batch is NULL");
+    if (!out) return bfail(b, LBM_ERR_ARG, "lbm_batch_measure: out is NULL");
+    lbm_status worst = LBM_OK;
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->has_geom[i]) {
+            out[2 * i].status = out[2 * i + 1].status = LBM_ERR_STATE;
+            continue;
+        }
+        b->inst[i]->cur = b->cur[i];
+        lbm_status st = lbm_measure_contact_angle(b->inst[i], &out[2 * i]);
+        if (st == LBM_ERR_NO_CONTACT) {
+            worst = LBM_ERR_NO_CONTACT;
+        } else if (st != LBM_OK) {
+            return bfail(b, st, lbm_last_error(b->inst[i]));
+        }
+    }
+    return worst;
+}
+
+lbm_status lbm_batch_instance(lbm_batch* b, int32_t i, lbm_ctx** ctx) {
+    if (!b || !ctx) return bfail(b, LBM_ERR_ARG, "lbm_batch_instance: NULL argument");
+    if (i < 0 || i >= b->n) return bfail(b, LBM_ERR_ARG, "lbm_batch_instance: bad index");
+    b->inst[i]->cur = b->cur[i];
+    b->inst[i]->steps = b->steps[i];
+    *ctx = b->inst[i];
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) {
+    return b ? b->err.c_str() : lbm_last_error(nullptr);
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (lbm_ctx* c : b->inst) lbm_destroy(c);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_ntiles);
+    cudaFree(b->d_active);
+    cudaFree(b->d_res);
+    cudaFree(b->snap);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -85,6 +85,20 @@ def lib() -> C.CDLL:
         L.lbm_destroy.restype = None
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = C.c_char_p
+        L.lbm_batch_create.argtypes = [C.POINTER(lbm_params), C.c_int32, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), C.POINTER(vp)]
+        L.lbm_batch_set_geometry.argtypes = [vp, C.c_int32, C.POINTER(lbm_geometry)]
+        L.lbm_batch_run.argtypes = [vp, C.c_int64, C.c_int32, C.c_double, i64p,
+                                    C.POINTER(C.c_int32), dp]
+        L.lbm_batch_measure.argtypes = [vp, C.POINTER(lbm_angle)]
+        L.lbm_batch_instance.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+        L.lbm_batch_last_error.argtypes = [vp]
+        L.lbm_batch_last_error.restype = C.c_char_p
+        L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_batch_destroy.restype = None
+        for n in ("lbm_batch_create", "lbm_batch_set_geometry", "lbm_batch_run",
+                  "lbm_batch_measure", "lbm_batch_instance"):
+            getattr(L, n).restype = C.c_int
         for n in ("lbm_coexistence", "lbm_create", "lbm_set_geometry", "lbm_step",
                   "lbm_measure_contact_angle", "lbm_read_fields", "lbm_mass", "lbm_read_geometry",
                   "lbm_read_candidates", "lbm_get_info", "lbm_synchronize"):
@@ -290,3 +304,109 @@ class Lattice:
 
     def info(self):
         return lbm_get_info(self.ctx)
+
+
+# ------------------------------------------------------------------------------ batched sweeps
+def _bcheck(status, b=None, allow=()):
+    if status != LBM_OK and status not in allow:
+        raise LbmError(status, lib().lbm_batch_last_error(b).decode())
+    return status
+
+
+def lbm_batch_create(params: lbm_params, nx, ny):
+    n = len(nx)
+    a = (C.c_int32 * n)(*[int(v) for v in nx])
+    b = (C.c_int32 * n)(*[int(v) for v in ny])
+    out = C.c_void_p()
+    _bcheck(lib().lbm_batch_create(C.byref(params), n, a, b, C.byref(out)))
+    return out
+
+
+def lbm_batch_set_geometry(b, i: int, geom: lbm_geometry, rho0=None):
+    keep = None
+    if rho0 is not None:
+        keep = np.ascontiguousarray(rho0, dtype=np.float64)
+        geom.rho0 = _dp(keep)
+    else:
+        geom.rho0 = None
+    _bcheck(lib().lbm_batch_set_geometry(b, int(i), C.byref(geom)), b)
+
+
+def lbm_batch_run(b, n: int, max_steps: int, check_every: int, tol: float):
+    steps = np.zeros(n, dtype=np.int64)
+    conv = np.zeros(n, dtype=np.int32)
+    res = np.zeros(n)
+    _bcheck(lib().lbm_batch_run(b, int(max_steps), int(check_every), float(tol),
+                                steps.ctypes.data_as(C.POINTER(C.c_int64)),
+                                conv.ctypes.data_as(C.POINTER(C.c_int32)), _dp(res)), b)
+    return steps, conv, res
+
+
+def lbm_batch_measure(b, n: int):
+    out = (lbm_angle * (2 * n))()
+    st = _bcheck(lib().lbm_batch_measure(b, out), b, allow=(LBM_ERR_NO_CONTACT,))
+    return st, [(_angle(out[2 * i]), _angle(out[2 * i + 1])) for i in range(n)]
+
+
+def lbm_batch_instance(b, i: int):
+    ctx = C.c_void_p()
+    _bcheck(lib().lbm_batch_instance(b, int(i), C.byref(ctx)), b)
+    return ctx
+
+
+def lbm_batch_destroy(b):
+    if b:
+        lib().lbm_batch_destroy(b)
+
+
+class Batch:
+    """n independent lattices advanced together (FP32), model parameters shared."""
+
+    def __init__(self, sizes, *, eos=LBM_EOS_PR, Tr=0.7, k2=0.1, kappa=0.0126, tau=1.0,
+                 s_e=1.64, s_eps=1.54, s_q=1.9, gx=0.0, gy=0.0, rho_g=0.0, rho_l=0.0,
+                 collision=LBM_MRT, device=0):
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        self.n = len(self.sizes)
+        self.params = lbm_params(0, 0, LBM_FP32, eos, collision, device, 0, 0, 0, Tr, k2, kappa,
+                                 tau, s_e, s_eps, s_q, gx, gy, rho_g, rho_l, None)
+        self.b = lbm_batch_create(self.params, [s[0] for s in self.sizes],
+                                  [s[1] for s in self.sizes])
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, i, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
+                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None):
+        g = lbm_geometry()
+        if circle is not None:
+            g.has_circle = 1
+            g.cx, g.cy, g.R = circle
+        g.mu_circle = mu_circle
+        if stripes is not None:
+            g.stripes = 1
+            g.stripe_arc, g.mu_stripe_b = stripes
+        g.mu_bottom, g.mu_top = mu_bottom, mu_top
+        g.drop_x, g.drop_y, g.drop_r, g.drop_W = drop
+        lbm_batch_set_geometry(self.b, i, g, rho0)
+
+    def run(self, max_steps, check_every=500, tol=1e-6):
+        return lbm_batch_run(self.b, self.n, max_steps, check_every, tol)
+
+    def measure(self):
+        return lbm_batch_measure(self.b, self.n)[1]
+
+    def rho(self, i):
+        ctx = lbm_batch_instance(self.b, i)
+        nx, ny = self.sizes[i]
+        return lbm_read_fields(ctx, LBM_FIELD_RHO, nx, ny)[0]
+
+    def mass(self, i):
+        return lbm_mass(lbm_batch_instance(self.b, i))[1]

@@ -94,3 +94,17 @@ def test_maxwell_regression(oracle_mod):
         m = oracle_mod.maxwell(row["eos"], row["Tr"])
         for k in ("rho_g", "rho_l", "p_sat", "mu_sat"):
             assert m[k] == pytest.approx(row[k], rel=1e-10)
+
+
+def test_batched_workload_generator():
+    """Seeded sweep members respect the drawn ranges and the rejection rule (2R + 16 <= nx,
+    R + 2r + 8 <= ny), and are reproducible."""
+    from paper_2202_06516_gb300 import workloads as W
+    a = W.batched(64, seed=3)
+    b = W.batched(64, seed=3)
+    assert [w.as_dict() for w in a] == [w.as_dict() for w in b]
+    for w in a:
+        R, r = w.circle[2], w.drop[2]
+        assert 128 <= w.nx <= 768 and 128 <= w.ny <= 512
+        assert 20 <= R <= 200 and 15 <= r <= 90
+        assert 2 * R + 16 <= w.nx and R + 2 * r + 8 <= w.ny
