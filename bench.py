@@ -336,7 +336,7 @@ def run_batched(args):
             b2.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
                             mu_bottom=neutral, mu_top=neutral, drop=w.drop)
         t = time.perf_counter()
-        steps, conv, res = b2.run(40000, check_every=500, tol=1e-6)
+        steps, conv, res = b2.run(40000, check_every=500, tol=1e-6, angle_tol=0.05)
         dt2 = time.perf_counter() - t
         ang = b2.measure()
         line["converge"] = {"seconds": dt2, "converged": int(conv.sum()),

@@ -211,13 +211,16 @@ lbm_status lbm_batch_create(const lbm_params *model, int32_t n, const int32_t *n
 /* Geometry and initial state of instance i (as lbm_set_geometry); marks it runnable. */
 lbm_status lbm_batch_set_geometry(lbm_batch *b, int32_t i, const lbm_geometry *g);
 
-/* Advance every runnable instance, check_every steps per graph replay (even, >= 2), until its
- * residual sum|rho(t) - rho(t - check_every)| / sum rho over fluid nodes (FP64, deterministic)
- * falls below tol or max_steps have been taken; converged or unstable instances leave the tile
- * table at the check. Outputs (each n entries, may be NULL): steps taken, converged flag, last
- * residual (-1 if never checked). Synchronous. */
+/* Advance every runnable instance, check_every steps per graph replay (even, >= 2), until it
+ * converges or max_steps have been taken. Converged at a check: the residual
+ * sum|rho(t) - rho(t - check_every)| / sum rho over fluid nodes (FP64, deterministic) is below
+ * tol, or (angle_tol > 0) both contact angles (Sec. 3.2 measurement) moved by at most angle_tol
+ * degrees since the previous check at two consecutive checks. Converged or unstable instances
+ * leave the tile table at the check. Outputs (each n entries, may be NULL): steps taken,
+ * converged flag, last residual (-1 if never checked). Synchronous. */
 lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int32_t check_every, double tol,
-                         int64_t *steps_out, int32_t *converged_out, double *residual_out);
+                         double angle_tol, int64_t *steps_out, int32_t *converged_out,
+                         double *residual_out);
 
 /* Contact angles of every instance (out[2 i], out[2 i + 1] = left, right), as
  * lbm_measure_contact_angle. Returns LBM_ERR_NO_CONTACT if any side of any instance failed. */

@@ -342,13 +342,16 @@ lbm_status lbm_batch_set_geometry(lbm_batch* b, int32_t i, const lbm_geometry* g
 }
 
 lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, double tol,
-                         int64_t* steps_out, int32_t* converged_out, double* residual_out) {
+                         double angle_tol, int64_t* steps_out, int32_t* converged_out,
+                         double* residual_out) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_run: batch is NULL");
     if (max_steps < 0 || check_every < 2 || (check_every & 1))
         return bfail(b, LBM_ERR_ARG, "lbm_batch_run: need max_steps >= 0 and an even check_every >= 2");
     BCUDA(b, cudaSetDevice(b->inst[0]->device));
     std::vector<int> conv(b->n, 0);
     std::vector<double> resid(b->n, -1.0);
+    std::vector<double> last_theta(2 * b->n, -1.0);
+    std::vector<int> stable(b->n, 0);
     // every instance with geometry starts at parity 0 (set_geometry) or where it stopped
     for (int i = 0; i < b->n; ++i) b->running[i] = b->has_geom[i];
     std::vector<int> act;
@@ -402,7 +405,32 @@ lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, d
             if (!(res[2 * i + 1] > 0) || !std::isfinite(res[2 * i + 1])) {
                 b->running[i] = 0;  // unstable: stop it, report not converged
                 changed = true;
-            } else if (r < tol) {
+                continue;
+            }
+            bool done_i = r < tol;
+            if (!done_i && angle_tol > 0) {
+                // angle stationarity: both sides measured and within angle_tol of the previous
+                // check, twice in a row
+                lbm_ctx* c = b->inst[i];
+                c->cur = b->cur[i];
+                lbm_angle ang[2];
+                const lbm_status ms = lbm_measure_contact_angle(c, ang);
+                if (ms == LBM_OK) {
+                    const bool still = last_theta[2 * i] >= 0 &&
+                                       fabs(ang[0].theta_deg - last_theta[2 * i]) <= angle_tol &&
+                                       fabs(ang[1].theta_deg - last_theta[2 * i + 1]) <= angle_tol;
+                    stable[i] = still ? stable[i] + 1 : 0;
+                    last_theta[2 * i] = ang[0].theta_deg;
+                    last_theta[2 * i + 1] = ang[1].theta_deg;
+                    done_i = stable[i] >= 2;
+                } else if (ms == LBM_ERR_NO_CONTACT) {
+                    stable[i] = 0;
+                    last_theta[2 * i] = last_theta[2 * i + 1] = -1.0;
+                } else {
+                    return bfail(b, ms, lbm_last_error(c));
+                }
+            }
+            if (done_i) {
                 conv[i] = 1;
                 b->running[i] = 0;
                 changed = true;

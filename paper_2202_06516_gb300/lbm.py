@@ -88,7 +88,7 @@ def lib() -> C.CDLL:
         L.lbm_batch_create.argtypes = [C.POINTER(lbm_params), C.c_int32, C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32), C.POINTER(vp)]
         L.lbm_batch_set_geometry.argtypes = [vp, C.c_int32, C.POINTER(lbm_geometry)]
-        L.lbm_batch_run.argtypes = [vp, C.c_int64, C.c_int32, C.c_double, i64p,
+        L.lbm_batch_run.argtypes = [vp, C.c_int64, C.c_int32, C.c_double, C.c_double, i64p,
                                     C.POINTER(C.c_int32), dp]
         L.lbm_batch_measure.argtypes = [vp, C.POINTER(lbm_angle)]
         L.lbm_batch_instance.argtypes = [vp, C.c_int32, C.POINTER(vp)]
@@ -332,11 +332,11 @@ def lbm_batch_set_geometry(b, i: int, geom: lbm_geometry, rho0=None):
     _bcheck(lib().lbm_batch_set_geometry(b, int(i), C.byref(geom)), b)
 
 
-def lbm_batch_run(b, n: int, max_steps: int, check_every: int, tol: float):
+def lbm_batch_run(b, n: int, max_steps: int, check_every: int, tol: float, angle_tol=0.0):
     steps = np.zeros(n, dtype=np.int64)
     conv = np.zeros(n, dtype=np.int32)
     res = np.zeros(n)
-    _bcheck(lib().lbm_batch_run(b, int(max_steps), int(check_every), float(tol),
+    _bcheck(lib().lbm_batch_run(b, int(max_steps), int(check_every), float(tol), float(angle_tol),
                                 steps.ctypes.data_as(C.POINTER(C.c_int64)),
                                 conv.ctypes.data_as(C.POINTER(C.c_int32)), _dp(res)), b)
     return steps, conv, res
@@ -397,8 +397,8 @@ class Batch:
         g.drop_x, g.drop_y, g.drop_r, g.drop_W = drop
         lbm_batch_set_geometry(self.b, i, g, rho0)
 
-    def run(self, max_steps, check_every=500, tol=1e-6):
-        return lbm_batch_run(self.b, self.n, max_steps, check_every, tol)
+    def run(self, max_steps, check_every=500, tol=1e-6, angle_tol=0.0):
+        return lbm_batch_run(self.b, self.n, max_steps, check_every, tol, angle_tol)
 
     def measure(self):
         return lbm_batch_measure(self.b, self.n)[1]

@@ -96,3 +96,32 @@ def test_batch_mass_conserved(lbm, oracle_mod):
     for i in range(len(cfgs)):
         assert abs(b.mass(i)["mass"] - m0[i]) / m0[i] < 1e-5
     b.close()
+
+
+def test_batch_angle_convergence(lbm, oracle_mod):
+    """With an angle criterion an instance stops at the first check where both angles moved by
+    <= 0.05 degrees since the previous check, for the second check in a row. Replaying the same
+    instance alone and measuring at its last three checks shows exactly that, and its final
+    state equals the batch's. (The criterion is a stopping rule: a contact line pinned on the
+    staircase wall can hold still for two checks and move again later.)"""
+    cfgs = _cfgs(oracle_mod)
+    b = _batch(lbm, cfgs)
+    steps, conv, res = b.run(20000, check_every=500, tol=0.0, angle_tol=0.05)
+    assert conv.any()
+    ang = b.measure()
+    for i in np.nonzero(conv)[0]:
+        s = int(steps[i])
+        assert 1500 <= s < 20000 and s % 500 == 0
+        single = gpu_lattice(lbm, cfgs[i])
+        single.step(s - 1000)
+        t0 = single.measure()
+        single.step(500)
+        t1 = single.measure()
+        single.step(500)
+        t2 = single.measure()
+        for side in (0, 1):
+            assert abs(t1[side].theta - t0[side].theta) <= 0.05
+            assert abs(t2[side].theta - t1[side].theta) <= 0.05
+            assert t2[side].theta == ang[i][side].theta
+        assert np.array_equal(single.rho(), b.rho(i))
+    b.close()
