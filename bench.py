@@ -348,6 +348,54 @@ def run_batched(args):
     return line
 
 
+def unet_flops(H, Wd, base):
+    """Multiply-add FLOPs of one forward pass (2 per MAC) of the U-Net."""
+    from paper_2202_06516_gb300 import workloads as W
+    res = [1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 4, 2, 2, 2, 1, 1, 1]  # downsampling factor per conv
+    f = 0
+    for (ci, co), d in zip(W.unet_layers(base), res):
+        f += 2 * (H // d) * (Wd // d) * 9 * ci * co
+    return f + 2 * H * Wd * base
+
+
+def run_warmstart(args):
+    """Learned warm start (256 x 256 cases): generate equilibria with the batched solver, train
+    the BF16 U-Net with the library's kernels, compare steps to the +-0.5 degree equilibrated
+    angle for cold (Eq. 16 cap) and warm (prediction) starts on held-out seeds."""
+    from paper_2202_06516_gb300 import lbm, warmstart as WS, workloads as W
+    log = lambda msg: print(msg, file=sys.stderr, flush=True)
+    t0 = time.perf_counter()
+    tr = W.warm_cases(args.train_cases, seed=1)
+    ev = W.warm_cases(args.eval_cases, seed=10000)
+    x, t, m = WS.generate(tr, steps=args.gen_steps)
+    t_gen = time.perf_counter() - t0
+    log(f"generated {len(tr)} cases in {t_gen:.1f}s")
+    sur = lbm.Surrogate(256, 256, base=32, max_batch=args.batch)
+    sur.set_weights(W.unet_init(32, seed=0))
+    losses, t_train = WS.train(sur, x, t, m, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                               log=log)
+    steps_per_epoch = len(tr) // args.batch
+    flops = 3 * unet_flops(256, 256, 32) * args.batch * steps_per_epoch * args.epochs
+    rows, hc, hw = WS.evaluate(sur, ev, steps=args.gen_steps, every=250, log=log)
+    cold = [r[0] for r in rows if r[0] is not None and r[1] is not None]
+    warm = [r[1] for r in rows if r[0] is not None and r[1] is not None]
+    both = len(cold)
+    line = {"metric": "steps to +-0.5 deg equilibrated angle (median, held-out)",
+            "impl": "cuda", "workload": "warm-start-256x256", "data": "synthetic",
+            "train_cases": len(tr), "eval_cases": len(ev), "epochs": args.epochs,
+            "loss_first_last": [losses[0], losses[-1]], "gen_seconds": t_gen,
+            "train_seconds": t_train,
+            "train_tflops": flops / t_train / 1e12,
+            "eval_pairs": both,
+            "cold_median_steps": float(np.median(cold)) if both else None,
+            "warm_median_steps": float(np.median(warm)) if both else None,
+            "warm_faster_fraction": float(np.mean(np.array(warm) < np.array(cold))) if both else None,
+            "cold_unreached": sum(1 for r in rows if r[0] is None),
+            "warm_unreached": sum(1 for r in rows if r[0] is not None and r[1] is None)}
+    sur.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,7 +406,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "warmstart"])
+    ap.add_argument("--train-cases", type=int, default=1024)
+    ap.add_argument("--eval-cases", type=int, default=64)
+    ap.add_argument("--gen-steps", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--converge", action="store_true")
     ap.add_argument("--min-blocks", type=int, default=0,
@@ -386,6 +440,10 @@ def main():
     if args.workload == "batched":
         if rank == 0:
             print(json.dumps(run_batched(args)), flush=True)
+        return
+    if args.workload == "warmstart":
+        if rank == 0:
+            print(json.dumps(run_warmstart(args)), flush=True)
         return
     if dist:
         dist.barrier()

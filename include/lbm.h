@@ -232,6 +232,48 @@ lbm_status lbm_batch_instance(lbm_batch *b, int32_t i, lbm_ctx **ctx);
 const char *lbm_batch_last_error(const lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper; it replaces part of the relaxation from the
+ * Eq. 16 flat-cap start): a U-Net on an H x W lattice mapping (solid mask, wall-wetting map,
+ * drop-volume plane) to phi = (rho - rho_g) / (rho_l - rho_g), trained on solver-equilibrated
+ * fields. BF16 activations and weight copies, FP32 master weights, FP32 accumulation on tensor
+ * cores. Architecture: encoder levels with base, 2, 4, 8 x base channels (two 3x3 conv + ReLU
+ * each, 2x2 average pooling between), decoder levels of a 3x3 conv on the 2x nearest-upsampled
+ * coarser output and two 3x3 convs on [that | skip], 1x1 sigmoid head. Parameters: one FP32
+ * vector, per convolution in forward order weight [c_out][ky][kx][c_in] then bias [c_out], then
+ * head weight [base] and bias [1].
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_surrogate lbm_surrogate;
+
+/* H, W multiples of 8; base in {8, 16, 32}; buffers for up to max_batch samples. Weights start
+ * at zero: call lbm_surrogate_set_weights. */
+lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_batch,
+                                int32_t device, lbm_surrogate **out);
+int64_t lbm_surrogate_num_params(const lbm_surrogate *s);
+/* Copy FP32 master weights from the host (resets the Adam moments and step count). */
+lbm_status lbm_surrogate_set_weights(lbm_surrogate *s, const float *host, int64_t n);
+/* Copy the FP32 master weights (grads = 0) or the last step's gradients (grads = 1) to host. */
+lbm_status lbm_surrogate_get_weights(lbm_surrogate *s, float *host, int64_t n, int32_t grads);
+/* x: device BF16 inputs (B, H, W, 8) NHWC; phi_out: device FP32 (B, H, W). Synchronous. */
+lbm_status lbm_surrogate_forward(lbm_surrogate *s, const void *x, int32_t B, float *phi_out);
+/* Forward, loss = sum mask (phi - target)^2 / sum mask, backward into the gradient vector and,
+ * for lr > 0, one Adam step (beta 0.9 / 0.999, eps 1e-8). target: device FP32 (B, H, W); mask:
+ * device uint8 (B, H, W). *loss receives the loss. Synchronous. */
+lbm_status lbm_surrogate_train_step(lbm_surrogate *s, const void *x, const float *target,
+                                    const uint8_t *mask, int32_t B, float lr, double *loss);
+/* Copy the last training step's phi (B, H, W) to the host. */
+lbm_status lbm_surrogate_phi(lbm_surrogate *s, float *host_phi, int32_t B);
+const char *lbm_surrogate_last_error(const lbm_surrogate *s);
+void lbm_surrogate_destroy(lbm_surrogate *s);
+
+/* The surrogate's tensor-core GEMM on its own: C = A B, BF16 device operands, FP32 device
+ * output C[m * ldc + n]. a_kmajor: A stored A[m * lda + k] (else A[k * lda + m]); b_kmajor: B
+ * stored B[n * ldb + k] (else B[k * ldb + n]). K-major operands need K and ld multiples of 8,
+ * MN-major ones M (N) and ld multiples of 8. Asynchronous on stream. */
+lbm_status lbm_sg_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t K,
+                       int32_t a_kmajor, int32_t b_kmajor, int32_t lda, int32_t ldb, float *C,
+                       int32_t ldc, void *stream);
+
 /* Wait for the context's stream. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
 

@@ -1,0 +1,704 @@
+// Learned warm start: a convolutional U-Net that maps (solid mask, wall-wetting map, drop-volume
+// plane) on an H x W lattice to a near-equilibrium density field, trained on equilibrated fields
+// the solver generates. The paper has no such component; it shortens the plain relaxation from a
+// flat-cap start (Sec. 4, Eq. 16) that the solver otherwise performs.
+//
+// Network (levels l = 1..4, channels c_l = base * 2^(l-1)):
+//   encoder   conv3x3 + ReLU twice per level, 2x2 average pooling between levels
+//   decoder   2x upsampling folded into the next conv3x3 (nearest), the skip concatenation folded
+//             into the following conv3x3 (two-source im2col), conv3x3 + ReLU twice per level
+//   head      1x1 conv to one channel, sigmoid: phi = (rho - rho_g) / (rho_l - rho_g)
+// Activations BF16 NHWC, weights FP32 masters with BF16 copies, all contractions on tensor cores
+// through one BF16 GEMM with FP32 accumulation (sg_gemm.cuh) over im2col / col2im buffers.
+// Loss: masked mean squared error on phi. Optimiser: Adam.
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+#include "sg_gemm.cuh"
+
+namespace lbm {
+void set_global_error(const std::string& msg);
+}
+
+using bf16 = __nv_bfloat16;
+
+namespace lbm {
+namespace sg {
+namespace {
+
+constexpr int kT = 256;
+
+int blocks_for(long long n) {
+    long long b = (n + kT - 1) / kT;
+    return (int)(b > 65535LL * 8 ? 65535LL * 8 : (b < 1 ? 1 : b));
+}
+
+// im2col of a 3x3, pad-1 convolution whose input channels are [source 1 | source 2]:
+// col[p][(ky*3+kx)*C + c] = x(n, y+ky-1, x+kx-1, c). Source 1 may be stored at half resolution
+// (up1 = 1: nearest 2x upsampling on the fly). Eight channels per thread (16-byte accesses).
+__global__ void k_im2col(const bf16* x1, int C1, int up1, const bf16* x2, int C2, int B, int H,
+                         int W, bf16* col) {
+    const int C = C1 + C2, C8 = C / 8;
+    const long long total = (long long)B * H * W * 9 * C8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(t % C8);
+        const long long r = t / C8;
+        const int tap = (int)(r % 9);
+        const long long p = r / 9;
+        const int xx = (int)(p % W), yy = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+        const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (sy >= 0 && sy < H && sx >= 0 && sx < W) {
+            const int c = c8 * 8;
+            if (c < C1) {
+                const int h1 = up1 ? H / 2 : H, w1 = up1 ? W / 2 : W;
+                const int ty = up1 ? sy >> 1 : sy, tx = up1 ? sx >> 1 : sx;
+                v = *reinterpret_cast<const uint4*>(x1 + (((size_t)n * h1 + ty) * w1 + tx) * C1 + c);
+            } else {
+                v = *reinterpret_cast<const uint4*>(x2 + (((size_t)n * H + sy) * W + sx) * C2 +
+                                                    (c - C1));
+            }
+        }
+        *reinterpret_cast<uint4*>(col + (size_t)p * 9 * C + tap * C + c8 * 8) = v;
+    }
+}
+
+// col2im (adjoint of k_im2col) into FP32 gradients of the two sources; accumulates when asked.
+__global__ void k_col2im(const bf16* dcol, int C1, int up1, float* dx1, int acc1, int C2,
+                         float* dx2, int acc2, int B, int H, int W) {
+    const int C = C1 + C2;
+    // source 1 elements (possibly half resolution), then source 2 elements
+    const int h1 = up1 ? H / 2 : H, w1 = up1 ? W / 2 : W;
+    const long long n1 = (long long)B * h1 * w1 * C1, n2 = (long long)B * H * W * C2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n1 + n2;
+         t += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        if (t < n1) {
+            const int c = (int)(t % C1);
+            const long long q = t / C1;
+            const int X = (int)(q % w1), Y = (int)((q / w1) % h1), n = (int)(q / ((long long)w1 * h1));
+            const int f = up1 ? 2 : 1;
+            for (int dy = 0; dy < f; ++dy)
+                for (int dxo = 0; dxo < f; ++dxo) {
+                    const int yy = Y * f + dy, xx = X * f + dxo;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int py = yy - (tap / 3 - 1), px = xx - (tap % 3 - 1);
+                        if (py < 0 || py >= H || px < 0 || px >= W) continue;
+                        s += __bfloat162float(
+                            dcol[(((size_t)n * H + py) * W + px) * 9 * C + tap * C + c]);
+                    }
+                }
+            if (acc1)
+                dx1[t] += s;
+            else
+                dx1[t] = s;
+        } else {
+            const long long u = t - n1;
+            const int c = (int)(u % C2);
+            const long long q = u / C2;
+            const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((long long)W * H));
+            for (int tap = 0; tap < 9; ++tap) {
+                const int py = yy - (tap / 3 - 1), px = xx - (tap % 3 - 1);
+                if (py < 0 || py >= H || px < 0 || px >= W) continue;
+                s += __bfloat162float(
+                    dcol[(((size_t)n * H + py) * W + px) * 9 * C + tap * C + C1 + c]);
+            }
+            if (acc2)
+                dx2[u] += s;
+            else
+                dx2[u] = s;
+        }
+    }
+}
+
+__global__ void k_avgpool(const bf16* x, bf16* y, int B, int H, int W, int C) {
+    const int h = H / 2, w = W / 2;
+    const long long total = (long long)B * h * w * C;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t % C);
+        const long long q = t / C;
+        const int X = (int)(q % w), Y = (int)((q / w) % h), n = (int)(q / ((long long)w * h));
+        const size_t b = (((size_t)n * H + 2 * Y) * W + 2 * X) * C + c;
+        const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) +
+                        __bfloat162float(x[b + (size_t)W * C]) +
+                        __bfloat162float(x[b + (size_t)W * C + C]);
+        y[t] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// adjoint of k_avgpool, accumulated into the full-resolution gradient
+__global__ void k_avgpool_bwd(const float* dy, float* dx, int B, int H, int W, int C) {
+    const long long total = (long long)B * H * W * C;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t % C);
+        const long long q = t / C;
+        const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((long long)W * H));
+        dx[t] += 0.25f * dy[(((size_t)n * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c];
+    }
+}
+
+// ReLU adjoint: g = dy * (y > 0), as BF16 for the gradient GEMMs
+__global__ void k_relu_mask(const float* dy, const bf16* y, bf16* g, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        g[t] = __float2bfloat16_rn(__bfloat162float(y[t]) > 0.f ? dy[t] : 0.f);
+}
+
+// column sums of g [P x C] (bias gradient), deterministic: block b sums rows b, b + nb, ...
+__global__ void k_colsum_partial(const bf16* g, long long P, int C, float* part) {
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.f;
+        for (long long p = blockIdx.x; p < P; p += gridDim.x) s += __bfloat162float(g[p * C + c]);
+        part[(size_t)blockIdx.x * C + c] = s;
+    }
+}
+__global__ void k_colsum_final(const float* part, int nb, int C, float* out) {
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * C + c];
+        out[c] = s;
+    }
+}
+
+// head: phi = sigmoid(sum_c x[p][c] w[c] + b); with targets, also the loss terms and the
+// gradient: dz = 2 m (phi - t) phi (1 - phi) / n_mask, dx[p][c] = dz w[c]; per-block partial sums
+// of loss, dz * x[p][c] (weight gradient) and dz (bias gradient) for a deterministic reduction.
+template <int C>
+__global__ void k_head(const bf16* x, const float* w, const float* bptr, float* phi, long long P,
+                       const float* target, const uint8_t* mask, float inv_n, float* dx,
+                       float* part /* per block: C + 2 */) {
+    __shared__ float sw[C];
+    __shared__ float red[kT / 32][C + 2];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sw[c] = w[c];
+    __syncthreads();
+    const float b = *bptr;
+    float acc[C + 2];
+#pragma unroll
+    for (int c = 0; c < C + 2; ++c) acc[c] = 0.f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        float z = b;
+        float xv[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            xv[c] = __bfloat162float(x[p * C + c]);
+            z += xv[c] * sw[c];
+        }
+        const float f = 1.f / (1.f + __expf(-z));
+        phi[p] = f;
+        if (target) {
+            const float m = mask[p] ? 1.f : 0.f;
+            const float e = f - target[p];
+            const float dz = 2.f * m * e * f * (1.f - f) * inv_n;
+            acc[C] += m * e * e * inv_n;
+            acc[C + 1] += dz;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                acc[c] += dz * xv[c];
+                dx[p * C + c] = dz * sw[c];
+            }
+        }
+    }
+    if (!target) return;
+#pragma unroll
+    for (int c = 0; c < C + 2; ++c) {
+        float v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C + 2; c += blockDim.x) {
+        float s = 0.f;
+        for (int q = 0; q < kT / 32; ++q) s += red[q][c];
+        part[(size_t)blockIdx.x * (C + 2) + c] = s;
+    }
+}
+
+__global__ void k_adam(float* w, const float* g, float* m, float* v, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[t];
+        const float mi = b1 * m[t] + (1.f - b1) * gi;
+        const float vi = b2 * v[t] + (1.f - b2) * gi * gi;
+        m[t] = mi;
+        v[t] = vi;
+        w[t] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+__global__ void k_to_bf16(const float* x, bf16* y, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        y[t] = __float2bfloat16_rn(x[t]);
+}
+
+struct Conv {
+    int src1, C1, up1;  // source tensor index, channels, stored at half resolution
+    int src2, C2;       // second source (-1: none)
+    int Cout, out;      // output tensor index
+    int H, W;           // output resolution
+    size_t w_off, b_off;  // offsets into the parameter vector
+};
+
+struct Tensor {
+    int H, W, C;
+    bf16* y = nullptr;   // activation
+    float* dy = nullptr; // gradient
+};
+
+}  // namespace
+}  // namespace sg
+}  // namespace lbm
+
+using namespace lbm::sg;
+
+struct lbm_surrogate {
+    int H = 0, W = 0, base = 0, maxB = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<Tensor> t;      // 0: input (8 channels)
+    std::vector<Conv> convs;
+    std::vector<std::pair<int, int>> pools;  // (from, to)
+    int head_in = -1;
+    size_t head_w = 0, head_b = 0;
+    size_t nparams = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    bf16* wb = nullptr;
+    bf16 *col = nullptr, *dcol = nullptr, *gmask = nullptr;
+    size_t col_elems = 0, act_elems = 0;
+    float* part = nullptr;  // reduction partials
+    float* phi = nullptr;   // head output
+    float* hpart = nullptr;
+    int part_blocks = 256;
+    long long adam_t = 0;
+    std::string err;
+};
+
+extern "C" void lbm_surrogate_destroy(lbm_surrogate* s);
+
+namespace {
+
+lbm_status sfail(lbm_surrogate* s, lbm_status st, const std::string& msg) {
+    if (s)
+        s->err = msg;
+    else
+        lbm::set_global_error(msg);
+    return st;
+}
+
+#define SCUDA(s, expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return sfail((s), LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <bool AK, bool BK>
+cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
+    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
+    k_gemm_bf16<AK, BK><<<grid, GTHREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int add_tensor(lbm_surrogate* s, int H, int W, int C) {
+    Tensor x;
+    x.H = H;
+    x.W = W;
+    x.C = C;
+    s->t.push_back(x);
+    return (int)s->t.size() - 1;
+}
+
+int add_conv(lbm_surrogate* s, int src1, int up1, int src2, int Cout) {
+    Conv c;
+    c.src1 = src1;
+    c.C1 = s->t[src1].C;
+    c.up1 = up1;
+    c.src2 = src2;
+    c.C2 = src2 >= 0 ? s->t[src2].C : 0;
+    c.H = up1 ? s->t[src1].H * 2 : s->t[src1].H;
+    c.W = up1 ? s->t[src1].W * 2 : s->t[src1].W;
+    c.Cout = Cout;
+    c.out = add_tensor(s, c.H, c.W, Cout);
+    c.w_off = s->nparams;
+    s->nparams += (size_t)Cout * 9 * (c.C1 + c.C2);
+    c.b_off = s->nparams;
+    s->nparams += Cout;
+    s->convs.push_back(c);
+    return c.out;
+}
+
+void build(lbm_surrogate* s) {
+    const int b = s->base;
+    int x = add_tensor(s, s->H, s->W, 8);
+    int s1 = add_conv(s, add_conv(s, x, 0, -1, b), 0, -1, b);
+    int p1 = add_tensor(s, s->H / 2, s->W / 2, b);
+    s->pools.push_back({s1, p1});
+    int s2 = add_conv(s, add_conv(s, p1, 0, -1, 2 * b), 0, -1, 2 * b);
+    int p2 = add_tensor(s, s->H / 4, s->W / 4, 2 * b);
+    s->pools.push_back({s2, p2});
+    int s3 = add_conv(s, add_conv(s, p2, 0, -1, 4 * b), 0, -1, 4 * b);
+    int p3 = add_tensor(s, s->H / 8, s->W / 8, 4 * b);
+    s->pools.push_back({s3, p3});
+    int bt = add_conv(s, add_conv(s, p3, 0, -1, 8 * b), 0, -1, 8 * b);
+    int u3 = add_conv(s, bt, 1, -1, 4 * b);
+    int d3 = add_conv(s, add_conv(s, u3, 0, s3, 4 * b), 0, -1, 4 * b);
+    int u2 = add_conv(s, d3, 1, -1, 2 * b);
+    int d2 = add_conv(s, add_conv(s, u2, 0, s2, 2 * b), 0, -1, 2 * b);
+    int u1 = add_conv(s, d2, 1, -1, b);
+    int d1 = add_conv(s, add_conv(s, u1, 0, s1, b), 0, -1, b);
+    s->head_in = d1;
+    s->head_w = s->nparams;
+    s->nparams += b;
+    s->head_b = s->nparams;
+    s->nparams += 1;
+}
+
+lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
+    s->t[0].y = const_cast<bf16*>(x);
+    // convolutions run in production order; a pool runs right after the conv that feeds it
+    for (const Conv& c : s->convs) {
+        const Tensor& a = s->t[c.src1];
+        if (a.y == nullptr) return sfail(s, LBM_ERR_STATE, "surrogate: missing activation");
+        const int Cin = c.C1 + c.C2;
+        const long long P = (long long)B * c.H * c.W;
+        k_im2col<<<blocks_for(P * 9 * Cin / 8), kT, 0, s->stream>>>(
+            a.y, c.C1, c.up1, c.src2 >= 0 ? s->t[c.src2].y : nullptr, c.C2, B, c.H, c.W, s->col);
+        GemmArgs g{};
+        g.A = s->col;
+        g.B = s->wb + c.w_off;
+        g.M = (int)P;
+        g.N = c.Cout;
+        g.K = 9 * Cin;
+        g.lda = 9 * Cin;
+        g.ldb = 9 * Cin;
+        g.Cb = s->t[c.out].y;
+        g.ldc = c.Cout;
+        g.bias = s->w + c.b_off;
+        g.relu = 1;
+        SCUDA(s, (gemm<true, true>(s->stream, g)));
+        // a pool whose source is this conv's output runs right after it
+        for (const auto& pl : s->pools)
+            if (pl.first == c.out) {
+                const Tensor& src = s->t[pl.first];
+                k_avgpool<<<blocks_for((long long)B * src.H * src.W * src.C / 4), kT, 0,
+                            s->stream>>>(src.y, s->t[pl.second].y, B, src.H, src.W, src.C);
+            }
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_batch,
+                                int32_t device, lbm_surrogate** out) {
+    if (!out) return sfail(nullptr, LBM_ERR_ARG, "lbm_surrogate_create: out is NULL");
+    *out = nullptr;
+    if (H <= 0 || W <= 0 || H % 8 || W % 8 || base <= 0 || base % 8 || max_batch <= 0)
+        return sfail(nullptr, LBM_ERR_ARG,
+                     "lbm_surrogate_create: H, W multiples of 8, base a multiple of 8, batch > 0");
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(nullptr, LBM_ERR_CUDA, "lbm_surrogate_create: cannot select the device");
+    }
+    lbm_surrogate* s = new lbm_surrogate();
+    s->H = H;
+    s->W = W;
+    s->base = base;
+    s->maxB = max_batch;
+    s->device = device;
+    build(s);
+    auto cleanup = [&](const char* e) {
+        lbm_surrogate_destroy(s);
+        return sfail(nullptr, LBM_ERR_CUDA, std::string("lbm_surrogate_create: ") + e);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cudaGetErrorString(e));
+    size_t colmax = 0;
+    for (const Conv& c : s->convs)
+        colmax = std::max(colmax, (size_t)max_batch * c.H * c.W * 9 * (c.C1 + c.C2));
+    s->col_elems = colmax;
+    for (size_t k = 1; k < s->t.size() && e == cudaSuccess; ++k) {
+        Tensor& x = s->t[k];
+        const size_t n = (size_t)max_batch * x.H * x.W * x.C;
+        e = cudaMalloc((void**)&x.y, n * sizeof(bf16));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&x.dy, n * sizeof(float));
+        s->act_elems = std::max(s->act_elems, n);
+    }
+    const size_t np = s->nparams;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->w, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->g, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->m, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->v, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->wb, np * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->col, colmax * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->dcol, colmax * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->gmask, s->act_elems * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&s->part, (size_t)s->part_blocks * 8 * base * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->phi, (size_t)max_batch * H * W * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&s->hpart, (size_t)s->part_blocks * (base + 2) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->w, 0, np * sizeof(float), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, np * sizeof(float), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, np * sizeof(float), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->wb, 0, np * sizeof(bf16), s->stream);
+    if (e != cudaSuccess) return cleanup(cudaGetErrorString(e));
+    *out = s;
+    return LBM_OK;
+}
+
+int64_t lbm_surrogate_num_params(const lbm_surrogate* s) { return s ? (int64_t)s->nparams : 0; }
+
+lbm_status lbm_surrogate_set_weights(lbm_surrogate* s, const float* host, int64_t n) {
+    if (!s || !host || n != (int64_t)s->nparams)
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_set_weights: need num_params floats");
+    SCUDA(s, cudaSetDevice(s->device));
+    SCUDA(s, cudaMemcpyAsync(s->w, host, n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    k_to_bf16<<<blocks_for(n), kT, 0, s->stream>>>(s->w, s->wb, n);
+    SCUDA(s, cudaMemsetAsync(s->m, 0, n * sizeof(float), s->stream));
+    SCUDA(s, cudaMemsetAsync(s->v, 0, n * sizeof(float), s->stream));
+    s->adam_t = 0;
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_get_weights(lbm_surrogate* s, float* host, int64_t n, int32_t grads) {
+    if (!s || !host || n != (int64_t)s->nparams)
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_get_weights: need num_params floats");
+    SCUDA(s, cudaSetDevice(s->device));
+    SCUDA(s, cudaMemcpyAsync(host, grads ? s->g : s->w, n * sizeof(float), cudaMemcpyDeviceToHost,
+                             s->stream));
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_forward(lbm_surrogate* s, const void* x, int32_t B, float* phi_out) {
+    if (!s || !x || !phi_out || B <= 0 || B > s->maxB)
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_forward: bad arguments");
+    SCUDA(s, cudaSetDevice(s->device));
+    lbm_status st = forward(s, (const bf16*)x, B);
+    if (st != LBM_OK) return st;
+    const long long P = (long long)B * s->H * s->W;
+    const int nb = std::min(s->part_blocks, blocks_for(P));
+    if (s->base == 32)
+        k_head<32><<<nb, kT, 0, s->stream>>>(s->t[s->head_in].y, s->w + s->head_w,
+                                             s->w + s->head_b, phi_out, P, nullptr, nullptr, 0.f,
+                                             nullptr, nullptr);
+    else if (s->base == 8)
+        k_head<8><<<nb, kT, 0, s->stream>>>(s->t[s->head_in].y, s->w + s->head_w,
+                                            s->w + s->head_b, phi_out, P, nullptr, nullptr, 0.f,
+                                            nullptr, nullptr);
+    else if (s->base == 16)
+        k_head<16><<<nb, kT, 0, s->stream>>>(s->t[s->head_in].y, s->w + s->head_w,
+                                             s->w + s->head_b, phi_out, P, nullptr, nullptr, 0.f,
+                                             nullptr, nullptr);
+    else
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_forward: base must be 8, 16 or 32");
+    SCUDA(s, cudaGetLastError());
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+// Gradients of the masked MSE into s->g; with lr > 0 also an Adam update. *loss gets the loss.
+lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const float* target,
+                                    const uint8_t* mask, int32_t B, float lr, double* loss) {
+    if (!s || !xin || !target || !mask || B <= 0 || B > s->maxB)
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_train_step: bad arguments");
+    SCUDA(s, cudaSetDevice(s->device));
+    lbm_status st = forward(s, (const bf16*)xin, B);
+    if (st != LBM_OK) return st;
+    const long long P = (long long)B * s->H * s->W;
+    std::vector<uint8_t> hm;
+    // zero all activation gradients (they accumulate from several consumers)
+    for (size_t k = 1; k < s->t.size(); ++k) {
+        const Tensor& x = s->t[k];
+        SCUDA(s, cudaMemsetAsync(x.dy, 0, (size_t)B * x.H * x.W * x.C * sizeof(float), s->stream));
+    }
+    SCUDA(s, cudaMemsetAsync(s->g, 0, s->nparams * sizeof(float), s->stream));
+    float inv_n = 1.f / (float)P;
+    {
+        // number of loss pixels: the mask (B*H*W bytes) is counted on the host once per step
+        hm.resize((size_t)P);
+        SCUDA(s, cudaMemcpyAsync(hm.data(), mask, (size_t)P, cudaMemcpyDeviceToHost, s->stream));
+        SCUDA(s, cudaStreamSynchronize(s->stream));
+        long long cnt = 0;
+        for (uint8_t b : hm) cnt += b != 0;
+        inv_n = cnt > 0 ? 1.f / (float)cnt : 0.f;
+    }
+    const int C = s->base;
+    const int nb = std::min(s->part_blocks, blocks_for(P));
+    Tensor& hin = s->t[s->head_in];
+    if (C == 32)
+        k_head<32><<<nb, kT, 0, s->stream>>>(hin.y, s->w + s->head_w, s->w + s->head_b, s->phi, P,
+                                             target, mask, inv_n, hin.dy, s->hpart);
+    else if (C == 16)
+        k_head<16><<<nb, kT, 0, s->stream>>>(hin.y, s->w + s->head_w, s->w + s->head_b, s->phi, P,
+                                             target, mask, inv_n, hin.dy, s->hpart);
+    else if (C == 8)
+        k_head<8><<<nb, kT, 0, s->stream>>>(hin.y, s->w + s->head_w, s->w + s->head_b, s->phi, P,
+                                            target, mask, inv_n, hin.dy, s->hpart);
+    else
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_train_step: base must be 8, 16 or 32");
+    SCUDA(s, cudaGetLastError());
+    // head gradients: sum the per-block partials (C weights, loss, bias)
+    k_colsum_final<<<1, kT, 0, s->stream>>>(s->hpart, nb, C + 2, s->part);
+    SCUDA(s, cudaMemcpyAsync(s->g + s->head_w, s->part, C * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s->stream));
+    SCUDA(s, cudaMemcpyAsync(s->g + s->head_b, s->part + C + 1, sizeof(float),
+                             cudaMemcpyDeviceToDevice, s->stream));
+    float hl = 0.f;
+    SCUDA(s, cudaMemcpyAsync(&hl, s->part + C, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    // backward through the convolutions (reverse order), pools interleaved
+    for (int ci = (int)s->convs.size() - 1; ci >= 0; --ci) {
+        const Conv& c = s->convs[ci];
+        // gradient arriving at this conv's output also includes the pool path (already added,
+        // pools run before: a pool's output gradient is complete once every later conv is done)
+        for (const auto& pl : s->pools)
+            if (pl.first == c.out) {
+                const Tensor& src = s->t[pl.first];
+                k_avgpool_bwd<<<blocks_for((long long)B * src.H * src.W * src.C), kT, 0,
+                                s->stream>>>(s->t[pl.second].dy, s->t[pl.first].dy, B, src.H,
+                                             src.W, src.C);
+            }
+        Tensor& o = s->t[c.out];
+        const int Cin = c.C1 + c.C2;
+        const long long Pc = (long long)B * c.H * c.W;
+        const long long n_out = Pc * c.Cout;
+        k_relu_mask<<<blocks_for(n_out), kT, 0, s->stream>>>(o.dy, o.y, s->gmask, n_out);
+        // bias gradient
+        const int cb = std::min<long long>(s->part_blocks, Pc);
+        k_colsum_partial<<<cb, kT, 0, s->stream>>>(s->gmask, Pc, c.Cout, s->part);
+        k_colsum_final<<<1, kT, 0, s->stream>>>(s->part, cb, c.Cout, s->g + c.b_off);
+        // weight gradient: dW[co][k] = sum_p g[p][co] col[p][k]
+        const Tensor& a = s->t[c.src1];
+        k_im2col<<<blocks_for(Pc * 9 * Cin / 8), kT, 0, s->stream>>>(
+            a.y, c.C1, c.up1, c.src2 >= 0 ? s->t[c.src2].y : nullptr, c.C2, B, c.H, c.W, s->col);
+        GemmArgs gw{};
+        gw.A = s->gmask;
+        gw.B = s->col;
+        gw.M = c.Cout;
+        gw.N = 9 * Cin;
+        gw.K = (int)Pc;
+        gw.lda = c.Cout;
+        gw.ldb = 9 * Cin;
+        gw.Cf = s->g + c.w_off;
+        gw.ldc = 9 * Cin;
+        SCUDA(s, (gemm<false, false>(s->stream, gw)));
+        // data gradient (not needed for the input tensor)
+        if (c.src1 == 0) continue;
+        GemmArgs gd{};
+        gd.A = s->gmask;
+        gd.B = s->wb + c.w_off;
+        gd.M = (int)Pc;
+        gd.N = 9 * Cin;
+        gd.K = c.Cout;
+        gd.lda = c.Cout;
+        gd.ldb = 9 * Cin;
+        gd.Cb = s->dcol;
+        gd.ldc = 9 * Cin;
+        SCUDA(s, (gemm<true, false>(s->stream, gd)));
+        const long long h1 = c.up1 ? c.H / 2 : c.H, w1 = c.up1 ? c.W / 2 : c.W;
+        const long long n1 = (long long)B * h1 * w1 * c.C1 + Pc * c.C2;
+        k_col2im<<<blocks_for(n1), kT, 0, s->stream>>>(
+            s->dcol, c.C1, c.up1, s->t[c.src1].dy, 1, c.C2,
+            c.src2 >= 0 ? s->t[c.src2].dy : nullptr, 1, B, c.H, c.W);
+        SCUDA(s, cudaGetLastError());
+    }
+    if (lr > 0.f) {
+        ++s->adam_t;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f / (1.f - powf(b1, (float)s->adam_t));
+        const float c2 = 1.f / (1.f - powf(b2, (float)s->adam_t));
+        k_adam<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(
+            s->w, s->g, s->m, s->v, (long long)s->nparams, lr, b1, b2, 1e-8f, c1, c2);
+        k_to_bf16<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(s->w, s->wb,
+                                                                           (long long)s->nparams);
+    }
+    SCUDA(s, cudaGetLastError());
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    if (loss) *loss = hl;
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_phi(lbm_surrogate* s, float* host_phi, int32_t B) {
+    if (!s || !host_phi || B <= 0 || B > s->maxB)
+        return sfail(s, LBM_ERR_ARG, "lbm_surrogate_phi: bad arguments");
+    SCUDA(s, cudaMemcpyAsync(host_phi, s->phi, (size_t)B * s->H * s->W * sizeof(float),
+                             cudaMemcpyDeviceToHost, s->stream));
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+// C = A * B with BF16 operands (device), FP32 output; a_kmajor / b_kmajor select the storage
+// of A (M x K) and B (K x N): K-major A[m*lda + k], B[n*ldb + k]; MN-major A[k*lda + m],
+// B[k*ldb + n].
+lbm_status lbm_sg_gemm(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                       int32_t a_kmajor, int32_t b_kmajor, int32_t lda, int32_t ldb, float* C,
+                       int32_t ldc, void* stream) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0)
+        return sfail(nullptr, LBM_ERR_ARG, "lbm_sg_gemm: bad arguments");
+    if ((a_kmajor && (K % 8 || lda % 8)) || (!a_kmajor && (M % 8 || lda % 8)) ||
+        (b_kmajor && (K % 8 || ldb % 8)) || (!b_kmajor && (N % 8 || ldb % 8)))
+        return sfail(nullptr, LBM_ERR_ARG, "lbm_sg_gemm: alignment (multiples of 8) violated");
+    GemmArgs g{};
+    g.A = (const bf16*)A;
+    g.B = (const bf16*)B;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.Cf = C;
+    g.ldc = ldc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (a_kmajor && b_kmajor)
+        e = gemm<true, true>(st, g);
+    else if (a_kmajor)
+        e = gemm<true, false>(st, g);
+    else if (b_kmajor)
+        e = gemm<false, true>(st, g);
+    else
+        e = gemm<false, false>(st, g);
+    if (e != cudaSuccess)
+        return sfail(nullptr, LBM_ERR_CUDA, std::string("lbm_sg_gemm: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+void lbm_surrogate_destroy(lbm_surrogate* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (size_t k = 1; k < s->t.size(); ++k) {
+        cudaFree(s->t[k].y);
+        cudaFree(s->t[k].dy);
+    }
+    cudaFree(s->w);
+    cudaFree(s->g);
+    cudaFree(s->m);
+    cudaFree(s->v);
+    cudaFree(s->wb);
+    cudaFree(s->col);
+    cudaFree(s->dcol);
+    cudaFree(s->gmask);
+    cudaFree(s->part);
+    cudaFree(s->phi);
+    cudaFree(s->hpart);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+const char* lbm_surrogate_last_error(const lbm_surrogate* s) {
+    return s ? s->err.c_str() : lbm_last_error(nullptr);
+}
+
+}  // extern "C"

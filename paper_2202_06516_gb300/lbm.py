@@ -410,3 +410,93 @@ class Batch:
 
     def mass(self, i):
         return lbm_mass(lbm_batch_instance(self.b, i))[1]
+
+
+# ------------------------------------------------------------------- warm-start surrogate
+def _sg_sig():
+    L = lib()
+    if getattr(L, "_sg_ready", False):
+        return L
+    vp, fp = C.c_void_p, C.POINTER(C.c_float)
+    L.lbm_surrogate_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                       C.POINTER(vp)]
+    L.lbm_surrogate_num_params.argtypes = [vp]
+    L.lbm_surrogate_num_params.restype = C.c_int64
+    L.lbm_surrogate_set_weights.argtypes = [vp, fp, C.c_int64]
+    L.lbm_surrogate_get_weights.argtypes = [vp, fp, C.c_int64, C.c_int32]
+    L.lbm_surrogate_forward.argtypes = [vp, vp, C.c_int32, vp]
+    L.lbm_surrogate_train_step.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_float,
+                                           C.POINTER(C.c_double)]
+    L.lbm_surrogate_phi.argtypes = [vp, fp, C.c_int32]
+    L.lbm_surrogate_destroy.argtypes = [vp]
+    L.lbm_surrogate_destroy.restype = None
+    L.lbm_surrogate_last_error.argtypes = [vp]
+    L.lbm_surrogate_last_error.restype = C.c_char_p
+    L.lbm_sg_gemm.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                              C.c_int32, C.c_int32, vp, C.c_int32, vp]
+    for n in ("lbm_surrogate_create", "lbm_surrogate_set_weights", "lbm_surrogate_get_weights",
+              "lbm_surrogate_forward", "lbm_surrogate_train_step", "lbm_surrogate_phi",
+              "lbm_sg_gemm"):
+        getattr(L, n).restype = C.c_int
+    L._sg_ready = True
+    return L
+
+
+def _scheck(status, s=None):
+    if status != LBM_OK:
+        raise LbmError(status, _sg_sig().lbm_surrogate_last_error(s).decode())
+
+
+def lbm_sg_gemm(A_ptr, B_ptr, M, N, K, a_kmajor, b_kmajor, lda, ldb, C_ptr, ldc, stream=None):
+    """C (FP32, device) = A * B with BF16 device operands; see include/lbm.h."""
+    _scheck(_sg_sig().lbm_sg_gemm(A_ptr, B_ptr, M, N, K, int(a_kmajor), int(b_kmajor), lda, ldb,
+                                  C_ptr, ldc, stream))
+
+
+class Surrogate:
+    """The warm-start U-Net on an H x W lattice (device inputs are torch tensors' pointers)."""
+
+    def __init__(self, H, W, base=32, max_batch=8, device=0):
+        L = _sg_sig()
+        self.H, self.W, self.base, self.max_batch = H, W, base, max_batch
+        out = C.c_void_p()
+        _scheck(L.lbm_surrogate_create(H, W, base, max_batch, device, C.byref(out)))
+        self.s = out
+        self.n = int(L.lbm_surrogate_num_params(self.s))
+
+    def close(self):
+        if getattr(self, "s", None):
+            _sg_sig().lbm_surrogate_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _scheck(_sg_sig().lbm_surrogate_set_weights(
+            self.s, w.ctypes.data_as(C.POINTER(C.c_float)), w.size), self.s)
+
+    def weights(self, grads=False) -> np.ndarray:
+        w = np.zeros(self.n, dtype=np.float32)
+        _scheck(_sg_sig().lbm_surrogate_get_weights(
+            self.s, w.ctypes.data_as(C.POINTER(C.c_float)), self.n, int(grads)), self.s)
+        return w
+
+    def forward(self, x_ptr, B, phi_ptr):
+        _scheck(_sg_sig().lbm_surrogate_forward(self.s, x_ptr, B, phi_ptr), self.s)
+
+    def train_step(self, x_ptr, target_ptr, mask_ptr, B, lr) -> float:
+        loss = C.c_double()
+        _scheck(_sg_sig().lbm_surrogate_train_step(self.s, x_ptr, target_ptr, mask_ptr, B,
+                                                   float(lr), C.byref(loss)), self.s)
+        return loss.value
+
+    def phi(self, B) -> np.ndarray:
+        out = np.zeros((B, self.H, self.W), dtype=np.float32)
+        _scheck(_sg_sig().lbm_surrogate_phi(self.s, out.ctypes.data_as(C.POINTER(C.c_float)), B),
+                self.s)
+        return out

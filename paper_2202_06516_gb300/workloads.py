@@ -115,3 +115,54 @@ def batched(n: int = 256, seed: int = 0) -> list[Workload]:
         out.append(Workload(f"batch{seed}-{i}", nx, ny, (cx, 0.0, R), drop,
                             mu_rel_circle=mu_rel_for_angle(theta), steps=40000))
     return out
+
+
+# ----------------------------------------------------------------------- warm-start surrogate
+def unet_layers(base: int = 32):
+    """(c_in, c_out) of the U-Net's 3x3 convolutions in forward order (encoder 4 levels of two
+    convolutions with base, 2, 4, 8 x base channels; decoder per level one convolution of the
+    upsampled coarser output and two on [that | skip]), input with 8 channels."""
+    b = base
+    return [(8, b), (b, b), (b, 2 * b), (2 * b, 2 * b), (2 * b, 4 * b), (4 * b, 4 * b),
+            (4 * b, 8 * b), (8 * b, 8 * b), (8 * b, 4 * b), (8 * b, 4 * b), (4 * b, 4 * b),
+            (4 * b, 2 * b), (4 * b, 2 * b), (2 * b, 2 * b), (2 * b, b), (2 * b, b), (b, b)]
+
+
+def unet_init(base: int = 32, seed: int = 0) -> np.ndarray:
+    """Seeded initial weights (He-normal convolutions, zero biases, small head) as one FP32
+    vector: per convolution [c_out][ky][kx][c_in] then bias[c_out]; head weight[base], bias[1]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co in unet_layers(base):
+        out.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), size=co * 9 * ci))
+        out.append(np.zeros(co))
+    out.append(rng.normal(0.0, 0.01, size=base))
+    out.append(np.zeros(1))
+    return np.concatenate(out).astype(np.float32)
+
+
+def warm_cases(n: int, seed: int, size: int = 256):
+    """Cases for the warm-start surrogate: the batched ranges (domain 128..768 x 128..512,
+    R 20..200, r 15..90, target angle 30..150 degrees) rescaled to a size x size lattice by
+    s = size / max(nx, ny), rejection-resampled until the scaled cylinder and drop fit
+    (2 R + 16 <= size, R + 2 r + 8 <= size) and the drop keeps r >= 12 (a smaller drop is mostly
+    interface at the 8.5 lu interface width). Seeds seed, seed+1, ... give case 0, 1, ..."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng([seed, i, 7])
+        while True:
+            nx = int(rng.integers(128, 769))
+            ny = int(rng.integers(128, 513))
+            R = float(rng.integers(20, 201))
+            r = float(rng.integers(15, 91))
+            theta = float(rng.uniform(30.0, 150.0))
+            s = size / max(nx, ny)
+            Rs = round(2 * R * s) / 2
+            rs = r * s
+            if Rs >= 4 and 2 * Rs + 16 <= size and Rs + 2 * rs + 8 <= size and rs >= 12:
+                break
+        cx = size / 2
+        drop = cap_drop(cx, 0, Rs, rs) if rs >= 60 else tangent_drop(cx, 0, Rs, rs)
+        out.append(Workload(f"warm{seed}-{i}", size, size, (cx, 0.0, Rs), drop,
+                            mu_rel_circle=mu_rel_for_angle(theta), steps=20000))
+    return out

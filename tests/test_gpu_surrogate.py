@@ -1,0 +1,117 @@
+"""GPU parity of the warm-start surrogate: the tensor-core GEMM against FP64 products of the
+same BF16 operands, and the U-Net's forward pass, loss and every gradient against the FP64
+oracle (oracle/surrogate.py) on the same BF16-rounded inputs and weights."""
+import numpy as np
+import pytest
+
+from paper_2202_06516_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2202_06516_gb300 import lbm
+    return torch, lbm
+
+
+@pytest.mark.parametrize("ak,bk", [(1, 1), (1, 0), (0, 0), (0, 1)])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 72, 136), (8, 256, 1000), (520, 40, 8)])
+def test_gemm_layouts(env, ak, bk, M, N, K):
+    torch, lbm = env
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    want = A.double() @ B.double()
+    Ad = (A if ak else A.t()).contiguous().cuda()   # K-major = row-major A; MN-major = A^T rows
+    Bd = (B.t() if bk else B).contiguous().cuda()
+    lda = K if ak else M
+    ldb = K if bk else N
+    Cd = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    lbm.lbm_sg_gemm(Ad.data_ptr(), Bd.data_ptr(), M, N, K, ak, bk, lda, ldb, Cd.data_ptr(), N)
+    torch.cuda.synchronize()
+    got = Cd.double().cpu()
+    err = (got - want).abs().max().item() / max(1.0, want.abs().max().item())
+    assert err < 2e-6, err
+
+
+def _case(seed=0, B=2, H=32, Wd=32, base=8):
+    rng = np.random.default_rng(seed)
+    x = np.zeros((B, H, Wd, 8), dtype=np.float32)
+    x[..., 0] = rng.uniform(size=(B, H, Wd)) > 0.7
+    x[..., 1] = rng.normal(0, 0.5, size=(B, H, Wd))
+    x[..., 2] = 0.3
+    target = rng.uniform(0, 1, size=(B, H, Wd)).astype(np.float32)
+    mask = (x[..., 0] == 0).astype(np.uint8)
+    p = W.unet_init(base, seed)
+    p = p + rng.normal(0, 0.02, size=p.size).astype(np.float32)
+    return x, target, mask, p
+
+
+def _bf16(a):
+    import torch
+    return torch.tensor(a).to(torch.bfloat16).double().numpy()
+
+
+@pytest.mark.parametrize("base,H", [(8, 32), (16, 64)])
+def test_forward_loss_gradients_match_oracle(env, base, H):
+    torch, lbm = env
+    from oracle import surrogate as S
+    x, t, m, p = _case(base=base, H=H, Wd=H)
+    s = lbm.Surrogate(H, H, base=base, max_batch=2)
+    assert s.n == p.size
+    s.set_weights(p)
+    xd = torch.tensor(x).to(torch.bfloat16).cuda()
+    td = torch.tensor(t).cuda()
+    md = torch.tensor(m).cuda()
+    loss = s.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 2, 0.0)
+    g = s.weights(grads=True).astype(np.float64)
+    phi = s.phi(2)
+    # oracle on the BF16-rounded inputs and weights the GPU used
+    pw = _bf16(p)
+    convs, n = S.layer_specs(base)
+    o = 0
+    for ci, co, _ in convs:          # biases stay FP32 in the GPU epilogue
+        o += co * 9 * ci
+        pw[o:o + co] = p[o:o + co]
+        o += co
+    pw[o:] = p[o:]                   # head is FP32 on the GPU
+    xb, tt, mb = _bf16(x), t.astype(np.float64), m.astype(bool)
+    lref, gref, phiref = S.loss_and_grad(pw, xb, tt, mb, base)
+    lbf, gbf, phibf = S.loss_and_grad(pw, xb, tt, mb, base, bf16_activations=True)
+    cosine = lambda a, b_: a @ b_ / (np.linalg.norm(a) * np.linalg.norm(b_) + 1e-30)
+    # against the FP64 network: within what BF16 storage of activations and gradients allows
+    assert np.abs(phi - phiref).max() < 2e-2
+    assert loss == pytest.approx(lref, rel=3e-2)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 0.1
+    assert cosine(g, gref) > 0.99
+    # against the oracle that stores activations in BF16 as the method does: every layer's
+    # weight gradient points the same way (the rest is BF16 storage of the gradients)
+    assert np.abs(phi - phibf).max() < 5e-3
+    assert cosine(g, gbf) > 0.995
+    o = 0
+    for k, (ci, co, _) in enumerate(convs):
+        sl = slice(o, o + co * 9 * ci)
+        assert cosine(g[sl], gbf[sl]) > 0.975, k
+        bias = slice(o + co * 9 * ci, o + co * 9 * ci + co)
+        assert cosine(g[bias], gbf[bias]) > 0.95, k
+        o += co * 9 * ci + co
+    head = slice(o, o + base + 1)
+    assert cosine(g[head], gbf[head]) > 0.999
+    s.close()
+
+
+def test_training_reduces_loss(env):
+    torch, lbm = env
+    x, t, m, p = _case(seed=3, H=32, Wd=32, base=8)
+    s = lbm.Surrogate(32, 32, base=8, max_batch=2)
+    s.set_weights(p)
+    xd = torch.tensor(x).to(torch.bfloat16).cuda()
+    td = torch.tensor(t).cuda()
+    md = torch.tensor(m).cuda()
+    losses = [s.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 2, 3e-3) for _ in range(60)]
+    assert losses[-1] < 0.7 * losses[0]
+    s.close()
