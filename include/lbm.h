@@ -237,8 +237,9 @@ void lbm_batch_destroy(lbm_batch *b);
  * Eq. 16 flat-cap start): a U-Net on an H x W lattice mapping (solid mask, wall-wetting map,
  * drop-volume plane) to phi = (rho - rho_g) / (rho_l - rho_g), trained on solver-equilibrated
  * fields. BF16 activations and weight copies, FP32 master weights, FP32 accumulation on tensor
- * cores. Architecture: encoder levels with base, 2, 4, 8 x base channels (two 3x3 conv + ReLU
- * each, 2x2 average pooling between), decoder levels of a 3x3 conv on the 2x nearest-upsampled
+ * cores. Architecture: encoder levels with base, 2, 4, 8 x base channels (two 3x3 conv + leaky
+ * ReLU (slope 0.1) each, 2x2 average pooling between), decoder levels of a 3x3 conv on the 2x
+ * nearest-upsampled
  * coarser output and two 3x3 convs on [that | skip], 1x1 sigmoid head. Parameters: one FP32
  * vector, per convolution in forward order weight [c_out][ky][kx][c_in] then bias [c_out], then
  * head weight [base] and bias [1].

@@ -6,7 +6,8 @@ independently from the library: the same specification, written with library pri
 
 Specification (shared reading, not shared code): input NHWC with 8 channels (mask, wetting map,
 volume plane, five zero channels); levels with base, 2 base, 4 base, 8 base channels; per level
-two 3x3 convolutions (padding 1) with ReLU; 2x2 average pooling between encoder levels; in the
+two 3x3 convolutions (padding 1) with leaky ReLU (slope 0.1); 2x2 average pooling between
+encoder levels; in the
 decoder each level starts with a 3x3 convolution of the 2x nearest-upsampled coarser output,
 then two 3x3 convolutions on [that result | encoder skip] (channel concatenation in that order);
 a 1x1 head with a sigmoid. Parameters are one flat FP32 vector: for every convolution in
@@ -68,7 +69,7 @@ def forward(params: torch.Tensor, x_nhwc: torch.Tensor, base: int,
     layers, hw, hb = unpack(params, base)
     x = x_nhwc.permute(0, 3, 1, 2)
     st = _bf16_store if bf16_activations else (lambda t: t)
-    conv = lambda t, k: st(F.relu(F.conv2d(t, layers[k][0], layers[k][1], padding=1)))
+    conv = lambda t, k: st(F.leaky_relu(F.conv2d(t, layers[k][0], layers[k][1], padding=1), 0.1))
     pool = lambda t: st(F.avg_pool2d(t, 2))
     s1 = conv(conv(x, 0), 1)
     s2 = conv(conv(pool(s1), 2), 3)

@@ -4,9 +4,9 @@
 // flat-cap start (Sec. 4, Eq. 16) that the solver otherwise performs.
 //
 // Network (levels l = 1..4, channels c_l = base * 2^(l-1)):
-//   encoder   conv3x3 + ReLU twice per level, 2x2 average pooling between levels
+//   encoder   conv3x3 + leaky ReLU (slope 0.1) twice per level, 2x2 average pooling between
 //   decoder   2x upsampling folded into the next conv3x3 (nearest), the skip concatenation folded
-//             into the following conv3x3 (two-source im2col), conv3x3 + ReLU twice per level
+//             into the following conv3x3 (two-source im2col), conv3x3 + leaky ReLU twice per level
 //   head      1x1 conv to one channel, sigmoid: phi = (rho - rho_g) / (rho_l - rho_g)
 // Activations BF16 NHWC, weights FP32 masters with BF16 copies, all contractions on tensor cores
 // through one BF16 GEMM with FP32 accumulation (sg_gemm.cuh) over im2col / col2im buffers.
@@ -144,11 +144,12 @@ __global__ void k_avgpool_bwd(const float* dy, float* dx, int B, int H, int W, i
     }
 }
 
-// ReLU adjoint: g = dy * (y > 0), as BF16 for the gradient GEMMs
+// leaky-ReLU adjoint: g = dy * (y > 0 ? 1 : 0.1) (the output has the sign of its input), as
+// BF16 for the gradient GEMMs
 __global__ void k_relu_mask(const float* dy, const bf16* y, bf16* g, long long n) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
-        g[t] = __float2bfloat16_rn(__bfloat162float(y[t]) > 0.f ? dy[t] : 0.f);
+        g[t] = __float2bfloat16_rn(__bfloat162float(y[t]) > 0.f ? dy[t] : 0.1f * dy[t]);
 }
 
 // column sums of g [P x C] (bias gradient), deterministic: block b sums rows b, b + nb, ...

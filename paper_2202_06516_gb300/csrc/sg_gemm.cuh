@@ -5,7 +5,8 @@
 // two-stage cp.async pipeline, fragments via ldmatrix (.trans for MN-major operands).
 // Requirements: K-major operands have K % 8 == 0 and 16-byte aligned rows; MN-major operands
 // have M (resp. N) % 8 == 0. Out-of-range rows and columns are zero-filled on load and masked on
-// store. Epilogue: optional bias[n], ReLU, FP32 or BF16 output, optional accumulation into FP32.
+// store. Epilogue: optional bias[n], leaky ReLU (slope 0.1), FP32 or BF16 output, optional
+// accumulation into FP32.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,7 +26,7 @@ struct GemmArgs {
     __nv_bfloat16* Cb; // BF16 output (or nullptr)
     int ldc;
     const float* bias; // per column n (or nullptr)
-    int relu;
+    int relu;          // apply the leaky ReLU max(v, 0.1 v)
     int accumulate;    // FP32 output: C += result
 };
 
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(const GemmArgs g) {
                 if (m >= g.M || n >= g.N) continue;
                 float v = acc[i][j][e];
                 if (g.bias) v += g.bias[n];
-                if (g.relu) v = fmaxf(v, 0.f);
+                if (g.relu) v = fmaxf(v, 0.1f * v);
                 const size_t o = (size_t)m * g.ldc + n;
                 if (g.Cf) {
                     if (g.accumulate)

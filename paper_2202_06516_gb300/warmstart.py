@@ -3,7 +3,11 @@ library's kernels, and the time-to-equilibrated-angle comparison of warm and col
 
 Inputs per case (H x W x 8, BF16): channel 0 the solid mask, channel 1 the wall chemical
 potential relative to the neutral wall (divided by 0.1) on the wetting layers, channel 2 the
-initial liquid area divided by H W (a constant plane), channels 3-7 zero. Target: the
+initial liquid area divided by H W (a constant plane); geometry encodings derived from the
+substrate: channel 3 the height y / H, channel 4 the horizontal offset from the cylinder axis
+divided by W, channel 5 the distance to the substrate surface divided by 64 (clipped to 1),
+channel 6 the wetting value of channel 1 spread over all nodes (the drop sees one wall
+chemical potential), channel 7 zero. Target: the
 equilibrated phi = (rho - rho_g) / (rho_l - rho_g), clipped to [0, 1], on fluid nodes (the loss
 mask). Orchestration only; every numerical step runs in the library (solver, geometry, network).
 """
@@ -43,6 +47,7 @@ def inputs_of(b, ws, neutral, co):
     n = len(ws)
     H, Wd = ws[0].ny, ws[0].nx
     x = np.zeros((n, H, Wd, 8), dtype=np.float32)
+    jj, ii = np.mgrid[0:H, 0:Wd].astype(np.float64)
     for i, w in enumerate(ws):
         ctx = lbm.lbm_batch_instance(b.b, i)
         flags, muw, _ = lbm.lbm_read_geometry(ctx, w.nx, w.ny)
@@ -53,6 +58,12 @@ def inputs_of(b, ws, neutral, co):
         rho = lbm.lbm_read_fields(ctx, lbm.LBM_FIELD_RHO, w.nx, w.ny)[0]
         phi0 = np.clip((rho - co["rho_g"]) / (co["rho_l"] - co["rho_g"]), 0, 1) * (f == 0)
         x[i, :, :, 2] = phi0.sum() / (H * Wd)
+        x[i, :, :, 3] = jj / H
+        cx, cy, R = w.circle
+        x[i, :, :, 4] = (ii - cx) / Wd
+        dist = np.minimum(np.hypot(ii - cx, jj - cy) - (R + 0.5), jj + 0.5)
+        x[i, :, :, 5] = np.clip(dist / 64.0, -1.0, 1.0)
+        x[i, :, :, 6] = w.mu_rel_circle / MU_SCALE
     return x
 
 
@@ -90,6 +101,11 @@ def train(sur, x, t, m, epochs=20, batch=8, lr=1e-3, seed=0, log=None):
     """Adam on the masked MSE; data held on the device (torch tensors as plain buffers)."""
     import torch
     n = x.shape[0]
+    # start the head at the mean target (logit of the mean liquid fraction)
+    w = sur.weights()
+    pm = float(np.clip((t * m).sum() / max(m.sum(), 1), 1e-3, 1 - 1e-3))
+    w[-1] = np.log(pm / (1 - pm))
+    sur.set_weights(w)
     xd = torch.tensor(x).to(torch.bfloat16).cuda()
     td = torch.tensor(t).cuda()
     md = torch.tensor(m).cuda()

@@ -54,8 +54,8 @@ def test_gradient_finite_differences():
 
 
 def test_layer_semantics():
-    """Hand-built checks of the specification: a constant input through a network whose
-    convolutions are identity-like keeps the structure; the head is a sigmoid of a dot product."""
+    """Hand-built checks of the specification: zero convolution weights with unit biases make
+    every activation 1 (leaky ReLU of a positive value), so the head sees a constant."""
     from oracle import surrogate as S
     base = 8
     convs, n = S.layer_specs(base)
@@ -71,3 +71,30 @@ def test_layer_semantics():
     x = np.random.default_rng(0).uniform(size=(1, 16, 16, 8))
     phi = S.predict(p, x, base)
     assert np.allclose(phi, 1.0 / (1.0 + np.exp(-(0.5 * base - 1.0))))
+
+
+def test_leaky_relu_slope():
+    """Negative pre-activations pass with slope 0.1: zero weights and biases of -1 make every
+    activation -0.1 at the first layer and the output a known constant."""
+    from oracle import surrogate as S
+    base = 8
+    convs, n = S.layer_specs(base)
+    p = np.zeros(n)
+    o = 0
+    ci, co, _ = convs[0]
+    o += co * 9 * ci
+    p[o:o + co] = -1.0   # first conv: output -0.1 everywhere
+    o += co
+    ci, co, _ = convs[1]
+    # second conv: centre tap weight 1 on channel 0 only -> -0.1 -> leaky -> -0.01 (plus bias 0)
+    w = np.zeros((co, 3, 3, ci))
+    w[:, 1, 1, 0] = 1.0
+    p[o:o + co * 9 * ci] = w.ravel()
+    x = np.zeros((1, 16, 16, 8))
+    import torch
+    layers, _, _ = S.unpack(torch.tensor(p), base)
+    t = torch.tensor(x).permute(0, 3, 1, 2)
+    a0 = torch.nn.functional.leaky_relu(torch.nn.functional.conv2d(t, layers[0][0], layers[0][1], padding=1), 0.1)
+    assert torch.allclose(a0, torch.full_like(a0, -0.1))
+    a1 = torch.nn.functional.leaky_relu(torch.nn.functional.conv2d(a0, layers[1][0], layers[1][1], padding=1), 0.1)
+    assert torch.allclose(a1[0, :, 5, 5], torch.full((8,), -0.01, dtype=torch.float64))
