@@ -277,6 +277,8 @@ struct lbm_surrogate {
     float* part = nullptr;  // reduction partials
     float* phi = nullptr;   // head output
     float* hpart = nullptr;
+    float* splitk = nullptr;  // split-K partials of the weight gradient
+    size_t splitk_elems = 0;
     int part_blocks = 256;
     long long adam_t = 0;
     std::string err;
@@ -305,6 +307,30 @@ template <bool AK, bool BK>
 cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
     dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
     k_gemm_bf16<AK, BK><<<grid, GTHREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Weight-gradient GEMM (C_out x 9 C_in, K = pixels): few output tiles and a very long K, so K
+// is split over up to 128 CTA slices whose FP32 partials are summed in a fixed order.
+cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
+                       float* out) {
+    const int tiles = ((a.N + GBN - 1) / GBN) * ((a.M + GBM - 1) / GBM);
+    int splits = std::max(1, std::min(128, 2 * 152 / std::max(1, tiles)));
+    const long long stride = (long long)a.M * a.ldc;
+    while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
+    if (splits == 1) {
+        a.Cf = out;
+        return gemm<false, false>(st, a);
+    }
+    int chunk = (a.K + splits - 1) / splits;
+    chunk = (chunk + GBK - 1) / GBK * GBK;
+    splits = (a.K + chunk - 1) / chunk;
+    a.Cf = scratch;
+    a.kchunk = chunk;
+    a.split_stride = stride;
+    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM, splits);
+    k_gemm_bf16<false, false><<<grid, GTHREADS, 0, st>>>(a);
+    k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
     return cudaGetLastError();
 }
 
@@ -449,6 +475,10 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->phi, (size_t)max_batch * H * W * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMalloc((void**)&s->hpart, (size_t)s->part_blocks * (base + 2) * sizeof(float));
+    size_t wmax = 0;
+    for (const Conv& c : s->convs) wmax = std::max(wmax, (size_t)c.Cout * 9 * (c.C1 + c.C2));
+    s->splitk_elems = std::min<size_t>(wmax * 128, (size_t)64 << 20);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->splitk, s->splitk_elems * sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(s->w, 0, np * sizeof(float), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, np * sizeof(float), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, np * sizeof(float), s->stream);
@@ -592,9 +622,8 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         gw.K = (int)Pc;
         gw.lda = c.Cout;
         gw.ldb = 9 * Cin;
-        gw.Cf = s->g + c.w_off;
         gw.ldc = 9 * Cin;
-        SCUDA(s, (gemm<false, false>(s->stream, gw)));
+        SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off));
         // data gradient (not needed for the input tensor)
         if (c.src1 == 0) continue;
         GemmArgs gd{};
@@ -694,6 +723,7 @@ void lbm_surrogate_destroy(lbm_surrogate* s) {
     cudaFree(s->part);
     cudaFree(s->phi);
     cudaFree(s->hpart);
+    cudaFree(s->splitk);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -4,7 +4,7 @@
 // one kernel without transposed copies. Tiles of 128 x 128 x 32 per CTA (8 warps of 64 x 32),
 // two-stage cp.async pipeline, fragments via ldmatrix (.trans for MN-major operands).
 // Requirements: K-major operands have K % 8 == 0 and 16-byte aligned rows; MN-major operands
-// have M (resp. N) % 8 == 0. Out-of-range rows and columns are zero-filled on load and masked on
+// have M (resp. N) % 8 == 0; a split-K chunk is a multiple of GBK. Out-of-range rows and columns are zero-filled on load and masked on
 // store. Epilogue: optional bias[n], leaky ReLU (slope 0.1), FP32 or BF16 output, optional
 // accumulation into FP32.
 #pragma once
@@ -28,6 +28,9 @@ struct GemmArgs {
     const float* bias; // per column n (or nullptr)
     int relu;          // apply the leaky ReLU max(v, 0.1 v)
     int accumulate;    // FP32 output: C += result
+    int kchunk;        // split-K: blockIdx.z covers K range [z kchunk, (z + 1) kchunk); its FP32
+                       // result goes to Cf + z * split_stride (0: no split)
+    long long split_stride;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -147,15 +150,20 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(const GemmArgs g) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
 
-    const int nk = (g.K + GBK - 1) / GBK;
-    load_tile<AK, GBM>(sA[0], g.A, g.lda, m0, g.M, 0, g.K);
-    load_tile<BK, GBN>(sB[0], g.B, g.ldb, n0, g.N, 0, g.K);
+    // K range of this CTA (the whole K without split-K); loads stay masked by the full K
+    const int kb = g.kchunk ? blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    const int nk = ke > kb ? (ke - kb + GBK - 1) / GBK : 0;
+    if (nk > 0) {
+        load_tile<AK, GBM>(sA[0], g.A, g.lda, m0, g.M, kb, ke);
+        load_tile<BK, GBN>(sB[0], g.B, g.ldb, n0, g.N, kb, ke);
+    }
     cp_async_commit();
     for (int kt = 0; kt < nk; ++kt) {
         const int st = kt & 1;
         if (kt + 1 < nk) {
-            load_tile<AK, GBM>(sA[st ^ 1], g.A, g.lda, m0, g.M, (kt + 1) * GBK, g.K);
-            load_tile<BK, GBN>(sB[st ^ 1], g.B, g.ldb, n0, g.N, (kt + 1) * GBK, g.K);
+            load_tile<AK, GBM>(sA[st ^ 1], g.A, g.lda, m0, g.M, kb + (kt + 1) * GBK, ke);
+            load_tile<BK, GBN>(sB[st ^ 1], g.B, g.ldb, n0, g.N, kb + (kt + 1) * GBK, ke);
         }
         cp_async_commit();
         cp_async_wait<1>();
@@ -196,7 +204,8 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(const GemmArgs g) {
                 float v = acc[i][j][e];
                 if (g.bias) v += g.bias[n];
                 if (g.relu) v = fmaxf(v, 0.1f * v);
-                const size_t o = (size_t)m * g.ldc + n;
+                const size_t o = (size_t)m * g.ldc + n +
+                                 (g.kchunk ? (size_t)blockIdx.z * g.split_stride : 0);
                 if (g.Cf) {
                     if (g.accumulate)
                         g.Cf[o] += v;
@@ -208,5 +217,20 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(const GemmArgs g) {
             }
 }
 
+}  // namespace sg
+}  // namespace lbm
+
+namespace lbm {
+namespace sg {
+// sum of the split-K partials in split order (deterministic): out[i] = sum_z part[z * stride + i]
+__global__ void k_splitk_sum(const float* part, int splits, long long stride, long long n,
+                             float* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * stride + i];
+        out[i] = s;
+    }
+}
 }  // namespace sg
 }  // namespace lbm
