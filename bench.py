@@ -117,6 +117,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (barrier-synchronised max-reduction); value itself at N = 1."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def rank_workload(rank: int):
+    """Each rank runs its own independent instance: the 2048 x 1024 workload seeded by rank."""
+    from paper_2202_06516_gb300 import workloads as W
+    return W.plain_large(seed=rank)
+
+
 def _resolve(w, lbm_mod):
     m = w.model
     co = lbm_mod.lbm_coexistence(m["eos"], m["Tr"])
@@ -141,7 +158,7 @@ def run_cuda(args, rank, world, dist):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    w = W.plain_large(seed=rank)
+    w = rank_workload(rank)
     stream = torch.cuda.Stream(device=dev)
     lat, geo = _make_lattice(lbm, w, stream=stream, tile=args.tile, min_blocks=args.min_blocks)
     lat.set_geometry(**geo)
@@ -188,11 +205,7 @@ def run_cuda(args, rank, world, dist):
     stable = st == lbm.LBM_OK
     angles = lat.measure()
     lat.close()
-    if dist:
-        t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(ms, dist, f"cuda:{dev}")
 
     # end to end through the C ABI from host buffers (rank-local, not part of the device timing)
     e2e = None

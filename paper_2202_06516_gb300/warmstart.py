@@ -139,6 +139,22 @@ def predict(sur, x, batch=8):
     return out
 
 
+def match_mass(phi, mask, target_mass, rho_g, rho_l):
+    """Shift phi by one constant (then clip to [0, 1]) so that the fluid nodes hold the mass of
+    the cold start: the warm and cold runs then relax the same amount of liquid. Bisection on
+    the shift."""
+    def mass(c):
+        return (rho_g + np.clip(phi + c, 0, 1) * (rho_l - rho_g))[mask].sum()
+    lo, hi = -1.0, 1.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if mass(mid) < target_mass:
+            lo = mid
+        else:
+            hi = mid
+    return np.clip(phi + 0.5 * (lo + hi), 0, 1)
+
+
 def angle_histories(b, n, steps, every):
     """Angles (n, n_meas, 2) measured every `every` steps (NaN where a side had no contact)."""
     hist = []
@@ -164,10 +180,17 @@ def evaluate(sur, ws, steps=20000, every=250, log=None):
     +-0.5 degree equilibrated angle of the cold run's final angle."""
     bc, co, neutral = make_batch(ws)
     x = inputs_of(bc, ws, neutral, co)
+    masses, fluid = [], []
+    for i, w in enumerate(ws):
+        ctx = lbm.lbm_batch_instance(bc.b, i)
+        masses.append(lbm.lbm_mass(ctx)[1]["mass"])
+        fluid.append(lbm.lbm_read_geometry(ctx, w.nx, w.ny)[0][2:-2] == 0)
     hc = angle_histories(bc, len(ws), steps, every)
     bc.close()
-    phi = predict(sur, x)
-    rho0 = co["rho_g"] + phi.astype(np.float64) * (co["rho_l"] - co["rho_g"])
+    phi = predict(sur, x).astype(np.float64)
+    phi = np.stack([match_mass(phi[i], fluid[i], masses[i], co["rho_g"], co["rho_l"])
+                    for i in range(len(ws))])
+    rho0 = co["rho_g"] + phi * (co["rho_l"] - co["rho_g"])
     bw, _, _ = make_batch(ws, rho0=rho0)
     hw = angle_histories(bw, len(ws), steps, every)
     bw.close()
