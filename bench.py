@@ -393,6 +393,10 @@ def run_warmstart(args):
     cold = [r[0] for r in rows if r[0] is not None and r[1] is not None]
     warm = [r[1] for r in rows if r[0] is not None and r[1] is not None]
     both = len(cold)
+    # each run against its own final angle (contact lines pin on the staircase wall, so a warm
+    # run may settle a little away from the cold run's final state)
+    own = [(r[2], r[3]) for r in rows if r[2] is not None and r[3] is not None]
+    gaps = [r[4] for r in rows if r[4] is not None]
     line = {"metric": "steps to +-0.5 deg equilibrated angle (median, held-out)",
             "impl": "cuda", "workload": "warm-start-256x256", "data": "synthetic",
             "train_cases": len(tr), "eval_cases": len(ev), "epochs": args.epochs,
@@ -404,7 +408,11 @@ def run_warmstart(args):
             "warm_median_steps": float(np.median(warm)) if both else None,
             "warm_faster_fraction": float(np.mean(np.array(warm) < np.array(cold))) if both else None,
             "cold_unreached": sum(1 for r in rows if r[0] is None),
-            "warm_unreached": sum(1 for r in rows if r[0] is not None and r[1] is None)}
+            "warm_unreached": sum(1 for r in rows if r[0] is not None and r[1] is None),
+            "self_equilibration_pairs": len(own),
+            "self_cold_median_steps": float(np.median([a for a, _ in own])) if own else None,
+            "self_warm_median_steps": float(np.median([b_ for _, b_ in own])) if own else None,
+            "final_angle_gap_deg_median": float(np.median(gaps)) if gaps else None}
     sur.close()
     return line
 

@@ -198,7 +198,11 @@ def evaluate(sur, ws, steps=20000, every=250, log=None):
     for i in range(len(ws)):
         final = hc[i, -1]
         if np.isnan(final).any():
-            rows.append((None, None))
+            rows.append((None, None, None, None, None))
             continue
-        rows.append((time_to_angle(hc[i], final, every), time_to_angle(hw[i], final, every)))
+        own = hw[i, -1]
+        rows.append((time_to_angle(hc[i], final, every), time_to_angle(hw[i], final, every),
+                     time_to_angle(hc[i], final, every),
+                     None if np.isnan(own).any() else time_to_angle(hw[i], own, every),
+                     None if np.isnan(own).any() else float(np.abs(own - final).max())))
     return rows, hc, hw
