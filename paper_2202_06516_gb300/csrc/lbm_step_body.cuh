@@ -53,12 +53,14 @@ __device__ __forceinline__ double psi_prime<double>(double rho, const StepArgs<d
            2.0 * a.aal * rho;
 }
 
-// Collision in deviation variables g_q = f_q - w_q rho, then exact-difference forcing.
+// Collision in deviation variables g_q = f_q - w_q rho with exact-difference forcing (Eq. 13).
 // MRT: Lallemand-Luo moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy); the equilibrium moments of
 // Eq. 2 minus those of w_q rho are (0, 3 rho u^2, -3 rho u^2, jx, -jx, jy, -jy,
-// rho (ux^2 - uy^2), rho ux uy). Relaxed moments are mapped back with M^-1 = M^T diag(1/|M_k|^2).
-// Forcing (Eq. 13): F_q = f_eq(rho, u + F/rho) - f_eq(rho, u)
-//                       = w_q [3 e.F + 4.5 (e.F)(e.s) - 1.5 F.s],  s = 2u + F/rho.
+// rho (ux^2 - uy^2), rho ux uy). The forcing term F_q = f_eq(rho, u') - f_eq(rho, u) with
+// u' = u + F / rho has the moments (0, 3 rho (u'^2 - u^2), -3 rho (u'^2 - u^2), Fx, -Fx, Fy, -Fy,
+// rho (u'x^2 - u'y^2 - ux^2 + uy^2), rho (u'x u'y - ux uy)); it is added in moment space, so a
+// single back-transform M^-1 = M^T diag(1/|M_k|^2) applies relaxation and forcing together.
+// BGK: g - (g - g_eq) / tau + F_q evaluated per direction.
 template <typename T>
 __device__ __forceinline__ void collide(T g[9], T rho, T Fx, T Fy, const StepArgs<T>& a,
                                         T& ux, T& uy) {
@@ -69,47 +71,52 @@ __device__ __forceinline__ void collide(T g[9], T rho, T Fx, T Fy, const StepArg
     uy = jy * inv_rho;
     const T uu = ux * ux + uy * uy;
     if (a.bgk) {
+        const T sx = (T)2 * ux + Fx * inv_rho, sy = (T)2 * uy + Fy * inv_rho;
+        const T Fs = Fx * sx + Fy * sy;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const T eu = (T)qx(q) * ux + (T)qy(q) * uy;
             const T geq = rho * qw<T>(q) * ((T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu);
-            g[q] -= (g[q] - geq) * a.inv_tau;
+            const T eF = (T)qx(q) * Fx + (T)qy(q) * Fy;
+            const T es = (T)qx(q) * sx + (T)qy(q) * sy;
+            g[q] += -(g[q] - geq) * a.inv_tau +
+                    qw<T>(q) * ((T)3 * eF + (T)4.5 * eF * es - (T)1.5 * Fs);
         }
-    } else {
-        const T axis = g[1] + g[2] + g[3] + g[4];
-        const T diag = g[5] + g[6] + g[7] + g[8];
-        const T m1 = (T)-4 * g[0] - axis + (T)2 * diag;
-        const T m2 = (T)4 * g[0] - (T)2 * axis + diag;
-        const T m4 = (T)-2 * g[1] + (T)2 * g[3] + g[5] - g[6] - g[7] + g[8];
-        const T m6 = (T)-2 * g[2] + (T)2 * g[4] + g[5] + g[6] - g[7] - g[8];
-        const T m7 = g[1] - g[2] + g[3] - g[4];
-        const T m8 = g[5] - g[6] + g[7] - g[8];
-        const T a1 = a.s_e * (m1 - (T)3 * rho * uu) * ((T)1 / (T)36);
-        const T a2 = a.s_eps * (m2 + (T)3 * rho * uu) * ((T)1 / (T)36);
-        const T a4 = a.s_q * (m4 + jx) * ((T)1 / (T)12);
-        const T a6 = a.s_q * (m6 + jy) * ((T)1 / (T)12);
-        const T a7 = a.s_v * (m7 - rho * (ux * ux - uy * uy)) * (T)0.25;
-        const T a8 = a.s_v * (m8 - rho * ux * uy) * (T)0.25;
-        const T c_ax = -a1 - (T)2 * a2;
-        const T c_dg = (T)2 * a1 + a2;
-        g[0] -= (T)-4 * a1 + (T)4 * a2;
-        g[1] -= c_ax - (T)2 * a4 + a7;
-        g[2] -= c_ax - (T)2 * a6 - a7;
-        g[3] -= c_ax + (T)2 * a4 + a7;
-        g[4] -= c_ax + (T)2 * a6 - a7;
-        g[5] -= c_dg + a4 + a6 + a8;
-        g[6] -= c_dg - a4 + a6 - a8;
-        g[7] -= c_dg - a4 - a6 + a8;
-        g[8] -= c_dg + a4 - a6 - a8;
+        return;
     }
-    const T sx = (T)2 * ux + Fx * inv_rho, sy = (T)2 * uy + Fy * inv_rho;
-    const T Fs = Fx * sx + Fy * sy;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const T eF = (T)qx(q) * Fx + (T)qy(q) * Fy;
-        const T es = (T)qx(q) * sx + (T)qy(q) * sy;
-        g[q] += qw<T>(q) * ((T)3 * eF + (T)4.5 * eF * es - (T)1.5 * Fs);
-    }
+    // forced velocity and the moment increments of the forcing term
+    const T vx = ux + Fx * inv_rho, vy = uy + Fy * inv_rho;
+    const T dE = (T)3 * rho * (vx * vx + vy * vy - uu);
+    const T dP = rho * ((vx * vx - vy * vy) - (ux * ux - uy * uy));
+    const T dQ = rho * (vx * vy - ux * uy);
+    const T axis = g[1] + g[2] + g[3] + g[4];
+    const T diag = g[5] + g[6] + g[7] + g[8];
+    const T m1 = (T)-4 * g[0] - axis + (T)2 * diag;
+    const T m2 = (T)4 * g[0] - (T)2 * axis + diag;
+    const T m4 = (T)-2 * g[1] + (T)2 * g[3] + g[5] - g[6] - g[7] + g[8];
+    const T m6 = (T)-2 * g[2] + (T)2 * g[4] + g[5] + g[6] - g[7] - g[8];
+    const T m7 = g[1] - g[2] + g[3] - g[4];
+    const T m8 = g[5] - g[6] + g[7] - g[8];
+    // a_k = (S_k (m_k - m_eq,k) - dM_k) / |M_k|^2
+    const T a1 = (a.s_e * (m1 - (T)3 * rho * uu) - dE) * ((T)1 / (T)36);
+    const T a2 = (a.s_eps * (m2 + (T)3 * rho * uu) + dE) * ((T)1 / (T)36);
+    const T a3 = -Fx * ((T)1 / (T)6);
+    const T a5 = -Fy * ((T)1 / (T)6);
+    const T a4 = (a.s_q * (m4 + jx) + Fx) * ((T)1 / (T)12);
+    const T a6 = (a.s_q * (m6 + jy) + Fy) * ((T)1 / (T)12);
+    const T a7 = (a.s_v * (m7 - rho * (ux * ux - uy * uy)) - dP) * (T)0.25;
+    const T a8 = (a.s_v * (m8 - rho * ux * uy) - dQ) * (T)0.25;
+    const T c_ax = -a1 - (T)2 * a2;
+    const T c_dg = (T)2 * a1 + a2;
+    g[0] -= (T)-4 * a1 + (T)4 * a2;
+    g[1] -= c_ax + a3 - (T)2 * a4 + a7;
+    g[2] -= c_ax + a5 - (T)2 * a6 - a7;
+    g[3] -= c_ax - a3 + (T)2 * a4 + a7;
+    g[4] -= c_ax - a5 + (T)2 * a6 - a7;
+    g[5] -= c_dg + a3 + a5 + a4 + a6 + a8;
+    g[6] -= c_dg - a3 + a5 - a4 + a6 - a8;
+    g[7] -= c_dg - a3 - a5 - a4 - a6 + a8;
+    g[8] -= c_dg + a3 - a5 + a4 - a6 - a8;
 }
 
 template <typename T, int TX, int TY>
@@ -212,6 +219,11 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
 
     // (5) force and collision on tile + 1
     const T c12 = (T)1 / (T)12;
+    // 32-bit element offsets (the same for every thread, so they live in uniform registers):
+    // plane q, and the pulled source of direction q one row and one column back along e_q
+    const unsigned upl = (unsigned)a.plane, uP = (unsigned)a.P;
+#define QPL(q) ((unsigned)(q) * upl)
+#define QSRC(q) ((unsigned)(q) * upl - (unsigned)(qy(q) * (int)uP + qx(q)))
     for (int idx = tid; idx < CW * CH; idx += NT) {
         const int cy = idx / CW, cx = idx - cy * CW;
         const int o = (cy + 6) * RW + (cx + 7);
@@ -229,16 +241,17 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
         const T Fx = -rho * dmux + drx * ((T)1 / (T)3) + rho * a.gx;
         const T Fy = -rho * dmuy + dry * ((T)1 / (T)3) + rho * a.gy;
         // pull the populations of time t (Eq. 4) with half-way bounce-back
+        const unsigned us = (unsigned)self;
+        const T* hb = a.h_in + us;
         T g[9];
-        g[0] = __ldg(a.h_in + self);
+        g[0] = __ldg(hb);
 #pragma unroll
         for (int q = 1; q < 9; ++q) {
             const int os = o - qy(q) * RW - qx(q);
             if (!MIXED || s_flag[os] == kFluid) {
-                const int src = self - qy(q) * a.P - qx(q);
-                g[q] = __ldg(a.h_in + (size_t)q * a.plane + src) + qw<T>(q) * (s_rho[os] - rho);
+                g[q] = __ldg(hb + (int)QSRC(q)) + qw<T>(q) * (s_rho[os] - rho);
             } else {
-                g[q] = __ldg(a.h_in + (size_t)qopp(q) * a.plane + self);
+                g[q] = __ldg(hb + (int)QPL(qopp(q)));
             }
         }
         T ux, uy;
@@ -278,20 +291,23 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
             }
         }
         const T r1 = A + B;
-        const int self = lidx(a.P, gx, gy);
+        const unsigned us = (unsigned)lidx(a.P, gx, gy);
         const bool lo = gx < kPadX, hi = gx >= a.nx - kPadX;
+        const T dr = r0 - r1;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const T v = s_g[q * CW * CH + oc] + qw<T>(q) * (r0 - r1);
-            T* hq = a.h_out + (size_t)q * a.plane;
-            hq[self] = v;
-            if (lo) hq[self + a.nx] = v;
-            if (hi) hq[self - a.nx] = v;
+            const T v = s_g[q * CW * CH + oc] + qw<T>(q) * dr;
+            T* ob = a.h_out + us + QPL(q);
+            ob[0] = v;
+            if (lo) ob[a.nx] = v;
+            if (hi) ob[-a.nx] = v;
         }
-        a.rho_out[self] = r1;
-        if (lo) a.rho_out[self + a.nx] = r1;
-        if (hi) a.rho_out[self - a.nx] = r1;
+        a.rho_out[us] = r1;
+        if (lo) a.rho_out[us + a.nx] = r1;
+        if (hi) a.rho_out[us - a.nx] = r1;
     }
+#undef QPL
+#undef QSRC
 }
 
 // (1) density and flags on x0-8 .. x0+TX+7, y0-7 .. y0+TY+6, four nodes per access; the pads
