@@ -53,6 +53,10 @@ __device__ __forceinline__ double psi_prime<double>(double rho, const StepArgs<d
            2.0 * a.aal * rho;
 }
 
+// correctly rounded reciprocal (hardware approximation plus refinement in FP32)
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Collision in deviation variables g_q = f_q - w_q rho with exact-difference forcing (Eq. 13).
 // MRT: Lallemand-Luo moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy); the equilibrium moments of
 // Eq. 2 minus those of w_q rho are (0, 3 rho u^2, -3 rho u^2, jx, -jx, jy, -jy,
@@ -64,7 +68,7 @@ __device__ __forceinline__ double psi_prime<double>(double rho, const StepArgs<d
 template <typename T>
 __device__ __forceinline__ void collide(T g[9], T rho, T Fx, T Fy, const StepArgs<T>& a,
                                         T& ux, T& uy) {
-    const T inv_rho = (T)1 / rho;
+    const T inv_rho = recip(rho);
     const T jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
     const T jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
     ux = jx * inv_rho;
@@ -124,8 +128,10 @@ struct Layout {
     static constexpr int RW = TX + 16, RH = TY + 14;  // rho / flags: x0-8.., y0-7..
     static constexpr int MW = TX + 6, MH = TY + 6;    // mu: x0-3.., y0-3..
     static constexpr int CW = TX + 2, CH = TY + 2;    // g*: x0-1.., y0-1..
+    // g* holds 9 planes plus one for sum_q w_q rho(x - e_q, t) (the rest-state part of the
+    // next density, formed where the neighbour densities are already in registers)
     static constexpr size_t bytes =
-        sizeof(T) * ((size_t)RW * RH + (size_t)MW * MH + 9 * (size_t)CW * CH) + (size_t)RW * RH;
+        sizeof(T) * ((size_t)RW * RH + (size_t)MW * MH + 10 * (size_t)CW * CH) + (size_t)RW * RH;
 };
 
 // four consecutive elements, global (aligned to 4 elements) to shared
@@ -245,13 +251,17 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
         const T* hb = a.h_in + us;
         T g[9];
         g[0] = __ldg(hb);
+        T A = qw<T>(0) * rho;  // sum_q w_q rho(x - e_q) with bounce-back sources taking rho(x)
 #pragma unroll
         for (int q = 1; q < 9; ++q) {
             const int os = o - qy(q) * RW - qx(q);
             if (!MIXED || s_flag[os] == kFluid) {
-                g[q] = __ldg(hb + (int)QSRC(q)) + qw<T>(q) * (s_rho[os] - rho);
+                const T rs = s_rho[os];
+                g[q] = __ldg(hb + (int)QSRC(q)) + qw<T>(q) * (rs - rho);
+                A += qw<T>(q) * rs;
             } else {
                 g[q] = __ldg(hb + (int)QPL(qopp(q)));
+                A += qw<T>(q) * rho;
             }
         }
         T ux, uy;
@@ -264,6 +274,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
         } else {
 #pragma unroll
             for (int q = 0; q < 9; ++q) s_g[q * CW * CH + idx] = g[q];
+            s_g[9 * CW * CH + idx] = A;
         }
     }
     if (MACRO) return;
@@ -278,17 +289,15 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
         if (MIXED && s_flag[o] != kFluid) continue;
         const int oc = (ty + 1) * CW + (tx + 1);
         const T r0 = s_rho[o];
-        T A = 0, B = 0;
+        const T A = s_g[9 * CW * CH + oc];
+        T B = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int os = o - qy(q) * RW - qx(q);
-            if (!MIXED || q == 0 || s_flag[os] == kFluid) {
+            if (!MIXED || q == 0 || s_flag[os] == kFluid)
                 B += s_g[q * CW * CH + oc - qy(q) * CW - qx(q)];
-                A += qw<T>(q) * s_rho[os];
-            } else {
+            else
                 B += s_g[qopp(q) * CW * CH + oc];
-                A += qw<T>(q) * r0;
-            }
         }
         const T r1 = A + B;
         const unsigned us = (unsigned)lidx(a.P, gx, gy);
@@ -347,7 +356,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
     T* s_rho = reinterpret_cast<T*>(smem);
     T* s_mu = s_rho + RW * RH;
     T* s_g = s_mu + MW * MH;
-    uint8_t* s_flag = reinterpret_cast<uint8_t*>(s_g + 9 * CW * CH);
+    uint8_t* s_flag = reinterpret_cast<uint8_t*>(s_g + 10 * CW * CH);
     const int any = stage_load<T, TX, TY, NT>(a, s_rho, s_flag, x0, y0);
     if (__syncthreads_or(any))
         step_body<T, TX, TY, NT, MACRO, true>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
