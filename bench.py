@@ -35,7 +35,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURE_EVERY = 500
-STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2202_06516_gb300", "csrc", "lbm_step.cu")
+# sources of the step kernel: a committed ncu summary applies only while these are unchanged
+STEP_KERNEL_SRCS = [os.path.join(ROOT, "paper_2202_06516_gb300", "csrc", f)
+                    for f in ("lbm_step.cu", "lbm_step_body.cuh", "lbm_internal.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "k_step_fp32_2048x1024.md")
 BYTES_PER_FLUID_NODE = 80  # 9 x 4 B populations read + written, 4 B density read + written
 
@@ -50,8 +52,11 @@ def _peaks():
 
 
 def _src_hash():
-    with open(STEP_KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for p in STEP_KERNEL_SRCS:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _profiled_traffic():
@@ -269,7 +274,7 @@ def run_cuda(args, rank, world, dist):
     return line
 
 
-def cpu_baseline(steps: int = 60):
+def cpu_baseline(steps: int = 400):
     """The oracle as it stands on the host cores: the same 2048 x 1024 workload, `steps` time
     steps (a bounded sample of the 50k-step run)."""
     import oracle as O
@@ -423,7 +428,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--cpu-steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")

@@ -239,3 +239,45 @@ def test_stream_from_torch(lbm, oracle_mod):
     lbm.lbm_read_fields(a.ctx, lbm.LBM_FIELD_RHO, 96, 64, device_out=(r.data_ptr(), None, None))
     torch.cuda.synchronize()
     assert np.array_equal(r.cpu().numpy().reshape(64, 96), a.rho())
+
+
+# -------------------------------------------------------------------- other model options
+def test_carnahan_starling_bgk_matches_oracle(lbm, oracle_mod):
+    """Second EOS (Carnahan-Starling, Tr = 0.7) with the BGK collision of Eq. 3."""
+    O = oracle_mod
+    mx = O.maxwell(1, 0.7)
+    k2 = 0.05
+    neutral = k2 * mx["mu_sat"]
+    cfg = O.Config(nx=96, ny=64, eos=1, collision=1, Tr=0.7, k2=k2, kappa=0.05, tau=1.0,
+                   rho_g=mx["rho_g"], rho_l=mx["rho_l"], has_circle=1, cx=48, cy=0, R=20,
+                   mu_circle=neutral, mu_bottom=neutral, mu_top=neutral, drop_x=48,
+                   drop_y=20.5 + 14, drop_r=14, drop_W=4.0)
+    ref = O.Sim(cfg)
+    ref.step(300)
+    assert np.isfinite(ref.rho()).all()
+    for prec, tol in ((1, 1e-9), (0, 2e-5)):
+        lat = gpu_lattice(lbm, cfg, precision=prec)
+        lat.step(300)
+        err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+        assert err < tol, (prec, err)
+
+
+def test_striped_wetting_and_pendent_gravity(lbm, oracle_mod):
+    """Heterogeneous (striped) circle wetting with a body force pulling the drop away from the
+    cylinder (pendent arrangement), FP32 vs oracle, 1500 steps."""
+    O = oracle_mod
+    w = W.Workload("stripes", 160, 110, (80.0, 0.0, 35.0), W.tangent_drop(80, 0, 35, 20),
+                   mu_rel_circle=-0.02, stripes=(9.0, 0.03), g=(2e-6, 5e-6))
+    cfg = oracle_config(O, w)[0]
+    ref = O.Sim(cfg)
+    ref.step(1500)
+    lat = gpu_lattice(lbm, cfg)
+    flags, muw, _ = lat.geometry()
+    _, _, _, omuw = ref.ext()
+    assert np.array_equal(muw.astype(np.float32), omuw.astype(np.float32))
+    lat.step(1500)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < 3e-5, err
+    gl, gr = lat.measure()
+    ol, orr, _ = ref.measure()
+    assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
