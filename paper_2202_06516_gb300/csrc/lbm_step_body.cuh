@@ -20,13 +20,18 @@ __device__ __forceinline__ T psi_prime(T rho, const StepArgs<T>& a);
 template <>
 __device__ __forceinline__ float psi_prime<float>(float rho, const StepArgs<float>& a) {
     if (a.eos == LBM_EOS_PR) {
+        // with d1 = 1 - b rho, d2 = sqrt2 + 1 - b rho, n2 = sqrt2 - 1 + b rho the three
+        // divisions of Eq. 11 share one reciprocal, since 1 + 2 b rho - (b rho)^2 = d2 n2
         const float br = a.b * rho;
         const float s2 = 1.41421356f;
-        const float inv = __fdividef(1.0f, 1.0f - br);
-        const float t13 = a.RT * (__logf(rho * inv) + inv);
-        const float t2 = a.aal * __fdividef(1.0f, 2.0f * s2 * a.b) *
-                         __logf(__fdividef(s2 - 1.0f + br, s2 + 1.0f - br));
-        const float t4 = __fdividef(a.aal * rho, 1.0f + 2.0f * br - br * br);
+        const float d1 = 1.0f - br, d2 = s2 + 1.0f - br, n2 = s2 - 1.0f + br;
+        const float dn = d2 * n2;
+        const float r = __fdividef(1.0f, d1 * dn);
+        const float inv_d1 = dn * r;          // 1 / d1
+        const float inv_dn = d1 * r;          // 1 / (d2 n2)
+        const float t13 = a.RT * (__logf(rho * inv_d1) + inv_d1);
+        const float t2 = a.aal * __fdividef(1.0f, 2.0f * s2 * a.b) * __logf(n2 * n2 * inv_dn);
+        const float t4 = a.aal * rho * inv_dn;
         return t13 - t2 - t4;
     }
     const float n = a.b * rho * 0.25f;
@@ -151,6 +156,58 @@ __device__ __forceinline__ T mu_fluid(const T* s_rho, int o, const StepArgs<T>& 
     const T lapy = -s_rho[o + 2 * RW] + (T)16 * s_rho[o + RW] - (T)30 * c0 +
                    (T)16 * s_rho[o - RW] - s_rho[o - 2 * RW];
     return a.k2 * psi_prime<T>(c0, a) - a.kappa * (lapx + lapy) * ((T)1 / (T)12);
+}
+
+// (6) of the step: new density rho(t+1) = sum_q f*_q(x - e_q) (half-way bounce-back where the
+// source is not fluid) and the stored deviations f*_q(x) - w_q rho(t+1)(x). EDGE: the tile lies
+// within kPadX of an x edge and also writes the periodic images into the pads.
+template <typename T, int TX, int TY, int NT, bool MIXED, bool EDGE>
+__device__ __forceinline__ void stream_out(const StepArgs<T>& a, const T* s_rho, const T* s_g,
+                                           const uint8_t* s_flag, int x0, int y0) {
+    using L = Layout<T, TX, TY>;
+    constexpr int RW = L::RW, CW = L::CW, CH = L::CH;
+    const unsigned upl = (unsigned)a.plane;
+    for (int idx = threadIdx.x; idx < TX * TY; idx += NT) {
+        const int ty = idx / TX, tx = idx - ty * TX;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (MIXED && (gx >= a.nx || gy >= a.ny)) continue;
+        const int o = (ty + 7) * RW + (tx + 8);
+        if (MIXED && s_flag[o] != kFluid) continue;
+        const int oc = (ty + 1) * CW + (tx + 1);
+        const T r0 = s_rho[o];
+        const T A = s_g[9 * CW * CH + oc];
+        T B = 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int os = o - qy(q) * RW - qx(q);
+            if (!MIXED || q == 0 || s_flag[os] == kFluid)
+                B += s_g[q * CW * CH + oc - qy(q) * CW - qx(q)];
+            else
+                B += s_g[qopp(q) * CW * CH + oc];
+        }
+        const T r1 = A + B;
+        const unsigned us = (unsigned)lidx(a.P, gx, gy);
+        const T dr = r0 - r1;
+        if (EDGE) {
+            const bool lo = gx < kPadX, hi = gx >= a.nx - kPadX;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const T v = s_g[q * CW * CH + oc] + qw<T>(q) * dr;
+                T* ob = a.h_out + us + (unsigned)q * upl;
+                ob[0] = v;
+                if (lo) ob[a.nx] = v;
+                if (hi) ob[-a.nx] = v;
+            }
+            a.rho_out[us] = r1;
+            if (lo) a.rho_out[us + a.nx] = r1;
+            if (hi) a.rho_out[us - a.nx] = r1;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                a.h_out[us + (unsigned)q * upl] = s_g[q * CW * CH + oc] + qw<T>(q) * dr;
+            a.rho_out[us] = r1;
+        }
+    }
 }
 
 // MIXED: the tile and its halo contain non-fluid nodes (walls, the disc, the domain edge), so
@@ -280,41 +337,12 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
     if (MACRO) return;
     __syncthreads();
 
-    // (6) streaming into the tile: new density and deviations (and their periodic images)
-    for (int idx = tid; idx < TX * TY; idx += NT) {
-        const int ty = idx / TX, tx = idx - ty * TX;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (MIXED && (gx >= a.nx || gy >= a.ny)) continue;
-        const int o = (ty + 7) * RW + (tx + 8);
-        if (MIXED && s_flag[o] != kFluid) continue;
-        const int oc = (ty + 1) * CW + (tx + 1);
-        const T r0 = s_rho[o];
-        const T A = s_g[9 * CW * CH + oc];
-        T B = 0;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int os = o - qy(q) * RW - qx(q);
-            if (!MIXED || q == 0 || s_flag[os] == kFluid)
-                B += s_g[q * CW * CH + oc - qy(q) * CW - qx(q)];
-            else
-                B += s_g[qopp(q) * CW * CH + oc];
-        }
-        const T r1 = A + B;
-        const unsigned us = (unsigned)lidx(a.P, gx, gy);
-        const bool lo = gx < kPadX, hi = gx >= a.nx - kPadX;
-        const T dr = r0 - r1;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const T v = s_g[q * CW * CH + oc] + qw<T>(q) * dr;
-            T* ob = a.h_out + us + QPL(q);
-            ob[0] = v;
-            if (lo) ob[a.nx] = v;
-            if (hi) ob[-a.nx] = v;
-        }
-        a.rho_out[us] = r1;
-        if (lo) a.rho_out[us + a.nx] = r1;
-        if (hi) a.rho_out[us - a.nx] = r1;
-    }
+    // (6) streaming into the tile: new density and deviations; tiles within kPadX of the x
+    // edges also refresh the periodic images in the pads (a CTA-uniform branch)
+    if (x0 < kPadX || x0 + TX > a.nx - kPadX)
+        stream_out<T, TX, TY, NT, MIXED, true>(a, s_rho, s_g, s_flag, x0, y0);
+    else
+        stream_out<T, TX, TY, NT, MIXED, false>(a, s_rho, s_g, s_flag, x0, y0);
 #undef QPL
 #undef QSRC
 }
