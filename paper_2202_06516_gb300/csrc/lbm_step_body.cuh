@@ -62,6 +62,18 @@ __device__ __forceinline__ double psi_prime<double>(double rho, const StepArgs<d
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Explicitly rounded operations: the collision is written with them so that its rounding does
+// not depend on where the compiler fuses a multiply into an add (which can differ between the
+// kernels that inline it), and the single-lattice and batched kernels stay bit-identical.
+__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
+__device__ __forceinline__ float sub_rn(float x, float y) { return __fsub_rn(x, y); }
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ float fma_rn(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+__device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
+__device__ __forceinline__ double sub_rn(double x, double y) { return __dsub_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+__device__ __forceinline__ double fma_rn(double x, double y, double z) { return __fma_rn(x, y, z); }
+
 // Collision in deviation variables g_q = f_q - w_q rho with exact-difference forcing (Eq. 13).
 // MRT: Lallemand-Luo moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy); the equilibrium moments of
 // Eq. 2 minus those of w_q rho are (0, 3 rho u^2, -3 rho u^2, jx, -jx, jy, -jy,
@@ -74,11 +86,17 @@ template <typename T>
 __device__ __forceinline__ void collide(T g[9], T rho, T Fx, T Fy, const StepArgs<T>& a,
                                         T& ux, T& uy) {
     const T inv_rho = recip(rho);
-    const T jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
-    const T jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
-    ux = jx * inv_rho;
-    uy = jy * inv_rho;
-    const T uu = ux * ux + uy * uy;
+    // sums and differences of opposite (axis) and mirrored (diagonal) pairs
+    const T s13 = add_rn(g[1], g[3]), s24 = add_rn(g[2], g[4]);
+    const T d13 = sub_rn(g[1], g[3]), d24 = sub_rn(g[2], g[4]);
+    const T s57 = add_rn(g[5], g[7]), s68 = add_rn(g[6], g[8]);
+    const T e57 = sub_rn(g[5], g[7]), e86 = sub_rn(g[8], g[6]);
+    const T jx = add_rn(d13, add_rn(e57, e86));
+    const T jy = add_rn(d24, sub_rn(e57, e86));
+    ux = mul_rn(jx, inv_rho);
+    uy = mul_rn(jy, inv_rho);
+    const T uxx = mul_rn(ux, ux), uyy = mul_rn(uy, uy), uxy = mul_rn(ux, uy);
+    const T uu = add_rn(uxx, uyy);
     if (a.bgk) {
         const T sx = (T)2 * ux + Fx * inv_rho, sy = (T)2 * uy + Fy * inv_rho;
         const T Fs = Fx * sx + Fy * sy;
@@ -94,38 +112,48 @@ __device__ __forceinline__ void collide(T g[9], T rho, T Fx, T Fy, const StepArg
         return;
     }
     // forced velocity and the moment increments of the forcing term
-    const T vx = ux + Fx * inv_rho, vy = uy + Fy * inv_rho;
-    const T dE = (T)3 * rho * (vx * vx + vy * vy - uu);
-    const T dP = rho * ((vx * vx - vy * vy) - (ux * ux - uy * uy));
-    const T dQ = rho * (vx * vy - ux * uy);
-    const T axis = g[1] + g[2] + g[3] + g[4];
-    const T diag = g[5] + g[6] + g[7] + g[8];
-    const T m1 = (T)-4 * g[0] - axis + (T)2 * diag;
-    const T m2 = (T)4 * g[0] - (T)2 * axis + diag;
-    const T m4 = (T)-2 * g[1] + (T)2 * g[3] + g[5] - g[6] - g[7] + g[8];
-    const T m6 = (T)-2 * g[2] + (T)2 * g[4] + g[5] + g[6] - g[7] - g[8];
-    const T m7 = g[1] - g[2] + g[3] - g[4];
-    const T m8 = g[5] - g[6] + g[7] - g[8];
+    const T vx = fma_rn(Fx, inv_rho, ux), vy = fma_rn(Fy, inv_rho, uy);
+    const T vxx = mul_rn(vx, vx), vyy = mul_rn(vy, vy), vxy = mul_rn(vx, vy);
+    const T r3 = mul_rn((T)3, rho);
+    const T pu = sub_rn(uxx, uyy);
+    const T dE = mul_rn(r3, sub_rn(add_rn(vxx, vyy), uu));
+    const T dP = mul_rn(rho, sub_rn(sub_rn(vxx, vyy), pu));
+    const T dQ = mul_rn(rho, sub_rn(vxy, uxy));
+    // non-conserved moments (Lallemand-Luo order)
+    const T axis = add_rn(s13, s24), diag = add_rn(s57, s68);
+    const T m1 = fma_rn((T)-4, g[0], fma_rn((T)2, diag, -axis));  // e
+    const T m2 = fma_rn((T)4, g[0], fma_rn((T)-2, axis, diag));   // eps
+    const T m4 = fma_rn((T)-3, d13, jx);                          // qx
+    const T m6 = fma_rn((T)-3, d24, jy);                          // qy
+    const T m7 = sub_rn(s13, s24);                                // pxx
+    const T m8 = sub_rn(s57, s68);                                // pxy
     // a_k = (S_k (m_k - m_eq,k) - dM_k) / |M_k|^2
-    const T a1 = (a.s_e * (m1 - (T)3 * rho * uu) - dE) * ((T)1 / (T)36);
-    const T a2 = (a.s_eps * (m2 + (T)3 * rho * uu) + dE) * ((T)1 / (T)36);
-    const T a3 = -Fx * ((T)1 / (T)6);
-    const T a5 = -Fy * ((T)1 / (T)6);
-    const T a4 = (a.s_q * (m4 + jx) + Fx) * ((T)1 / (T)12);
-    const T a6 = (a.s_q * (m6 + jy) + Fy) * ((T)1 / (T)12);
-    const T a7 = (a.s_v * (m7 - rho * (ux * ux - uy * uy)) - dP) * (T)0.25;
-    const T a8 = (a.s_v * (m8 - rho * ux * uy) - dQ) * (T)0.25;
-    const T c_ax = -a1 - (T)2 * a2;
-    const T c_dg = (T)2 * a1 + a2;
-    g[0] -= (T)-4 * a1 + (T)4 * a2;
-    g[1] -= c_ax + a3 - (T)2 * a4 + a7;
-    g[2] -= c_ax + a5 - (T)2 * a6 - a7;
-    g[3] -= c_ax - a3 + (T)2 * a4 + a7;
-    g[4] -= c_ax - a5 + (T)2 * a6 - a7;
-    g[5] -= c_dg + a3 + a5 + a4 + a6 + a8;
-    g[6] -= c_dg - a3 + a5 - a4 + a6 - a8;
-    g[7] -= c_dg - a3 - a5 - a4 - a6 + a8;
-    g[8] -= c_dg + a3 - a5 + a4 - a6 - a8;
+    const T ruu3 = mul_rn(r3, uu);
+    const T a1 = mul_rn(fma_rn(a.s_e, sub_rn(m1, ruu3), -dE), (T)1 / (T)36);
+    const T a2 = mul_rn(fma_rn(a.s_eps, add_rn(m2, ruu3), dE), (T)1 / (T)36);
+    const T a3 = mul_rn(Fx, (T)-1 / (T)6);
+    const T a5 = mul_rn(Fy, (T)-1 / (T)6);
+    const T a4 = mul_rn(fma_rn(a.s_q, add_rn(m4, jx), Fx), (T)1 / (T)12);
+    const T a6 = mul_rn(fma_rn(a.s_q, add_rn(m6, jy), Fy), (T)1 / (T)12);
+    const T a7 = mul_rn(fma_rn(a.s_v, fma_rn(-rho, pu, m7), -dP), (T)0.25);
+    const T a8 = mul_rn(fma_rn(a.s_v, fma_rn(-rho, uxy, m8), -dQ), (T)0.25);
+    // back-transform M^-1 a, grouped by pairs: g_q -= sum_k M_kq a_k
+    const T c_ax = fma_rn((T)-2, a2, -a1);
+    const T c_dg = fma_rn((T)2, a1, a2);
+    g[0] = fma_rn((T)4, sub_rn(a1, a2), g[0]);
+    const T S13 = add_rn(c_ax, a7), D13 = fma_rn((T)-2, a4, a3);
+    const T S24 = sub_rn(c_ax, a7), D24 = fma_rn((T)-2, a6, a5);
+    g[1] = sub_rn(g[1], add_rn(S13, D13));
+    g[3] = sub_rn(g[3], sub_rn(S13, D13));
+    g[2] = sub_rn(g[2], add_rn(S24, D24));
+    g[4] = sub_rn(g[4], sub_rn(S24, D24));
+    const T p34 = add_rn(a3, a4), p56 = add_rn(a5, a6);
+    const T S57 = add_rn(c_dg, a8), S68 = sub_rn(c_dg, a8);
+    const T D57 = add_rn(p34, p56), D68 = sub_rn(p56, p34);
+    g[5] = sub_rn(g[5], add_rn(S57, D57));
+    g[7] = sub_rn(g[7], sub_rn(S57, D57));
+    g[6] = sub_rn(g[6], add_rn(S68, D68));
+    g[8] = sub_rn(g[8], sub_rn(S68, D68));
 }
 
 template <typename T, int TX, int TY>
