@@ -41,6 +41,7 @@ enum { LBM_FP32 = 0, LBM_FP64 = 1 };          /* storage and arithmetic type of 
 enum { LBM_EOS_PR = 0, LBM_EOS_CS = 1 };      /* Peng-Robinson (Eq. 10) or Carnahan-Starling */
 enum { LBM_MRT = 0, LBM_BGK = 1 };            /* collision of Eq. 1 or Eq. 3 */
 enum { LBM_FLUID = 0, LBM_LAYER1 = 1, LBM_LAYER2 = 2, LBM_SOLID = 3 }; /* node classes */
+enum { LBM_TILE_AUTO = -1 };                  /* lbm_params.tile_x: choose by autotuning */
 
 /* Model parameters (lattice units).
  *  k2, kappa: k^2 and kappa-hat of the mesh-space chemical potential, Eq. 12.
@@ -52,6 +53,8 @@ enum { LBM_FLUID = 0, LBM_LAYER1 = 1, LBM_LAYER2 = 2, LBM_SOLID = 3 }; /* node c
  *    budget is fitted to (0 = no constraint); all three 0 selects 32x16/5 in FP32 and 32x16/0 in
  *    FP64. Supported (tile/min_blocks):
  *    FP32 32x8/0, 32x8/6, 32x16/0, 32x16/5, 32x16/6, 64x16/0, 32x32/0; FP64 32x8/0, 32x16/0.
+ *    tile_x = LBM_TILE_AUTO: start with the default and let lbm_autotune pick the variant at the
+ *    first lbm_step (for lbm_batch_create: lbm_batch_autotune at the first lbm_batch_run).
  *  stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or NULL. */
 typedef struct lbm_params {
     int32_t nx, ny;
@@ -171,6 +174,25 @@ lbm_status lbm_read_candidates(lbm_ctx *ctx, int64_t *ids, double *pxyd, int64_t
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 
+/* One timed step-kernel variant: tile shape, register budget (CTAs per SM, 0 = none) and the
+ * mean device time of one step over the trial, in microseconds. */
+typedef struct lbm_tune_entry {
+    int32_t tile_x, tile_y, min_blocks;
+    double us_per_step;
+} lbm_tune_entry;
+
+/* Step-kernel autotuner (no counterpart in the paper; it only picks among launch shapes that
+ * compute the same step). Times every compiled variant of the lattice's precision over
+ * trial_steps launches (after 2 untimed ones) with CUDA events on the lattice's stream, on the
+ * lattice's own geometry and state, and keeps the fastest; later lbm_step calls (and their
+ * captured graphs) use it. The trial launches read the current populations and write the other
+ * ping-pong buffer without advancing, so the simulation state and step count are unchanged.
+ * entries (may be NULL) receives up to max_entries timings in variant order, *n_out (may be NULL)
+ * the number of variants timed. LBM_ERR_STATE before lbm_set_geometry, LBM_ERR_ARG for
+ * trial_steps < 1. Synchronous. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trial_steps, lbm_tune_entry *entries,
+                        int32_t max_entries, int32_t *n_out);
+
 /* Allocation-free variant of lbm_mass for a caller-owned FP32 density field.
  * For callers that must not allocate device memory at this point: a framework that owns every
  * device byte through its own pool, code that cannot afford the implicit device synchronisation
@@ -202,9 +224,11 @@ lbm_status lbm_mass_noalloc(const float *rho, const uint8_t *flags, int32_t nx, 
  * ------------------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch; /* opaque; owns n lattices, their stream and tile tables */
 
-/* Create n lattices of sizes nx[i] x ny[i] sharing the model parameters (model->nx, ny, tile_x,
- * tile_y, min_blocks and stream are ignored; precision must be LBM_FP32). Every instance is an
- * lbm_ctx on the batch's private stream. On failure *out is NULL and nothing is leaked. */
+/* Create n lattices of sizes nx[i] x ny[i] sharing the model parameters (model->nx, ny, tile_y,
+ * min_blocks and stream are ignored; precision must be LBM_FP32; model->tile_x = LBM_TILE_AUTO
+ * autotunes the batch kernel at the first lbm_batch_run, any other value starts with the
+ * default 32x16 tiles). Every instance is an lbm_ctx on the batch's private stream. On failure
+ * *out is NULL and nothing is leaked. */
 lbm_status lbm_batch_create(const lbm_params *model, int32_t n, const int32_t *nx,
                             const int32_t *ny, lbm_batch **out);
 
@@ -221,6 +245,15 @@ lbm_status lbm_batch_set_geometry(lbm_batch *b, int32_t i, const lbm_geometry *g
 lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int32_t check_every, double tol,
                          double angle_tol, int64_t *steps_out, int32_t *converged_out,
                          double *residual_out);
+
+/* Autotuner of the batched kernel: times each compiled tile variant of the persistent kernel
+ * (FP32 32x8, 32x16, 64x16, 32x32, each with its register budget) over trial_steps launches on
+ * the tile table of the instances that have geometry (those sharing the parity of the first), and
+ * keeps the fastest for later lbm_batch_run calls. As in lbm_autotune the trial launches do not
+ * advance any instance. entries / n_out as in lbm_autotune. LBM_ERR_STATE if no instance has
+ * geometry. Synchronous. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trial_steps, lbm_tune_entry *entries,
+                              int32_t max_entries, int32_t *n_out);
 
 /* Contact angles of every instance (out[2 i], out[2 i + 1] = left, right), as
  * lbm_measure_contact_angle. Returns LBM_ERR_NO_CONTACT if any side of any instance failed. */

@@ -265,10 +265,13 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     double co[4];
     if (!(p->Tr > 0 && p->Tr < 1) || !coexistence(he, co))
         return fail(nullptr, LBM_ERR_ARG, "lbm_create: no coexistence at this Tr");
-    const int tx = p->tile_x ? p->tile_x : 32, ty = p->tile_y ? p->tile_y : 16;
+    const bool tile_auto = p->tile_x == LBM_TILE_AUTO;
+    const bool tile_default = tile_auto || (!p->tile_x && !p->tile_y && !p->min_blocks);
+    const int tx = tile_default || !p->tile_x ? 32 : p->tile_x;
+    const int ty = tile_default || !p->tile_y ? 16 : p->tile_y;
     const size_t esz = p->precision == LBM_FP32 ? 4 : 8;
     // default variant: FP32 32x16 fitted to 5 CTAs per SM (measured fastest on GB300)
-    const int min_blocks = (!p->tile_x && !p->tile_y && !p->min_blocks && esz == 4) ? 5 : p->min_blocks;
+    const int min_blocks = tile_default ? (esz == 4 ? 5 : 0) : p->min_blocks;
     if (lbm::step_smem_bytes(tx, ty, esz, min_blocks) == 0)
         return fail(nullptr, LBM_ERR_ARG,
                     "lbm_create: unsupported (tile, min_blocks) variant for this precision");
@@ -300,6 +303,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->tile_x = tx;
     c->tile_y = ty;
     c->min_blocks = min_blocks;
+    c->autotune_pending = tile_auto;
     c->eosc.eos = p->eos;
     c->eosc.RT = he.R * he.T;
     c->eosc.aal = he.a * he.al;
@@ -410,6 +414,11 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "lbm_step: nsteps < 0");
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_step: call lbm_set_geometry first");
     DeviceGuard dg(c->device);
+    if (c->autotune_pending && nsteps > 0) {
+        c->autotune_pending = false;
+        const lbm_status st = lbm_autotune(c, lbm::kAutotuneTrial, nullptr, 0, nullptr);
+        if (st != LBM_OK) return st;
+    }
     int64_t left = nsteps;
     if (left >= lbm::kGraphChunk && !c->graph[c->cur] && !c->graph_failed) capture_graph(c, c->cur);
     while (left >= lbm::kGraphChunk && c->graph[c->cur]) {
@@ -421,6 +430,65 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
         c->cur ^= 1;
     }
     c->steps += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, lbm_tune_entry* entries,
+                        int32_t max_entries, int32_t* n_out) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_autotune: ctx is NULL");
+    if (trial_steps < 1) return fail(c, LBM_ERR_ARG, "lbm_autotune: trial_steps < 1");
+    if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_autotune: call lbm_set_geometry first");
+    DeviceGuard dg(c->device);
+    std::vector<lbm::StepVariant> vs;
+    lbm::step_variants(c->esz, &vs);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LBM_CUDA(c, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        LBM_CUDA(c, ce);
+    }
+    const lbm::StepVariant keep{c->tile_x, c->tile_y, c->min_blocks};
+    int best = -1;
+    double best_us = 0;
+    cudaError_t err = cudaSuccess;
+    for (size_t i = 0; i < vs.size() && err == cudaSuccess; ++i) {
+        c->tile_x = vs[i].tile_x;
+        c->tile_y = vs[i].tile_y;
+        c->min_blocks = vs[i].min_blocks;
+        err = lbm::step_configure(c);
+        // every launch reads buffer cur and writes buffer cur ^ 1: the state does not advance
+        for (int w = 0; w < 2 && err == cudaSuccess; ++w) err = lbm::launch_step(c, c->cur, false);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < trial_steps && err == cudaSuccess; ++s)
+            err = lbm::launch_step(c, c->cur, false);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) break;
+        const double us = 1e3 * (double)ms / trial_steps;
+        if (entries && (int32_t)i < max_entries)
+            entries[i] = lbm_tune_entry{vs[i].tile_x, vs[i].tile_y, vs[i].min_blocks, us};
+        if (best < 0 || us < best_us) {
+            best = (int)i;
+            best_us = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const lbm::StepVariant pick = (err == cudaSuccess && best >= 0) ? vs[best] : keep;
+    c->tile_x = pick.tile_x;
+    c->tile_y = pick.tile_y;
+    c->min_blocks = pick.min_blocks;
+    LBM_CUDA(c, err);
+    LBM_CUDA(c, lbm::step_configure(c));
+    // the captured graphs hold the previous variant
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+    }
+    if (n_out) *n_out = (int32_t)vs.size();
     return LBM_OK;
 }
 

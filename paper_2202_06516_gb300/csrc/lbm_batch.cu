@@ -39,6 +39,9 @@ struct lbm_batch {
     std::vector<size_t> snap_off;
     int max_tiles = 0;
     int grid = 0;
+    int variant = 0;              // index into the compiled tile variants
+    int tx = 32, ty = 16;         // its tile shape
+    bool autotune_pending = false;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     int graph_parity = -1;
@@ -51,7 +54,13 @@ namespace {
 
 using namespace stepdev;
 
-constexpr int TXB = 32, TYB = 16, NTB = 256, MINBB = 5;
+constexpr int NTB = 256;
+
+// Compiled tile variants of the persistent kernel: tile (TX, TY) and the CTAs per SM its
+// register budget is fitted to. Variant 1 (32 x 16, 5 CTAs/SM) is the default; the autotuner
+// times all of them on the batch's own tile table.
+#define LBM_BATCH_VARIANTS(X) X(32, 8, 5) X(32, 16, 5) X(64, 16, 3) X(32, 32, 3)
+constexpr int kBatchDefaultVariant = 1;
 
 struct BatchInst {
     float* h[2];
@@ -59,11 +68,12 @@ struct BatchInst {
     const uint8_t* flags;
     const float* muw;
     float* snap;
-    int nx, ny, P, plane, tiles_x;
+    int nx, ny, P, plane;
     float rho_mid;
 };
 
-__global__ void __launch_bounds__(NTB, MINBB)
+template <int TX, int TY, int MINB>
+__global__ void __launch_bounds__(NTB, MINB)
     k_batch_step(const StepArgs<float> model, const BatchInst* inst, const int2* tiles,
                  const int* n_tiles, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -82,8 +92,9 @@ __global__ void __launch_bounds__(NTB, MINBB)
         a.ny = I.ny;
         a.P = I.P;
         a.plane = I.plane;
-        const int ty = e.y / I.tiles_x, tx = e.y - ty * I.tiles_x;
-        step_tile<float, TXB, TYB, NTB, false>(a, I.rho_mid, smem_raw, tx * TXB, ty * TYB);
+        const int tiles_x = (I.nx + TX - 1) / TX;
+        const int ty = e.y / tiles_x, tx = e.y - ty * tiles_x;
+        step_tile<float, TX, TY, NTB, false>(a, I.rho_mid, smem_raw, tx * TX, ty * TY);
         __syncthreads();  // the next tile reuses shared memory
     }
 }
@@ -142,7 +153,56 @@ lbm_status bfail(lbm_batch* b, lbm_status st, const std::string& msg) {
             return bfail((b), LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-int tiles_of(const lbm_ctx* c) { return ((c->nx + TXB - 1) / TXB) * ((c->ny + TYB - 1) / TYB); }
+int tiles_of(const lbm_ctx* c, int tx, int ty) {
+    return ((c->nx + tx - 1) / tx) * ((c->ny + ty - 1) / ty);
+}
+int tiles_of(const lbm_batch* b, const lbm_ctx* c) { return tiles_of(c, b->tx, b->ty); }
+
+int num_variants() {
+    int n = 0;
+#define X(A, B, M) ++n;
+    LBM_BATCH_VARIANTS(X)
+#undef X
+    return n;
+}
+
+// select variant v: shared-memory attribute, tile shape and the persistent grid (resident CTAs
+// per SM x SMs)
+cudaError_t configure_variant(lbm_batch* b, int v) {
+    int i = 0, per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define X(A, B, M)                                                                           \
+    if (v == i++) {                                                                          \
+        const int bytes = (int)Layout<float, A, B>::bytes;                                   \
+        e = cudaFuncSetAttribute(k_batch_step<A, B, M>,                                      \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);        \
+        if (e == cudaSuccess)                                                                \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<A, B, M>, \
+                                                              NTB, bytes);                   \
+        b->tx = A;                                                                           \
+        b->ty = B;                                                                           \
+    }
+    LBM_BATCH_VARIANTS(X)
+#undef X
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    b->variant = v;
+    b->grid = (per_sm > 0 ? per_sm : 1) * sms;
+    return cudaSuccess;
+}
+
+void variant_shape(int v, int* tx, int* ty, int* minb) {
+    int i = 0;
+#define X(A, B, M)  \
+    if (v == i++) { \
+        *tx = A;    \
+        *ty = B;    \
+        *minb = M;  \
+    }
+    LBM_BATCH_VARIANTS(X)
+#undef X
+}
 
 lbm_status upload_desc(lbm_batch* b) {
     std::vector<BatchInst> d(b->n);
@@ -160,7 +220,6 @@ lbm_status upload_desc(lbm_batch* b) {
         I.ny = c->ny;
         I.P = c->P;
         I.plane = (int)c->plane;
-        I.tiles_x = (c->nx + TXB - 1) / TXB;
         I.rho_mid = (float)(0.5 * (c->rho_g + c->rho_l));
     }
     BCUDA(b, cudaMemcpyAsync(b->d_desc, d.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice,
@@ -176,7 +235,7 @@ lbm_status upload_tiles(lbm_batch* b, int p, int* ntiles, std::vector<int>* act)
     for (int i = 0; i < b->n; ++i) {
         if (!b->running[i] || b->cur[i] != p) continue;
         act->push_back(i);
-        const int k = tiles_of(b->inst[i]);
+        const int k = tiles_of(b, b->inst[i]);
         for (int q = 0; q < k; ++q) t.push_back(make_int2(i, q));
     }
     *ntiles = (int)t.size();
@@ -193,9 +252,16 @@ lbm_status upload_tiles(lbm_batch* b, int p, int* ntiles, std::vector<int>* act)
 }
 
 cudaError_t launch_batch_step(lbm_batch* b, int parity) {
-    k_batch_step<<<b->grid, NTB, Layout<float, TXB, TYB>::bytes, b->stream>>>(
-        b->model, (const BatchInst*)b->d_desc, b->d_tiles, b->d_ntiles, parity);
-    return cudaGetLastError();
+    int i = 0;
+#define X(A, B, M)                                                                           \
+    if (b->variant == i++) {                                                                 \
+        k_batch_step<A, B, M><<<b->grid, NTB, Layout<float, A, B>::bytes, b->stream>>>(      \
+            b->model, (const BatchInst*)b->d_desc, b->d_tiles, b->d_ntiles, parity);         \
+        return cudaGetLastError();                                                           \
+    }
+    LBM_BATCH_VARIANTS(X)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
 lbm_status capture(lbm_batch* b, int chunk, int parity) {
@@ -270,9 +336,9 @@ lbm_status lbm_batch_create(const lbm_params* model, int32_t n, const int32_t* n
         lbm_params p = *model;
         p.nx = nx[i];
         p.ny = ny[i];
-        p.tile_x = TXB;
-        p.tile_y = TYB;
-        p.min_blocks = MINBB;
+        p.tile_x = 32;
+        p.tile_y = 16;
+        p.min_blocks = 5;
         p.stream = b->stream;
         lbm_ctx* c = nullptr;
         lbm_status st = lbm_create(&p, &c);
@@ -282,7 +348,13 @@ lbm_status lbm_batch_create(const lbm_params* model, int32_t n, const int32_t* n
         b->inst.push_back(c);
         b->snap_off.push_back(snap_total);
         snap_total += c->plane;
-        b->max_tiles += tiles_of(c);
+        int most = 0;
+        for (int v = 0; v < num_variants(); ++v) {
+            int vx = 0, vy = 0, vm = 0;
+            variant_shape(v, &vx, &vy, &vm);
+            most = std::max(most, tiles_of(c, vx, vy));
+        }
+        b->max_tiles += most;
     }
     b->cur.assign(n, 0);
     b->steps.assign(n, 0);
@@ -295,17 +367,10 @@ lbm_status lbm_batch_create(const lbm_params* model, int32_t n, const int32_t* n
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_res, sizeof(double) * 2 * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->snap, sizeof(float) * snap_total);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->snap, 0, sizeof(float) * snap_total, b->stream);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Layout<float, TXB, TYB>::bytes);
-    int per_sm = 0, sms = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step, NTB,
-                                                          Layout<float, TXB, TYB>::bytes);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = configure_variant(b, kBatchDefaultVariant);
     if (e != cudaSuccess)
         return cleanup(LBM_ERR_CUDA, std::string("lbm_batch_create: ") + cudaGetErrorString(e));
-    b->grid = (per_sm > 0 ? per_sm : 1) * sms;
+    b->autotune_pending = model->tile_x == LBM_TILE_AUTO;
     // model part of the step arguments (per-instance fields are filled in the kernel)
     lbm_ctx* c0 = b->inst[0];
     StepArgs<float>& a = b->model;
@@ -348,6 +413,15 @@ lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, d
     if (max_steps < 0 || check_every < 2 || (check_every & 1))
         return bfail(b, LBM_ERR_ARG, "lbm_batch_run: need max_steps >= 0 and an even check_every >= 2");
     BCUDA(b, cudaSetDevice(b->inst[0]->device));
+    if (b->autotune_pending) {
+        bool any = false;
+        for (int i = 0; i < b->n; ++i) any = any || b->has_geom[i];
+        if (any) {
+            b->autotune_pending = false;
+            const lbm_status ts = lbm_batch_autotune(b, kAutotuneTrial, nullptr, 0, nullptr);
+            if (ts != LBM_OK) return ts;
+        }
+    }
     std::vector<int> conv(b->n, 0);
     std::vector<double> resid(b->n, -1.0);
     std::vector<double> last_theta(2 * b->n, -1.0);
@@ -449,6 +523,68 @@ lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, d
         if (converged_out) converged_out[i] = conv[i];
         if (residual_out) residual_out[i] = resid[i];
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, lbm_tune_entry* entries,
+                              int32_t max_entries, int32_t* n_out) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_autotune: batch is NULL");
+    if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "lbm_batch_autotune: trial_steps < 1");
+    BCUDA(b, cudaSetDevice(b->inst[0]->device));
+    // the instances with geometry that share the parity of the first one
+    int parity = -1;
+    for (int i = 0; i < b->n; ++i)
+        if (b->has_geom[i] && parity < 0) parity = b->cur[i];
+    if (parity < 0) return bfail(b, LBM_ERR_STATE, "lbm_batch_autotune: no instance has geometry");
+    const std::vector<int> keep_running = b->running;
+    for (int i = 0; i < b->n; ++i) b->running[i] = b->has_geom[i] && b->cur[i] == parity;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    const int keep = b->variant;
+    int best = -1;
+    double best_us = 0;
+    lbm_status st = LBM_OK;
+    std::vector<int> act;
+    for (int v = 0; v < num_variants() && err == cudaSuccess && st == LBM_OK; ++v) {
+        err = configure_variant(b, v);
+        if (err != cudaSuccess) break;
+        int ntiles = 0;
+        st = upload_tiles(b, parity, &ntiles, &act);
+        if (st != LBM_OK) break;
+        // every launch reads buffer `parity` and writes the other one: nothing advances
+        for (int w = 0; w < 2 && err == cudaSuccess; ++w) err = launch_batch_step(b, parity);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < trial_steps && err == cudaSuccess; ++k)
+            err = launch_batch_step(b, parity);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) break;
+        const double us = 1e3 * (double)ms / trial_steps;
+        int vx = 0, vy = 0, vm = 0;
+        variant_shape(v, &vx, &vy, &vm);
+        if (entries && v < max_entries) entries[v] = lbm_tune_entry{vx, vy, vm, us};
+        if (best < 0 || us < best_us) {
+            best = v;
+            best_us = us;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->running = keep_running;
+    const cudaError_t ce = configure_variant(b, (err == cudaSuccess && st == LBM_OK && best >= 0)
+                                                    ? best : keep);
+    if (st != LBM_OK) return st;
+    BCUDA(b, err);
+    BCUDA(b, ce);
+    // the captured graph was built for the previous tile table
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_chunk = 0;
+    b->graph_parity = -1;
+    if (n_out) *n_out = num_variants();
     return LBM_OK;
 }
 

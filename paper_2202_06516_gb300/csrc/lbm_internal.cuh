@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 
@@ -120,6 +121,7 @@ struct lbm_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
     int tile_x = 32, tile_y = 16, min_blocks = 0;
+    bool autotune_pending = false;  // LBM_TILE_AUTO: tune at the first lbm_step
     std::string err;
 };
 
@@ -127,12 +129,18 @@ namespace lbm {
 
 constexpr int kGraphChunk = 64;   // steps per captured graph (even: ping-pong parity preserved)
 constexpr int kRedThreads = 256;
+constexpr int kAutotuneTrial = 20;  // timed launches per variant when LBM_TILE_AUTO tunes
 
 // launchers (return the CUDA error of the launch)
 cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g);
 cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& g, const double* d_rho0);
 cudaError_t launch_step(lbm_ctx* c, int src, bool macro);
 size_t step_smem_bytes(int tile_x, int tile_y, size_t esz, int min_blocks);
+struct StepVariant {
+    int tile_x, tile_y, min_blocks;
+};
+// the compiled step-kernel variants for element size esz (4: FP32, 8: FP64)
+void step_variants(size_t esz, std::vector<StepVariant>* out);
 cudaError_t step_configure(lbm_ctx* c);
 cudaError_t launch_reduce(lbm_ctx* c);
 cudaError_t launch_measure(lbm_ctx* c);

@@ -101,6 +101,14 @@ size_t step_smem_bytes(int tx, int ty, size_t esz, int min_blocks) {
     return 0;
 }
 
+void step_variants(size_t esz, std::vector<StepVariant>* out) {
+    out->clear();
+#define X(T, A, B, M) \
+    if (esz == sizeof(T)) out->push_back(StepVariant{A, B, M == 1 ? 0 : M});
+    LBM_STEP_VARIANTS(X)
+#undef X
+}
+
 cudaError_t step_configure(lbm_ctx* c) {
 #define X(T, A, B, M) \
     if (c->esz == sizeof(T) && c->tile_x == A && c->tile_y == B && minb_of(c) == M) \

@@ -19,6 +19,7 @@ LBM_FP32, LBM_FP64 = 0, 1
 LBM_EOS_PR, LBM_EOS_CS = 0, 1
 LBM_MRT, LBM_BGK = 0, 1
 LBM_FIELD_RHO, LBM_FIELD_VEL, LBM_FIELD_DEVICE_DST = 1, 2, 4
+LBM_TILE_AUTO = -1
 
 
 class LbmError(RuntimeError):
@@ -61,6 +62,11 @@ class lbm_info(C.Structure):
                 ("precision", C.c_int32), ("min_blocks", C.c_int32)]
 
 
+class lbm_tune_entry(C.Structure):
+    _fields_ = [("tile_x", C.c_int32), ("tile_y", C.c_int32), ("min_blocks", C.c_int32),
+                ("us_per_step", C.c_double)]
+
+
 _sig = None
 
 
@@ -96,6 +102,11 @@ def lib() -> C.CDLL:
         L.lbm_batch_last_error.restype = C.c_char_p
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_batch_destroy.restype = None
+        tp, i32p = C.POINTER(lbm_tune_entry), C.POINTER(C.c_int32)
+        L.lbm_autotune.argtypes = [vp, C.c_int32, tp, C.c_int32, i32p]
+        L.lbm_batch_autotune.argtypes = [vp, C.c_int32, tp, C.c_int32, i32p]
+        L.lbm_autotune.restype = C.c_int
+        L.lbm_batch_autotune.restype = C.c_int
         for n in ("lbm_batch_create", "lbm_batch_set_geometry", "lbm_batch_run",
                   "lbm_batch_measure", "lbm_batch_instance"):
             getattr(L, n).restype = C.c_int
@@ -203,6 +214,21 @@ def lbm_get_info(ctx) -> lbm_info:
     return out
 
 
+def _tune(fn, handle, trial_steps, check):
+    cap = 16
+    out = (lbm_tune_entry * cap)()
+    n = C.c_int32()
+    check(fn(handle, int(trial_steps), out, cap, C.byref(n)), handle)
+    return [dict(tile=(out[i].tile_x, out[i].tile_y), min_blocks=out[i].min_blocks,
+                 us_per_step=out[i].us_per_step) for i in range(min(n.value, cap))]
+
+
+def lbm_autotune(ctx, trial_steps: int = 20):
+    """Time every step-kernel variant on the lattice's state and keep the fastest; returns
+    the timings (list of dicts)."""
+    return _tune(lib().lbm_autotune, ctx, trial_steps, _check)
+
+
 def lbm_synchronize(ctx):
     _check(lib().lbm_synchronize(ctx), ctx)
 
@@ -305,6 +331,9 @@ class Lattice:
     def info(self):
         return lbm_get_info(self.ctx)
 
+    def autotune(self, trial_steps=20):
+        return lbm_autotune(self.ctx, trial_steps)
+
 
 # ------------------------------------------------------------------------------ batched sweeps
 def _bcheck(status, b=None, allow=()):
@@ -354,6 +383,11 @@ def lbm_batch_instance(b, i: int):
     return ctx
 
 
+def lbm_batch_autotune(b, trial_steps: int = 20):
+    """Time every tile variant of the batched kernel and keep the fastest."""
+    return _tune(lib().lbm_batch_autotune, b, trial_steps, _bcheck)
+
+
 def lbm_batch_destroy(b):
     if b:
         lib().lbm_batch_destroy(b)
@@ -364,10 +398,11 @@ class Batch:
 
     def __init__(self, sizes, *, eos=LBM_EOS_PR, Tr=0.7, k2=0.1, kappa=0.0126, tau=1.0,
                  s_e=1.64, s_eps=1.54, s_q=1.9, gx=0.0, gy=0.0, rho_g=0.0, rho_l=0.0,
-                 collision=LBM_MRT, device=0):
+                 collision=LBM_MRT, device=0, tile_auto=False):
         self.sizes = [(int(a), int(b)) for a, b in sizes]
         self.n = len(self.sizes)
-        self.params = lbm_params(0, 0, LBM_FP32, eos, collision, device, 0, 0, 0, Tr, k2, kappa,
+        self.params = lbm_params(0, 0, LBM_FP32, eos, collision, device,
+                                 LBM_TILE_AUTO if tile_auto else 0, 0, 0, Tr, k2, kappa,
                                  tau, s_e, s_eps, s_q, gx, gy, rho_g, rho_l, None)
         self.b = lbm_batch_create(self.params, [s[0] for s in self.sizes],
                                   [s[1] for s in self.sizes])
@@ -410,6 +445,9 @@ class Batch:
 
     def mass(self, i):
         return lbm_mass(lbm_batch_instance(self.b, i))[1]
+
+    def autotune(self, trial_steps=20):
+        return lbm_batch_autotune(self.b, trial_steps)
 
 
 # ------------------------------------------------------------------- warm-start surrogate

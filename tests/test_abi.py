@@ -80,3 +80,13 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "lbm_oracle" not in txt, f
+
+
+def test_autotune_rejects_null_handles():
+    """The autotuners report a NULL handle as an argument error (no device work)."""
+    import ctypes as C
+    from paper_2202_06516_gb300 import lbm
+    L = lbm.lib()
+    n = C.c_int32()
+    assert L.lbm_autotune(None, 5, None, 0, C.byref(n)) == lbm.LBM_ERR_ARG
+    assert L.lbm_batch_autotune(None, 5, None, 0, C.byref(n)) == lbm.LBM_ERR_ARG
