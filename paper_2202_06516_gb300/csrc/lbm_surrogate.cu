@@ -19,6 +19,9 @@
 
 #include "lbm_internal.cuh"
 #include "sg_gemm.cuh"
+#include "sg_tc.cuh"
+
+#include <mutex>
 
 namespace lbm {
 void set_global_error(const std::string& msg);
@@ -37,81 +40,124 @@ int blocks_for(long long n) {
     return (int)(b > 65535LL * 8 ? 65535LL * 8 : (b < 1 ? 1 : b));
 }
 
+// Pixel index p -> (n, y, x) of a batch of H x W images (NHWC); P2: H and W are powers of two
+// and the split is done with shifts and masks.
+struct PixDims {
+    int H, W, lh, lw;  // lh, lw: log2 H, log2 W when P2
+};
+
+template <bool P2>
+__device__ __forceinline__ void pix_split(int p, const PixDims& d, int& n, int& y, int& x) {
+    if (P2) {
+        x = p & (d.W - 1);
+        y = (p >> d.lw) & (d.H - 1);
+        n = p >> (d.lw + d.lh);
+    } else {
+        x = p % d.W;
+        const int q = p / d.W;
+        y = q % d.H;
+        n = q / d.H;
+    }
+}
+
+__device__ __forceinline__ void add8(float* s, const uint4& v) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(h[i]);
+        s[2 * i] += f.x;
+        s[2 * i + 1] += f.y;
+    }
+}
+
+__device__ __forceinline__ void store8(float* dst, const float* s, int acc) {
+    float4* d = reinterpret_cast<float4*>(dst);
+    float4 a = make_float4(s[0], s[1], s[2], s[3]), b = make_float4(s[4], s[5], s[6], s[7]);
+    if (acc) {
+        const float4 o0 = d[0], o1 = d[1];
+        a.x += o0.x; a.y += o0.y; a.z += o0.z; a.w += o0.w;
+        b.x += o1.x; b.y += o1.y; b.z += o1.z; b.w += o1.w;
+    }
+    d[0] = a;
+    d[1] = b;
+}
+
 // im2col of a 3x3, pad-1 convolution whose input channels are [source 1 | source 2]:
 // col[p][(ky*3+kx)*C + c] = x(n, y+ky-1, x+kx-1, c). Source 1 may be stored at half resolution
-// (up1 = 1: nearest 2x upsampling on the fly). Eight channels per thread (16-byte accesses).
-__global__ void k_im2col(const bf16* x1, int C1, int up1, const bf16* x2, int C2, int B, int H,
-                         int W, bf16* col) {
-    const int C = C1 + C2, C8 = C / 8;
-    const long long total = (long long)B * H * W * 9 * C8;
+// (up1 = 1: nearest 2x upsampling on the fly). Eight channels per thread (16-byte accesses); the
+// number of 8-channel groups C / 8 = 2^lc8, so thread t writes the 16 bytes at col + 8 t.
+template <bool P2>
+__global__ void k_im2col(const bf16* x1, int C1, int up1, const bf16* x2, int C2, PixDims d,
+                         int P, int lc8, bf16* col) {
+    const int C8 = 1 << lc8;
+    const long long total = (long long)P * 9 * C8;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int c8 = (int)(t % C8);
-        const long long r = t / C8;
-        const int tap = (int)(r % 9);
-        const long long p = r / 9;
-        const int xx = (int)(p % W), yy = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+        const int c8 = (int)(t & (C8 - 1));
+        const int tq = (int)(t >> lc8);  // p * 9 + tap
+        const int p = tq / 9, tap = tq - p * 9;
+        int n, yy, xx;
+        pix_split<P2>(p, d, n, yy, xx);
         const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (sy >= 0 && sy < H && sx >= 0 && sx < W) {
+        if (sy >= 0 && sy < d.H && sx >= 0 && sx < d.W) {
             const int c = c8 * 8;
             if (c < C1) {
-                const int h1 = up1 ? H / 2 : H, w1 = up1 ? W / 2 : W;
+                const int h1 = up1 ? d.H / 2 : d.H, w1 = up1 ? d.W / 2 : d.W;
                 const int ty = up1 ? sy >> 1 : sy, tx = up1 ? sx >> 1 : sx;
                 v = *reinterpret_cast<const uint4*>(x1 + (((size_t)n * h1 + ty) * w1 + tx) * C1 + c);
             } else {
-                v = *reinterpret_cast<const uint4*>(x2 + (((size_t)n * H + sy) * W + sx) * C2 +
+                v = *reinterpret_cast<const uint4*>(x2 + (((size_t)n * d.H + sy) * d.W + sx) * C2 +
                                                     (c - C1));
             }
         }
-        *reinterpret_cast<uint4*>(col + (size_t)p * 9 * C + tap * C + c8 * 8) = v;
+        *reinterpret_cast<uint4*>(col + (size_t)t * 8) = v;
     }
 }
 
 // col2im (adjoint of k_im2col) into FP32 gradients of the two sources; accumulates when asked.
+// Eight channels per thread: (C1 / 8) = 2^l1 groups per pixel of source 1 (at d1 resolution),
+// (C2 / 8) = 2^l2 of source 2 (C2 = 0: none). Taps are summed in the order of k_im2col's
+// columns, so every element is the same sum as a scalar gather.
+template <bool P2>
 __global__ void k_col2im(const bf16* dcol, int C1, int up1, float* dx1, int acc1, int C2,
-                         float* dx2, int acc2, int B, int H, int W) {
+                         float* dx2, int acc2, PixDims d, PixDims d1, int B, int l1, int l2) {
     const int C = C1 + C2;
-    // source 1 elements (possibly half resolution), then source 2 elements
-    const int h1 = up1 ? H / 2 : H, w1 = up1 ? W / 2 : W;
-    const long long n1 = (long long)B * h1 * w1 * C1, n2 = (long long)B * H * W * C2;
+    const long long n1 = (long long)B * d1.H * d1.W << l1;
+    const long long n2 = C2 > 0 ? (long long)B * d.H * d.W << l2 : 0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n1 + n2;
          t += (long long)gridDim.x * blockDim.x) {
-        float s = 0.f;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (t < n1) {
-            const int c = (int)(t % C1);
-            const long long q = t / C1;
-            const int X = (int)(q % w1), Y = (int)((q / w1) % h1), n = (int)(q / ((long long)w1 * h1));
+            const int q = (int)(t >> l1), c = (int)(t & ((1 << l1) - 1)) * 8;
+            int n, Y, X;
+            pix_split<P2>(q, d1, n, Y, X);
             const int f = up1 ? 2 : 1;
             for (int dy = 0; dy < f; ++dy)
                 for (int dxo = 0; dxo < f; ++dxo) {
                     const int yy = Y * f + dy, xx = X * f + dxo;
+#pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
                         const int py = yy - (tap / 3 - 1), px = xx - (tap % 3 - 1);
-                        if (py < 0 || py >= H || px < 0 || px >= W) continue;
-                        s += __bfloat162float(
-                            dcol[(((size_t)n * H + py) * W + px) * 9 * C + tap * C + c]);
+                        if (py < 0 || py >= d.H || px < 0 || px >= d.W) continue;
+                        add8(s, *reinterpret_cast<const uint4*>(
+                                    dcol + (((size_t)n * d.H + py) * d.W + px) * 9 * C + tap * C + c));
                     }
                 }
-            if (acc1)
-                dx1[t] += s;
-            else
-                dx1[t] = s;
+            store8(dx1 + t * 8, s, acc1);
         } else {
             const long long u = t - n1;
-            const int c = (int)(u % C2);
-            const long long q = u / C2;
-            const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((long long)W * H));
+            const int q = (int)(u >> l2), c = (int)(u & ((1 << l2) - 1)) * 8;
+            int n, yy, xx;
+            pix_split<P2>(q, d, n, yy, xx);
+#pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const int py = yy - (tap / 3 - 1), px = xx - (tap % 3 - 1);
-                if (py < 0 || py >= H || px < 0 || px >= W) continue;
-                s += __bfloat162float(
-                    dcol[(((size_t)n * H + py) * W + px) * 9 * C + tap * C + C1 + c]);
+                if (py < 0 || py >= d.H || px < 0 || px >= d.W) continue;
+                add8(s, *reinterpret_cast<const uint4*>(
+                            dcol + (((size_t)n * d.H + py) * d.W + px) * 9 * C + tap * C + C1 + c));
             }
-            if (acc2)
-                dx2[u] += s;
-            else
-                dx2[u] = s;
+            store8(dx2 + u * 8, s, acc2);
         }
     }
 }
@@ -145,27 +191,62 @@ __global__ void k_avgpool_bwd(const float* dy, float* dx, int B, int H, int W, i
 }
 
 // leaky-ReLU adjoint: g = dy * (y > 0 ? 1 : 0.1) (the output has the sign of its input), as
-// BF16 for the gradient GEMMs
-__global__ void k_relu_mask(const float* dy, const bf16* y, bf16* g, long long n) {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x)
-        g[t] = __float2bfloat16_rn(__bfloat162float(y[t]) > 0.f ? dy[t] : 0.1f * dy[t]);
+// BF16 for the gradient GEMMs; eight elements per thread (n8 groups)
+__global__ void k_relu_mask(const float* dy, const bf16* y, bf16* g, long long n8) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n8;
+         t += (long long)gridDim.x * blockDim.x) {
+        const uint4 yv = reinterpret_cast<const uint4*>(y)[t];
+        const float4 a = reinterpret_cast<const float4*>(dy)[2 * t];
+        const float4 b = reinterpret_cast<const float4*>(dy)[2 * t + 1];
+        const float d[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        const __nv_bfloat162* yh = reinterpret_cast<const __nv_bfloat162*>(&yv);
+        uint4 out;
+        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&out);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 yf = __bfloat1622float2(yh[i]);
+            const float g0 = yf.x > 0.f ? d[2 * i] : 0.1f * d[2 * i];
+            const float g1 = yf.y > 0.f ? d[2 * i + 1] : 0.1f * d[2 * i + 1];
+            oh[i] = __floats2bfloat162_rn(g0, g1);
+        }
+        reinterpret_cast<uint4*>(g)[t] = out;
+    }
 }
 
-// column sums of g [P x C] (bias gradient), deterministic: block b sums rows b, b + nb, ...
+// column sums of g [P x C] (bias gradient), deterministic: with R = blockDim / C rows per pass,
+// thread (r, c) of block b sums rows b R + r, b R + r + gridDim R, ...; the R partial sums of a
+// column are then added in r order. Requires C <= blockDim.
 __global__ void k_colsum_partial(const bf16* g, long long P, int C, float* part) {
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.f;
-        for (long long p = blockIdx.x; p < P; p += gridDim.x) s += __bfloat162float(g[p * C + c]);
-        part[(size_t)blockIdx.x * C + c] = s;
+    __shared__ float sm[kT];
+    const int R = blockDim.x / C;
+    const int r = threadIdx.x / C, c = threadIdx.x - r * C;
+    float s = 0.f;
+    if (r < R)
+        for (long long p = (long long)blockIdx.x * R + r; p < P; p += (long long)gridDim.x * R)
+            s += __bfloat162float(g[p * C + c]);
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int k = 0; k < R; ++k) t += sm[k * C + threadIdx.x];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
     }
 }
+
+// out[c] = sum over b of part[b * C + c]: one block per column, a fixed-shape tree in shared
+// memory (deterministic)
 __global__ void k_colsum_final(const float* part, int nb, int C, float* out) {
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.f;
-        for (int b = 0; b < nb; ++b) s += part[(size_t)b * C + c];
-        out[c] = s;
+    __shared__ float sm[kT];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)b * C + c];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[c] = sm[0];
 }
 
 // head: phi = sigmoid(sum_c x[p][c] w[c] + b); with targets, also the loss terms and the
@@ -241,6 +322,16 @@ __global__ void k_to_bf16(const float* x, bf16* y, long long n) {
         y[t] = __float2bfloat16_rn(x[t]);
 }
 
+// W^T of one convolution: wt[k * cout + co] = w[co * kc + k] (kc = 9 C_in)
+__global__ void k_transpose_w(const bf16* w, bf16* wt, int cout, int kc) {
+    const long long n = (long long)cout * kc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / cout), co = (int)(i - (long long)k * cout);
+        wt[i] = w[(size_t)co * kc + k];
+    }
+}
+
 struct Conv {
     int src1, C1, up1;  // source tensor index, channels, stored at half resolution
     int src2, C2;       // second source (-1: none)
@@ -272,6 +363,7 @@ struct lbm_surrogate {
     size_t nparams = 0;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     bf16* wb = nullptr;
+    bf16* wbt = nullptr;        // per convolution W^T [9 C_in][C_out] (data-gradient operand)
     bf16 *col = nullptr, *dcol = nullptr, *gmask = nullptr;
     size_t col_elems = 0, act_elems = 0;
     float* part = nullptr;  // reduction partials
@@ -303,8 +395,90 @@ lbm_status sfail(lbm_surrogate* s, lbm_status st, const std::string& msg) {
             return sfail((s), LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Latched timeout flag of the tensor-core GEMM: mapped host memory that the kernels write on
+// a wait that ran out; reported (and cleared) by the next host call that checks it.
+struct TcFlag {
+    volatile int* host = nullptr;
+    int* dev = nullptr;
+};
+
+TcFlag& tc_flag() {
+    static std::mutex mu;
+    static TcFlag f;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!f.host) {
+        int* h = nullptr;
+        if (cudaHostAlloc((void**)&h, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            return f;
+        }
+        *h = 0;
+        int* d = nullptr;
+        if (cudaHostGetDevicePointer((void**)&d, h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(h);
+            return f;
+        }
+        f.host = h;
+        f.dev = d;
+    }
+    return f;
+}
+
+// true (and the flag cleared) if a tensor-core GEMM launched earlier gave up waiting
+bool tc_timed_out() {
+    TcFlag& f = tc_flag();
+    if (!f.host) return false;
+    const bool t = *f.host != 0;
+    *f.host = 0;
+    return t;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
+    using TS = lbm::sgtc::TcShape<BN, STAGES>;
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            lbm::sgtc::k_gemm_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int* flag = tc_flag().dev;
+    if (!flag) return cudaErrorMemoryAllocation;
+    dim3 grid((a.N + BN - 1) / BN, (a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM, splits);
+    lbm::sgtc::k_gemm_tc<BN, STAGES><<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
+    return cudaGetLastError();
+}
+
+// C = A B^T with both operands K-major on the tcgen05 tensor cores. The N tile is the compiled
+// width that covers N with the fewest computed columns (ties: fewer tiles); wide tiles keep two
+// stages so that two CTAs share an SM and one's epilogue overlaps the other's MMAs.
+cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
+    static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
+    int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
+    for (int w : widths) {
+        const int tiles = (a.N + w - 1) / w, cols = tiles * w;
+        if (cols < best_cols || (cols == best_cols && tiles < best_tiles)) {
+            best = w;
+            best_cols = cols;
+            best_tiles = tiles;
+        }
+    }
+    switch (best) {
+        case 32: return launch_tc<32, 3>(st, a, splits);
+        case 64: return launch_tc<64, 3>(st, a, splits);
+        case 80: return launch_tc<80, 4>(st, a, splits);
+        case 128: return launch_tc<128, 3>(st, a, splits);
+        case 144: return launch_tc<144, 2>(st, a, splits);
+        case 192: return launch_tc<192, 2>(st, a, splits);
+        default: return launch_tc<256, 2>(st, a, splits);
+    }
+}
+
 template <bool AK, bool BK>
 cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
+    if (AK && BK) return gemm_tc(st, a);
     dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
     k_gemm_bf16<AK, BK><<<grid, GTHREADS, 0, st>>>(a);
     return cudaGetLastError();
@@ -331,6 +505,63 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM, splits);
     k_gemm_bf16<false, false><<<grid, GTHREADS, 0, st>>>(a);
     k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
+    return cudaGetLastError();
+}
+
+// BF16 copies of the weights (after the FP32 masters changed): W for the forward pass, W^T for
+// the data gradient
+cudaError_t refresh_bf16_weights(lbm_surrogate* s) {
+    k_to_bf16<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(s->w, s->wb,
+                                                                       (long long)s->nparams);
+    for (const Conv& c : s->convs) {
+        const int kc = 9 * (c.C1 + c.C2);
+        k_transpose_w<<<blocks_for((long long)c.Cout * kc), kT, 0, s->stream>>>(
+            s->wb + c.w_off, s->wbt + c.w_off, c.Cout, kc);
+    }
+    return cudaGetLastError();
+}
+
+int ilog2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return (1 << l) == v ? l : -1;
+}
+
+PixDims pix_dims(int H, int W) { return PixDims{H, W, ilog2_exact(H), ilog2_exact(W)}; }
+
+// im2col of convolution c (channel groups of 8, a power of two, checked at creation)
+cudaError_t launch_im2col(lbm_surrogate* s, const Conv& c, int B) {
+    const bf16* x1 = s->t[c.src1].y;
+    const bf16* x2 = c.src2 >= 0 ? s->t[c.src2].y : nullptr;
+    const PixDims d = pix_dims(c.H, c.W);
+    const int P = B * c.H * c.W;
+    const int lc8 = ilog2_exact((c.C1 + c.C2) / 8);
+    const long long total = (long long)P * 9 * ((c.C1 + c.C2) / 8);
+    if (d.lh >= 0 && d.lw >= 0)
+        k_im2col<true><<<blocks_for(total), kT, 0, s->stream>>>(x1, c.C1, c.up1, x2, c.C2, d, P,
+                                                                lc8, s->col);
+    else
+        k_im2col<false><<<blocks_for(total), kT, 0, s->stream>>>(x1, c.C1, c.up1, x2, c.C2, d, P,
+                                                                 lc8, s->col);
+    return cudaGetLastError();
+}
+
+// col2im of convolution c from s->dcol, accumulated into the sources' gradients
+cudaError_t launch_col2im(lbm_surrogate* s, const Conv& c, int B) {
+    const PixDims d = pix_dims(c.H, c.W);
+    const PixDims d1 = c.up1 ? pix_dims(c.H / 2, c.W / 2) : d;
+    const int l1 = ilog2_exact(c.C1 / 8), l2 = c.C2 > 0 ? ilog2_exact(c.C2 / 8) : 0;
+    const long long n = ((long long)B * d1.H * d1.W << l1) +
+                        (c.C2 > 0 ? ((long long)B * d.H * d.W << l2) : 0);
+    float* dx2 = c.src2 >= 0 ? s->t[c.src2].dy : nullptr;
+    if (d.lh >= 0 && d.lw >= 0 && d1.lh >= 0 && d1.lw >= 0)
+        k_col2im<true><<<blocks_for(n), kT, 0, s->stream>>>(s->dcol, c.C1, c.up1,
+                                                            s->t[c.src1].dy, 1, c.C2, dx2, 1, d,
+                                                            d1, B, l1, l2);
+    else
+        k_col2im<false><<<blocks_for(n), kT, 0, s->stream>>>(s->dcol, c.C1, c.up1,
+                                                             s->t[c.src1].dy, 1, c.C2, dx2, 1, d,
+                                                             d1, B, l1, l2);
     return cudaGetLastError();
 }
 
@@ -396,8 +627,7 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         if (a.y == nullptr) return sfail(s, LBM_ERR_STATE, "surrogate: missing activation");
         const int Cin = c.C1 + c.C2;
         const long long P = (long long)B * c.H * c.W;
-        k_im2col<<<blocks_for(P * 9 * Cin / 8), kT, 0, s->stream>>>(
-            a.y, c.C1, c.up1, c.src2 >= 0 ? s->t[c.src2].y : nullptr, c.C2, B, c.H, c.W, s->col);
+        SCUDA(s, launch_im2col(s, c, B));
         GemmArgs g{};
         g.A = s->col;
         g.B = s->wb + c.w_off;
@@ -430,9 +660,10 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
                                 int32_t device, lbm_surrogate** out) {
     if (!out) return sfail(nullptr, LBM_ERR_ARG, "lbm_surrogate_create: out is NULL");
     *out = nullptr;
-    if (H <= 0 || W <= 0 || H % 8 || W % 8 || base <= 0 || base % 8 || max_batch <= 0)
+    if (H <= 0 || W <= 0 || H % 8 || W % 8 || (base != 8 && base != 16 && base != 32) ||
+        max_batch <= 0)
         return sfail(nullptr, LBM_ERR_ARG,
-                     "lbm_surrogate_create: H, W multiples of 8, base a multiple of 8, batch > 0");
+                     "lbm_surrogate_create: H, W multiples of 8, base 8, 16 or 32, batch > 0");
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return sfail(nullptr, LBM_ERR_CUDA, "lbm_surrogate_create: cannot select the device");
@@ -467,6 +698,7 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->m, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->v, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->wb, np * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->wbt, np * sizeof(bf16));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->col, colmax * sizeof(bf16));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->dcol, colmax * sizeof(bf16));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->gmask, s->act_elems * sizeof(bf16));
@@ -483,6 +715,7 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, np * sizeof(float), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, np * sizeof(float), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->wb, 0, np * sizeof(bf16), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->wbt, 0, np * sizeof(bf16), s->stream);
     if (e != cudaSuccess) return cleanup(cudaGetErrorString(e));
     *out = s;
     return LBM_OK;
@@ -495,7 +728,7 @@ lbm_status lbm_surrogate_set_weights(lbm_surrogate* s, const float* host, int64_
         return sfail(s, LBM_ERR_ARG, "lbm_surrogate_set_weights: need num_params floats");
     SCUDA(s, cudaSetDevice(s->device));
     SCUDA(s, cudaMemcpyAsync(s->w, host, n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    k_to_bf16<<<blocks_for(n), kT, 0, s->stream>>>(s->w, s->wb, n);
+    SCUDA(s, refresh_bf16_weights(s));
     SCUDA(s, cudaMemsetAsync(s->m, 0, n * sizeof(float), s->stream));
     SCUDA(s, cudaMemsetAsync(s->v, 0, n * sizeof(float), s->stream));
     s->adam_t = 0;
@@ -537,6 +770,8 @@ lbm_status lbm_surrogate_forward(lbm_surrogate* s, const void* x, int32_t B, flo
         return sfail(s, LBM_ERR_ARG, "lbm_surrogate_forward: base must be 8, 16 or 32");
     SCUDA(s, cudaGetLastError());
     SCUDA(s, cudaStreamSynchronize(s->stream));
+    if (tc_timed_out())
+        return sfail(s, LBM_ERR_TIMEOUT, "lbm_surrogate_forward: a tensor-core wait timed out");
     return LBM_OK;
 }
 
@@ -582,7 +817,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         return sfail(s, LBM_ERR_ARG, "lbm_surrogate_train_step: base must be 8, 16 or 32");
     SCUDA(s, cudaGetLastError());
     // head gradients: sum the per-block partials (C weights, loss, bias)
-    k_colsum_final<<<1, kT, 0, s->stream>>>(s->hpart, nb, C + 2, s->part);
+    k_colsum_final<<<C + 2, kT, 0, s->stream>>>(s->hpart, nb, C + 2, s->part);
     SCUDA(s, cudaMemcpyAsync(s->g + s->head_w, s->part, C * sizeof(float),
                              cudaMemcpyDeviceToDevice, s->stream));
     SCUDA(s, cudaMemcpyAsync(s->g + s->head_b, s->part + C + 1, sizeof(float),
@@ -605,15 +840,13 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         const int Cin = c.C1 + c.C2;
         const long long Pc = (long long)B * c.H * c.W;
         const long long n_out = Pc * c.Cout;
-        k_relu_mask<<<blocks_for(n_out), kT, 0, s->stream>>>(o.dy, o.y, s->gmask, n_out);
+        k_relu_mask<<<blocks_for(n_out / 8), kT, 0, s->stream>>>(o.dy, o.y, s->gmask, n_out / 8);
         // bias gradient
         const int cb = std::min<long long>(s->part_blocks, Pc);
         k_colsum_partial<<<cb, kT, 0, s->stream>>>(s->gmask, Pc, c.Cout, s->part);
-        k_colsum_final<<<1, kT, 0, s->stream>>>(s->part, cb, c.Cout, s->g + c.b_off);
+        k_colsum_final<<<c.Cout, kT, 0, s->stream>>>(s->part, cb, c.Cout, s->g + c.b_off);
         // weight gradient: dW[co][k] = sum_p g[p][co] col[p][k]
-        const Tensor& a = s->t[c.src1];
-        k_im2col<<<blocks_for(Pc * 9 * Cin / 8), kT, 0, s->stream>>>(
-            a.y, c.C1, c.up1, c.src2 >= 0 ? s->t[c.src2].y : nullptr, c.C2, B, c.H, c.W, s->col);
+        SCUDA(s, launch_im2col(s, c, B));
         GemmArgs gw{};
         gw.A = s->gmask;
         gw.B = s->col;
@@ -628,21 +861,16 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         if (c.src1 == 0) continue;
         GemmArgs gd{};
         gd.A = s->gmask;
-        gd.B = s->wb + c.w_off;
+        gd.B = s->wbt + c.w_off;   // W^T [9 C_in][C_out]: both operands K-major
         gd.M = (int)Pc;
         gd.N = 9 * Cin;
         gd.K = c.Cout;
         gd.lda = c.Cout;
-        gd.ldb = 9 * Cin;
+        gd.ldb = c.Cout;
         gd.Cb = s->dcol;
         gd.ldc = 9 * Cin;
-        SCUDA(s, (gemm<true, false>(s->stream, gd)));
-        const long long h1 = c.up1 ? c.H / 2 : c.H, w1 = c.up1 ? c.W / 2 : c.W;
-        const long long n1 = (long long)B * h1 * w1 * c.C1 + Pc * c.C2;
-        k_col2im<<<blocks_for(n1), kT, 0, s->stream>>>(
-            s->dcol, c.C1, c.up1, s->t[c.src1].dy, 1, c.C2,
-            c.src2 >= 0 ? s->t[c.src2].dy : nullptr, 1, B, c.H, c.W);
-        SCUDA(s, cudaGetLastError());
+        SCUDA(s, (gemm<true, true>(s->stream, gd)));
+        SCUDA(s, launch_col2im(s, c, B));
     }
     if (lr > 0.f) {
         ++s->adam_t;
@@ -651,11 +879,12 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         const float c2 = 1.f / (1.f - powf(b2, (float)s->adam_t));
         k_adam<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(
             s->w, s->g, s->m, s->v, (long long)s->nparams, lr, b1, b2, 1e-8f, c1, c2);
-        k_to_bf16<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(s->w, s->wb,
-                                                                           (long long)s->nparams);
+        SCUDA(s, refresh_bf16_weights(s));
     }
     SCUDA(s, cudaGetLastError());
     SCUDA(s, cudaStreamSynchronize(s->stream));
+    if (tc_timed_out())
+        return sfail(s, LBM_ERR_TIMEOUT, "lbm_surrogate_train_step: a tensor-core wait timed out");
     if (loss) *loss = hl;
     return LBM_OK;
 }
@@ -680,6 +909,8 @@ lbm_status lbm_sg_gemm(const void* A, const void* B, int32_t M, int32_t N, int32
     if ((a_kmajor && (K % 8 || lda % 8)) || (!a_kmajor && (M % 8 || lda % 8)) ||
         (b_kmajor && (K % 8 || ldb % 8)) || (!b_kmajor && (N % 8 || ldb % 8)))
         return sfail(nullptr, LBM_ERR_ARG, "lbm_sg_gemm: alignment (multiples of 8) violated");
+    if (tc_timed_out())
+        return sfail(nullptr, LBM_ERR_TIMEOUT, "lbm_sg_gemm: an earlier tensor-core wait timed out");
     GemmArgs g{};
     g.A = (const bf16*)A;
     g.B = (const bf16*)B;
@@ -717,6 +948,7 @@ void lbm_surrogate_destroy(lbm_surrogate* s) {
     cudaFree(s->m);
     cudaFree(s->v);
     cudaFree(s->wb);
+    cudaFree(s->wbt);
     cudaFree(s->col);
     cudaFree(s->dcol);
     cudaFree(s->gmask);

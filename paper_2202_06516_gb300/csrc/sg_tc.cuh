@@ -1,0 +1,361 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory) for the
+// surrogate network: C[M x N] = A[M x K] B[N x K]^T with both operands K-major (the forward
+// convolution Xcol W^T and, with a transposed weight copy, the data gradient dY W).
+//
+// One CTA of 128 threads computes a 128 x BN tile. All threads stage K-slices of 64 elements
+// into shared memory with cp.async, in the 128-byte-swizzled K-major layout the tensor core
+// reads (8-row atoms of 1 KB; the 16-byte chunk c of row r stored at chunk c ^ (r % 8)); STAGES
+// slices are in flight. Thread 0 issues four 128 x BN x 16 MMAs per slice (kind::f16, BF16 in,
+// FP32 accumulate into BN tensor-memory columns) and commits them to the slice's mbarrier,
+// which frees the slice for the next load. The epilogue reads the accumulator lanes back with
+// tcgen05.ld (warp w owns rows 32 w .. 32 w + 31), adds the bias, applies the leaky ReLU and
+// stores FP32 or BF16.
+//
+// Every wait on an mbarrier is polled by one thread with an iteration limit; on expiry the
+// CTA sets *err, waits (bounded) for the MMAs it issued, frees its tensor memory and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "sg_gemm.cuh"
+
+namespace lbm {
+namespace sgtc {
+
+constexpr int BM = 128, BK = 64, TC_THREADS = 128;
+constexpr long long kWaitLimit = 1ll << 22;
+
+__host__ __device__ constexpr int tmem_cols(int bn) {
+    return bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
+}
+
+template <int BN, int STAGES>
+struct TcShape {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N of kind::f16 at M = 128");
+    static constexpr int A_BYTES = BM * BK * 2;  // 16 KB
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    // 1 KB alignment slack for the swizzle atoms, then the stages, mbarriers and the TMEM slot
+    static constexpr int RAW_BYTES = 1024 + STAGES * STAGE_BYTES + 8 * (STAGES + 1) + 16;
+    // at least enough shared memory that the CTAs resident on one SM never ask for more than
+    // the 512 tensor-memory columns together (an allocation beyond them would wait)
+    static constexpr int TMEM_CTAS = 512 / tmem_cols(BN);
+    static constexpr int MIN_BYTES = 233472 / (TMEM_CTAS + 1) + 1;
+    static constexpr int SMEM_BYTES = RAW_BYTES > MIN_BYTES ? RAW_BYTES : MIN_BYTES;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1 KB apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+// poll one phase of an mbarrier; false when the iteration limit ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of the warp's 32 lanes (one row per thread)
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 16 consecutive FP32 accumulator columns of the warp's 32 lanes
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// one K-slice of ROWS x 64 elements of a K-major operand into the swizzled layout; rows past
+// nrows and k past ke are zero-filled
+template <int ROWS>
+__device__ __forceinline__ void load_slice(uint8_t* s, const __nv_bfloat16* g, int ld, int row0,
+                                           int nrows, int k0, int ke) {
+    constexpr int CHUNKS = ROWS * (BK / 8);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < CHUNKS; i += TC_THREADS) {
+        const int r = i >> 3, c = i & 7;
+        const bool ok = (row0 + r < nrows) && (k0 + c * 8 < ke);
+        const __nv_bfloat16* src = ok ? g + (size_t)(row0 + r) * ld + k0 + c * 8 : g;
+        uint8_t* dst = s + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+        sg::cp_async16(dst, src, ok);
+    }
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
+    using S = TcShape<BN, STAGES>;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    // 1 KB-aligned base of the stages (the swizzle pattern follows shared-memory address bits)
+    const uint32_t raw = su32(smem_raw);
+    uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * S::STAGE_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES + 1);
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = g.kchunk ? blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         su32(tmem_slot)),
+                     "r"(tmem_cols(BN))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s <= STAGES; ++s) mbar_init(su32(bars + s), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_ok = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+
+    auto stage_a = [&](int s) { return base + s * S::STAGE_BYTES; };
+    auto stage_b = [&](int s) { return base + s * S::STAGE_BYTES + S::A_BYTES; };
+
+#pragma unroll 1
+    for (int p = 0; p < STAGES - 1; ++p) {
+        if (p < nk) {
+            load_slice<BM>(stage_a(p), g.A, g.lda, m0, g.M, kb + p * BK, ke);
+            load_slice<BN>(stage_b(p), g.B, g.ldb, n0, g.N, kb + p * BK, ke);
+        }
+        sg::cp_async_commit();
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES;
+        sg::cp_async_wait<STAGES - 2>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = su32(stage_a(s)), b0 = su32(stage_b(s));
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)
+                tc_mma(tmem, desc_sw128(a0 + 32 * j), desc_sw128(b0 + 32 * j), IDESC,
+                       (kt > 0 || j > 0) ? 1u : 0u);
+            tc_commit(su32(bars + s));
+        }
+        const int nxt = kt + STAGES - 1;
+        if (nxt < nk && kt >= 1) {
+            // the slice being refilled was read by the MMAs of k-tile kt - 1
+            if (tid == 0 && !mbar_wait(su32(bars + (kt - 1) % STAGES), ((kt - 1) / STAGES) & 1))
+                s_ok = 0;
+            __syncthreads();
+            if (!s_ok) {
+                ok = false;
+                break;
+            }
+        }
+        if (nxt < nk) {
+            load_slice<BM>(stage_a(nxt % STAGES), g.A, g.lda, m0, g.M, kb + nxt * BK, ke);
+            load_slice<BN>(stage_b(nxt % STAGES), g.B, g.ldb, n0, g.N, kb + nxt * BK, ke);
+        }
+        sg::cp_async_commit();
+    }
+    sg::cp_async_wait<0>();
+    // completion of every MMA issued (the last commit tracks all earlier ones)
+    if (nk > 0) {
+        if (tid == 0) {
+            tc_commit(su32(bars + STAGES));
+            if (!mbar_wait(su32(bars + STAGES), 0)) s_ok = 0;
+        }
+        __syncthreads();
+        ok = ok && s_ok;
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        tc_fence_after();
+        // accumulator rows go through a per-warp 32 x 32 staging block (rows 144 B apart) in the
+        // now idle stage buffers, so that stores write whole row segments: 16-byte vectors when
+        // the output allows (no accumulation or split, aligned rows), else one column per lane
+        float* ep = reinterpret_cast<float*>(base) + warp * (32 * 36);
+        const size_t zoff = g.kchunk ? (size_t)blockIdx.z * g.split_stride : 0;
+        const bool vec = !g.accumulate && !g.kchunk &&
+                         (g.Cb ? (g.ldc % 8 == 0 && ((uintptr_t)g.Cb & 15) == 0)
+                               : (g.ldc % 4 == 0 && ((uintptr_t)g.Cf & 15) == 0));
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            if (n0 + c0 >= g.N) break;
+            const int w = BN - c0 >= 32 ? 32 : 16;
+            float v[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            if (nk == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+            } else if (w == 32) {
+                tc_ld32(ta, v);
+            } else {
+                tc_ld16(ta, v);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                if (j < w)
+                    *reinterpret_cast<float4*>(ep + lane * 36 + j) =
+                        make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            __syncwarp();
+            if (vec && w == 32 && n0 + c0 + 32 <= g.N) {
+                if (g.Cb) {
+                    // lane: row it * 8 + lane / 4, columns 8 (lane % 4) .. + 7
+                    const int cc = 8 * (lane & 3), n = n0 + c0 + cc;
+                    float bn[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
+#pragma unroll
+                    for (int it = 0; it < 4; ++it) {
+                        const int r = it * 8 + (lane >> 2), m = m0 + warp * 32 + r;
+                        if (m >= g.M) continue;
+                        const float4 x0 = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
+                        const float4 x1 = *reinterpret_cast<const float4*>(ep + r * 36 + cc + 4);
+                        float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                        uint4 o;
+                        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+                        for (int j = 0; j < 8; j += 2) {
+                            float a0 = x[j] + bn[j], a1 = x[j + 1] + bn[j + 1];
+                            if (g.relu) {
+                                a0 = fmaxf(a0, 0.1f * a0);
+                                a1 = fmaxf(a1, 0.1f * a1);
+                            }
+                            oh[j / 2] = __floats2bfloat162_rn(a0, a1);
+                        }
+                        *reinterpret_cast<uint4*>(g.Cb + (size_t)m * g.ldc + n) = o;
+                    }
+                } else {
+                    // lane: row it * 4 + lane / 8, columns 4 (lane % 8) .. + 3
+                    const int cc = 4 * (lane & 7), n = n0 + c0 + cc;
+                    float bn[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int r = it * 4 + (lane >> 3), m = m0 + warp * 32 + r;
+                        if (m >= g.M) continue;
+                        float4 x = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
+                        x.x += bn[0];
+                        x.y += bn[1];
+                        x.z += bn[2];
+                        x.w += bn[3];
+                        if (g.relu) {
+                            x.x = fmaxf(x.x, 0.1f * x.x);
+                            x.y = fmaxf(x.y, 0.1f * x.y);
+                            x.z = fmaxf(x.z, 0.1f * x.z);
+                            x.w = fmaxf(x.w, 0.1f * x.w);
+                        }
+                        *reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n) = x;
+                    }
+                }
+            } else {
+                const int n = n0 + c0 + lane;
+                const bool col_ok = lane < w && n < g.N;
+                const float bn = (col_ok && g.bias) ? g.bias[n] : 0.f;
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const int m = m0 + warp * 32 + r;
+                    if (!col_ok || m >= g.M) continue;
+                    float x = ep[r * 36 + lane] + bn;
+                    if (g.relu) x = fmaxf(x, 0.1f * x);
+                    const size_t o = (size_t)m * g.ldc + n + zoff;
+                    if (g.Cf) {
+                        if (g.accumulate)
+                            g.Cf[o] += x;
+                        else
+                            g.Cf[o] = x;
+                    } else {
+                        g.Cb[o] = __float2bfloat16_rn(x);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(tmem_cols(BN))
+                     : "memory");
+    }
+}
+
+}  // namespace sgtc
+}  // namespace lbm

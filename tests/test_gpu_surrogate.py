@@ -38,6 +38,26 @@ def test_gemm_layouts(env, ak, bk, M, N, K):
     assert err < 2e-6, err
 
 
+@pytest.mark.parametrize("M,N,K", [(1000, 32, 288), (4096, 64, 576), (1024, 256, 2304),
+                                   (384, 300, 72), (129, 130, 64), (640, 512, 1152)])
+def test_gemm_tensor_core_shapes(env, M, N, K):
+    """K-major x K-major products run on the tcgen05 kernel: every N-tile width (32, 64, 128,
+    256), several M and N tiles, K tails inside a 64-wide slice, against FP64 products."""
+    torch, lbm = env
+    g = torch.Generator().manual_seed(M + 11 * N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    Bt = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    want = A.double() @ Bt.double().t()
+    Ad, Bd = A.cuda(), Bt.cuda()   # kept alive until the asynchronous GEMM has run
+    Cd = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    lbm.lbm_sg_gemm(Ad.data_ptr(), Bd.data_ptr(), M, N, K, 1, 1, K, K, Cd.data_ptr(), N)
+    torch.cuda.synchronize()
+    err = (Cd.double().cpu() - want).abs().max().item() / max(1.0, want.abs().max().item())
+    # the products of BF16 operands are exact in FP32; the FP32 sum of K of them drifts like a
+    # random walk, ~sqrt(K) u of the largest output (u = 2^-24), a few times that at the maximum
+    assert err < max(2e-6, 2e-7 * np.sqrt(K)), err
+
+
 def _case(seed=0, B=2, H=32, Wd=32, base=8):
     rng = np.random.default_rng(seed)
     x = np.zeros((B, H, Wd, 8), dtype=np.float32)
