@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NTB, MINB)
         a.plane = I.plane;
         const int tiles_x = (I.nx + TX - 1) / TX;
         const int ty = e.y / tiles_x, tx = e.y - ty * tiles_x;
-        step_tile<float, TX, TY, NTB, false>(a, I.rho_mid, smem_raw, tx * TX, ty * TY);
+        step_tile<float, TX, TY, NTB, false, false>(a, I.rho_mid, smem_raw, tx * TX, ty * TY);
         __syncthreads();  // the next tile reuses shared memory
     }
 }

@@ -53,6 +53,8 @@ template <typename T>
 struct StepArgs {
     const T* h_in;     // 9 planes, post-collision deviations f*_q - w_q rho (see step .cu)
     T* h_out;
+    const T* hq_in[9]; // the same planes one pointer each (single-lattice kernel)
+    T* hq_out[9];
     const T* rho_in;   // rho(t)
     T* rho_out;        // rho(t+1)
     const uint8_t* flags;

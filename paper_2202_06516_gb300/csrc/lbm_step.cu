@@ -54,6 +54,10 @@ StepArgs<T> make_args(lbm_ctx* c, int src) {
     StepArgs<T> a{};
     a.h_in = (const T*)c->h[src];
     a.h_out = (T*)c->h[src ^ 1];
+    for (int q = 0; q < 9; ++q) {
+        a.hq_in[q] = a.h_in + (size_t)q * c->plane;
+        a.hq_out[q] = a.h_out + (size_t)q * c->plane;
+    }
     a.rho_in = (const T*)c->rho[src];
     a.rho_out = (T*)c->rho[src ^ 1];
     a.flags = c->flags;

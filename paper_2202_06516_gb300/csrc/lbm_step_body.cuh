@@ -10,6 +10,18 @@
 namespace lbm {
 namespace stepdev {
 
+// Explicitly rounded operations: the FP32 step is written with them so that its rounding does not
+// depend on where the compiler fuses a multiply into an add (which can differ between the kernels
+// that inline it), and the single-lattice and batched kernels stay bit-identical.
+__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
+__device__ __forceinline__ float sub_rn(float x, float y) { return __fsub_rn(x, y); }
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ float fma_rn(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+__device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
+__device__ __forceinline__ double sub_rn(double x, double y) { return __dsub_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+__device__ __forceinline__ double fma_rn(double x, double y, double z) { return __fma_rn(x, y, z); }
+
 // Bulk chemical potential psi'(rho) at k = 1: Eq. 11 without the gradient term (PR), or the CS
 // counterpart from Eq. 9 with the ideal-gas antiderivative. The FP32 path uses the hardware
 // logarithm and approximate division (relative error ~1e-6 on psi', far below the FP32 noise
@@ -22,23 +34,24 @@ __device__ __forceinline__ float psi_prime<float>(float rho, const StepArgs<floa
     if (a.eos == LBM_EOS_PR) {
         // with d1 = 1 - b rho, d2 = sqrt2 + 1 - b rho, n2 = sqrt2 - 1 + b rho the three
         // divisions of Eq. 11 share one reciprocal, since 1 + 2 b rho - (b rho)^2 = d2 n2
-        const float br = a.b * rho;
         const float s2 = 1.41421356f;
-        const float d1 = 1.0f - br, d2 = s2 + 1.0f - br, n2 = s2 - 1.0f + br;
-        const float dn = d2 * n2;
-        const float r = __fdividef(1.0f, d1 * dn);
-        const float inv_d1 = dn * r;          // 1 / d1
-        const float inv_dn = d1 * r;          // 1 / (d2 n2)
-        const float t13 = a.RT * (__logf(rho * inv_d1) + inv_d1);
-        const float t2 = a.aal * __fdividef(1.0f, 2.0f * s2 * a.b) * __logf(n2 * n2 * inv_dn);
-        const float t4 = a.aal * rho * inv_dn;
-        return t13 - t2 - t4;
+        const float br = mul_rn(a.b, rho);
+        const float d1 = sub_rn(1.0f, br), d2 = sub_rn(s2 + 1.0f, br), n2 = add_rn(s2 - 1.0f, br);
+        const float dn = mul_rn(d2, n2);
+        const float r = __fdividef(1.0f, mul_rn(d1, dn));
+        const float inv_d1 = mul_rn(dn, r);  // 1 / d1
+        const float inv_dn = mul_rn(d1, r);  // 1 / (d2 n2)
+        const float t13 = mul_rn(a.RT, add_rn(__logf(mul_rn(rho, inv_d1)), inv_d1));
+        const float c2 = mul_rn(a.aal, __fdividef(1.0f, mul_rn(2.0f * s2, a.b)));
+        const float t2 = mul_rn(c2, __logf(mul_rn(mul_rn(n2, n2), inv_dn)));
+        const float t4 = mul_rn(mul_rn(a.aal, rho), inv_dn);
+        return sub_rn(sub_rn(t13, t2), t4);
     }
-    const float n = a.b * rho * 0.25f;
-    const float om = 1.0f - n;
-    return a.RT * (__logf(rho) + __fdividef(8.0f * n - 9.0f * n * n + 3.0f * n * n * n,
-                                            om * om * om)) -
-           2.0f * a.aal * rho;
+    const float n = mul_rn(mul_rn(a.b, rho), 0.25f);
+    const float om = sub_rn(1.0f, n);
+    const float num = mul_rn(n, fma_rn(fma_rn(3.0f, n, -9.0f), n, 8.0f));  // 8n - 9n^2 + 3n^3
+    return fma_rn(a.RT, add_rn(__logf(rho), __fdividef(num, mul_rn(mul_rn(om, om), om))),
+                  mul_rn(-2.0f * a.aal, rho));
 }
 
 template <>
@@ -62,17 +75,6 @@ __device__ __forceinline__ double psi_prime<double>(double rho, const StepArgs<d
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// Explicitly rounded operations: the collision is written with them so that its rounding does
-// not depend on where the compiler fuses a multiply into an add (which can differ between the
-// kernels that inline it), and the single-lattice and batched kernels stay bit-identical.
-__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
-__device__ __forceinline__ float sub_rn(float x, float y) { return __fsub_rn(x, y); }
-__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
-__device__ __forceinline__ float fma_rn(float x, float y, float z) { return __fmaf_rn(x, y, z); }
-__device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
-__device__ __forceinline__ double sub_rn(double x, double y) { return __dsub_rn(x, y); }
-__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
-__device__ __forceinline__ double fma_rn(double x, double y, double z) { return __fma_rn(x, y, z); }
 
 // Collision in deviation variables g_q = f_q - w_q rho with exact-difference forcing (Eq. 13).
 // MRT: Lallemand-Luo moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy); the equilibrium moments of
@@ -179,17 +181,20 @@ __device__ __forceinline__ void load4(const double* g, double* s) {
 template <typename T, int RW>
 __device__ __forceinline__ T mu_fluid(const T* s_rho, int o, const StepArgs<T>& a) {
     const T c0 = s_rho[o];
-    const T lapx = -s_rho[o + 2] + (T)16 * s_rho[o + 1] - (T)30 * c0 + (T)16 * s_rho[o - 1] -
-                   s_rho[o - 2];
-    const T lapy = -s_rho[o + 2 * RW] + (T)16 * s_rho[o + RW] - (T)30 * c0 +
-                   (T)16 * s_rho[o - RW] - s_rho[o - 2 * RW];
-    return a.k2 * psi_prime<T>(c0, a) - a.kappa * (lapx + lapy) * ((T)1 / (T)12);
+    // 12 x the fourth-order Laplacian: 16 (sum of axis neighbours at 1) - 60 c0 - (sum at 2)
+    const T s1 = add_rn(add_rn(s_rho[o + 1], s_rho[o - 1]), add_rn(s_rho[o + RW], s_rho[o - RW]));
+    const T s2 = add_rn(add_rn(s_rho[o + 2], s_rho[o - 2]),
+                        add_rn(s_rho[o + 2 * RW], s_rho[o - 2 * RW]));
+    const T lap12 = fma_rn((T)16, s1, fma_rn((T)-60, c0, -s2));
+    return fma_rn(a.k2, psi_prime<T>(c0, a), mul_rn(mul_rn(a.kappa, (T)-1 / (T)12), lap12));
 }
 
 // (6) of the step: new density rho(t+1) = sum_q f*_q(x - e_q) (half-way bounce-back where the
 // source is not fluid) and the stored deviations f*_q(x) - w_q rho(t+1)(x). EDGE: the tile lies
-// within kPadX of an x edge and also writes the periodic images into the pads.
-template <typename T, int TX, int TY, int NT, bool MIXED, bool EDGE>
+// within kPadX of an x edge and also writes the periodic images into the pads. PP: the planes
+// are addressed through the per-plane pointers of StepArgs (single-lattice kernel), else as
+// h_out + q * plane (batched kernel).
+template <typename T, int TX, int TY, int NT, bool MIXED, bool EDGE, bool PP>
 __device__ __forceinline__ void stream_out(const StepArgs<T>& a, const T* s_rho, const T* s_g,
                                            const uint8_t* s_flag, int x0, int y0) {
     using L = Layout<T, TX, TY>;
@@ -203,36 +208,41 @@ __device__ __forceinline__ void stream_out(const StepArgs<T>& a, const T* s_rho,
         if (MIXED && s_flag[o] != kFluid) continue;
         const int oc = (ty + 1) * CW + (tx + 1);
         const T r0 = s_rho[o];
-        const T A = s_g[9 * CW * CH + oc];
-        T B = 0;
+        T B = s_g[oc];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
+        for (int q = 1; q < 9; ++q) {
             const int os = o - qy(q) * RW - qx(q);
-            if (!MIXED || q == 0 || s_flag[os] == kFluid)
-                B += s_g[q * CW * CH + oc - qy(q) * CW - qx(q)];
+            if (!MIXED || s_flag[os] == kFluid)
+                B = add_rn(B, s_g[q * CW * CH + oc - qy(q) * CW - qx(q)]);
             else
-                B += s_g[qopp(q) * CW * CH + oc];
+                B = add_rn(B, s_g[qopp(q) * CW * CH + oc]);
         }
-        const T r1 = A + B;
+        const T r1 = add_rn(s_g[9 * CW * CH + oc], B);
         const unsigned us = (unsigned)lidx(a.P, gx, gy);
-        const T dr = r0 - r1;
+        const T dr = sub_rn(r0, r1);
+        T v[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] = fma_rn(qw<T>(q), dr, s_g[q * CW * CH + oc]);
         if (EDGE) {
             const bool lo = gx < kPadX, hi = gx >= a.nx - kPadX;
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                const T v = s_g[q * CW * CH + oc] + qw<T>(q) * dr;
-                T* ob = a.h_out + us + (unsigned)q * upl;
-                ob[0] = v;
-                if (lo) ob[a.nx] = v;
-                if (hi) ob[-a.nx] = v;
+                T* ob = (PP ? a.hq_out[q] : a.h_out + (unsigned)q * upl) + us;
+                ob[0] = v[q];
+                if (lo) ob[a.nx] = v[q];
+                if (hi) ob[-a.nx] = v[q];
             }
             a.rho_out[us] = r1;
             if (lo) a.rho_out[us + a.nx] = r1;
             if (hi) a.rho_out[us - a.nx] = r1;
         } else {
 #pragma unroll
-            for (int q = 0; q < 9; ++q)
-                a.h_out[us + (unsigned)q * upl] = s_g[q * CW * CH + oc] + qw<T>(q) * dr;
+            for (int q = 0; q < 9; ++q) {
+                if (PP)
+                    a.hq_out[q][us] = v[q];
+                else
+                    a.h_out[us + (unsigned)q * upl] = v[q];
+            }
             a.rho_out[us] = r1;
         }
     }
@@ -241,7 +251,7 @@ __device__ __forceinline__ void stream_out(const StepArgs<T>& a, const T* s_rho,
 // MIXED: the tile and its halo contain non-fluid nodes (walls, the disc, the domain edge), so
 // wetting layers are rebuilt and every neighbour access checks the node class. Interior tiles
 // take the branch-free path (the choice is uniform per CTA).
-template <typename T, int TX, int TY, int NT, bool MACRO, bool MIXED>
+template <typename T, int TX, int TY, int NT, bool MACRO, bool MIXED, bool PP>
 __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid, T* s_rho,
                                           T* s_mu, T* s_g, const uint8_t* s_flag, int x0,
                                           int y0) {
@@ -262,8 +272,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
             for (int q = 1; q < 9; ++q) {
                 const int on = o + qy(q) * RW + qx(q);
                 if (s_flag[on] == kFluid) {
-                    num += qw<T>(q) * s_rho[on];
-                    den += qw<T>(q);
+                    num = fma_rn(qw<T>(q), s_rho[on], num);
+                    den = add_rn(den, qw<T>(q));
                 }
             }
             s_rho[o] = den > (T)0 ? num / den : rho_mid;
@@ -279,8 +289,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
             for (int q = 1; q < 9; ++q) {
                 const int on = o + qy(q) * RW + qx(q);
                 if (s_flag[on] == kLayer1) {
-                    num += qw<T>(q) * s_rho[on];
-                    den += qw<T>(q);
+                    num = fma_rn(qw<T>(q), s_rho[on], num);
+                    den = add_rn(den, qw<T>(q));
                 }
             }
             s_rho[o] = den > (T)0 ? num / den : rho_mid;
@@ -309,9 +319,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
     __syncthreads();
 
     // (5) force and collision on tile + 1
-    const T c12 = (T)1 / (T)12;
-    // 32-bit element offsets (the same for every thread, so they live in uniform registers):
-    // plane q, and the pulled source of direction q one row and one column back along e_q
+    // PP = false: 32-bit element offsets of plane q and of the pulled source of direction q
+    // (the same for every thread, so they live in uniform registers)
     const unsigned upl = (unsigned)a.plane, uP = (unsigned)a.P;
 #define QPL(q) ((unsigned)(q) * upl)
 #define QSRC(q) ((unsigned)(q) * upl - (unsigned)(qy(q) * (int)uP + qx(q)))
@@ -323,30 +332,39 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
         const int gx = x0 - 1 + cx, gy = y0 - 1 + cy;
         const int self = lidx(a.P, gx, gy);
         const T rho = s_rho[o];
-        const T dmux = ((T)8 * (s_mu[om + 1] - s_mu[om - 1]) - (s_mu[om + 2] - s_mu[om - 2])) * c12;
-        const T dmuy =
-            ((T)8 * (s_mu[om + MW] - s_mu[om - MW]) - (s_mu[om + 2 * MW] - s_mu[om - 2 * MW])) * c12;
-        const T drx = ((T)8 * (s_rho[o + 1] - s_rho[o - 1]) - (s_rho[o + 2] - s_rho[o - 2])) * c12;
-        const T dry =
-            ((T)8 * (s_rho[o + RW] - s_rho[o - RW]) - (s_rho[o + 2 * RW] - s_rho[o - 2 * RW])) * c12;
-        const T Fx = -rho * dmux + drx * ((T)1 / (T)3) + rho * a.gx;
-        const T Fy = -rho * dmuy + dry * ((T)1 / (T)3) + rho * a.gy;
+        // Eq. 7: F = -rho grad(mu) + c_s^2 grad(rho) + rho g with fourth-order differences;
+        // G = 12 x the derivative: 8 (f(+1) - f(-1)) - (f(+2) - f(-2))
+        const T Gmx = fma_rn((T)8, sub_rn(s_mu[om + 1], s_mu[om - 1]),
+                             sub_rn(s_mu[om - 2], s_mu[om + 2]));
+        const T Gmy = fma_rn((T)8, sub_rn(s_mu[om + MW], s_mu[om - MW]),
+                             sub_rn(s_mu[om - 2 * MW], s_mu[om + 2 * MW]));
+        const T Grx = fma_rn((T)8, sub_rn(s_rho[o + 1], s_rho[o - 1]),
+                             sub_rn(s_rho[o - 2], s_rho[o + 2]));
+        const T Gry = fma_rn((T)8, sub_rn(s_rho[o + RW], s_rho[o - RW]),
+                             sub_rn(s_rho[o - 2 * RW], s_rho[o + 2 * RW]));
+        const T Fx = fma_rn(rho, fma_rn(Gmx, (T)-1 / (T)12, a.gx), mul_rn(Grx, (T)1 / (T)36));
+        const T Fy = fma_rn(rho, fma_rn(Gmy, (T)-1 / (T)12, a.gy), mul_rn(Gry, (T)1 / (T)36));
         // pull the populations of time t (Eq. 4) with half-way bounce-back
         const unsigned us = (unsigned)self;
         const T* hb = a.h_in + us;
+        // PP: rows of the sources with e_q,y = 0, +1, -1
+        const unsigned r0 = us, rdn = us - uP, rup = us + uP;
         T g[9];
-        g[0] = __ldg(hb);
-        T A = qw<T>(0) * rho;  // sum_q w_q rho(x - e_q) with bounce-back sources taking rho(x)
+        g[0] = PP ? __ldg(a.hq_in[0] + r0) : __ldg(hb);
+        T A = mul_rn(qw<T>(0), rho);  // sum_q w_q rho(x - e_q); bounce-back sources take rho(x)
 #pragma unroll
         for (int q = 1; q < 9; ++q) {
             const int os = o - qy(q) * RW - qx(q);
             if (!MIXED || s_flag[os] == kFluid) {
                 const T rs = s_rho[os];
-                g[q] = __ldg(hb + (int)QSRC(q)) + qw<T>(q) * (rs - rho);
-                A += qw<T>(q) * rs;
+                const T h = PP ? __ldg(a.hq_in[q] + (int)((qy(q) > 0 ? rdn : qy(q) < 0 ? rup : r0) -
+                                                          qx(q)))
+                               : __ldg(hb + (int)QSRC(q));
+                g[q] = fma_rn(qw<T>(q), sub_rn(rs, rho), h);
+                A = fma_rn(qw<T>(q), rs, A);
             } else {
-                g[q] = __ldg(hb + (int)QPL(qopp(q)));
-                A += qw<T>(q) * rho;
+                g[q] = PP ? __ldg(a.hq_in[qopp(q)] + r0) : __ldg(hb + (int)QPL(qopp(q)));
+                A = fma_rn(qw<T>(q), rho, A);
             }
         }
         T ux, uy;
@@ -368,9 +386,9 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
     // (6) streaming into the tile: new density and deviations; tiles within kPadX of the x
     // edges also refresh the periodic images in the pads (a CTA-uniform branch)
     if (x0 < kPadX || x0 + TX > a.nx - kPadX)
-        stream_out<T, TX, TY, NT, MIXED, true>(a, s_rho, s_g, s_flag, x0, y0);
+        stream_out<T, TX, TY, NT, MIXED, true, PP>(a, s_rho, s_g, s_flag, x0, y0);
     else
-        stream_out<T, TX, TY, NT, MIXED, false>(a, s_rho, s_g, s_flag, x0, y0);
+        stream_out<T, TX, TY, NT, MIXED, false, PP>(a, s_rho, s_g, s_flag, x0, y0);
 #undef QPL
 #undef QSRC
 }
@@ -404,7 +422,7 @@ __device__ __forceinline__ int stage_load(const StepArgs<T>& a, T* s_rho, uint8_
 }
 
 // One time step of one TX x TY tile with origin (x0, y0); smem holds Layout<T, TX, TY>::bytes.
-template <typename T, int TX, int TY, int NT, bool MACRO>
+template <typename T, int TX, int TY, int NT, bool MACRO, bool PP>
 __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
                                           unsigned char* smem, int x0, int y0) {
     using L = Layout<T, TX, TY>;
@@ -415,15 +433,15 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
     uint8_t* s_flag = reinterpret_cast<uint8_t*>(s_g + 10 * CW * CH);
     const int any = stage_load<T, TX, TY, NT>(a, s_rho, s_flag, x0, y0);
     if (__syncthreads_or(any))
-        step_body<T, TX, TY, NT, MACRO, true>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
+        step_body<T, TX, TY, NT, MACRO, true, PP>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
     else
-        step_body<T, TX, TY, NT, MACRO, false>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
+        step_body<T, TX, TY, NT, MACRO, false, PP>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
 }
 
 template <typename T, int TX, int TY, int NT, bool MACRO, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs<T> a, const T rho_mid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_tile<T, TX, TY, NT, MACRO>(a, rho_mid, smem_raw, blockIdx.x * TX, blockIdx.y * TY);
+    step_tile<T, TX, TY, NT, MACRO, true>(a, rho_mid, smem_raw, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 }  // namespace stepdev
