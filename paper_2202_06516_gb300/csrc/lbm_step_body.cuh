@@ -394,8 +394,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
 }
 
 // (1) density and flags on x0-8 .. x0+TX+7, y0-7 .. y0+TY+6, four nodes per access; the pads
-// supply periodic images and wall rows, positions past the padded plane read as solid. Returns
-// non-zero in a thread that saw a non-fluid node.
+// supply periodic images and wall rows, positions past the padded plane read as solid. Returns,
+// in the thread's bits: 1 if it saw a non-fluid node, 2 if it saw a fluid node of the tile.
 template <typename T, int TX, int TY, int NT>
 __device__ __forceinline__ int stage_load(const StepArgs<T>& a, T* s_rho, uint8_t* s_flag, int x0,
                                           int y0) {
@@ -416,7 +416,10 @@ __device__ __forceinline__ int stage_load(const StepArgs<T>& a, T* s_rho, uint8_
             sr[0] = sr[1] = sr[2] = sr[3] = (T)0;
         }
         *reinterpret_cast<uint32_t*>(s_flag + r * RW + 4 * c4) = fl;
-        any |= fl != 0u;
+        any |= fl != 0u ? 1 : 0;
+        // a zero byte (fluid) among the four, inside the tile proper
+        const bool inside = r >= 7 && r < 7 + TY && c4 >= 2 && c4 < 2 + TX / 4;
+        if (inside && ((fl - 0x01010101u) & ~fl & 0x80808080u)) any |= 2;
     }
     return any;
 }
@@ -432,7 +435,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
     T* s_g = s_mu + MW * MH;
     uint8_t* s_flag = reinterpret_cast<uint8_t*>(s_g + 10 * CW * CH);
     const int any = stage_load<T, TX, TY, NT>(a, s_rho, s_flag, x0, y0);
-    if (__syncthreads_or(any))
+    const int mixed = __syncthreads_or(any & 1);
+    // a tile without fluid nodes (inside the disc or the wall rows) has nothing to write
+    if (!__syncthreads_or(any & 2)) return;
+    if (mixed)
         step_body<T, TX, TY, NT, MACRO, true, PP>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
     else
         step_body<T, TX, TY, NT, MACRO, false, PP>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);

@@ -97,8 +97,19 @@ def generate(ws, steps=20000, chunk=512):
     return np.concatenate(xs), np.concatenate(ts), np.concatenate(ms)
 
 
-def train(sur, x, t, m, epochs=20, batch=8, lr=1e-3, seed=0, log=None):
-    """Adam on the masked MSE; data held on the device (torch tensors as plain buffers)."""
+def lr_at(step, total, lr, warmup=200, schedule="warmcos"):
+    """Learning rate of step `step` of `total`: linear warm-up over `warmup` steps, then a cosine
+    decay to zero ("warmcos"), or constant ("const")."""
+    if schedule == "const":
+        return lr
+    w = min(1.0, (step + 1) / max(1, warmup))
+    return lr * w * 0.5 * (1.0 + np.cos(np.pi * step / max(1, total)))
+
+
+def train(sur, x, t, m, epochs=20, batch=8, lr=1e-3, seed=0, log=None, schedule="warmcos",
+          warmup=200):
+    """Adam on the masked MSE with the `lr_at` schedule; data held on the device (torch tensors
+    as plain buffers)."""
     import torch
     n = x.shape[0]
     # start the head at the mean target (logit of the mean liquid fraction)
@@ -112,13 +123,17 @@ def train(sur, x, t, m, epochs=20, batch=8, lr=1e-3, seed=0, log=None):
     rng = np.random.default_rng(seed)
     losses = []
     t0 = time.perf_counter()
+    total = epochs * (n // batch)
+    step = 0
     for ep in range(epochs):
         perm = rng.permutation(n)
         el = []
         for k in range(0, n - batch + 1, batch):
             idx = torch.tensor(perm[k:k + batch], device="cuda")
             xb, tb, mb = xd[idx].contiguous(), td[idx].contiguous(), md[idx].contiguous()
-            el.append(sur.train_step(xb.data_ptr(), tb.data_ptr(), mb.data_ptr(), batch, lr))
+            el.append(sur.train_step(xb.data_ptr(), tb.data_ptr(), mb.data_ptr(), batch,
+                                     lr_at(step, total, lr, warmup, schedule)))
+            step += 1
         losses.append(float(np.mean(el)))
         if log:
             log(f"epoch {ep} loss {losses[-1]:.5f} ({time.perf_counter() - t0:.1f}s)")

@@ -63,6 +63,18 @@ def test_create_validates_arguments():
     assert e.value.status == lbm.LBM_ERR_ARG
 
 
+def test_create_rejects_oversized_and_empty_lattices():
+    """A lattice whose nine padded planes would exceed 2^31 nodes, and an empty one, are argument
+    errors found on the host before any device work."""
+    from paper_2202_06516_gb300 import lbm
+    for nx, ny in [(60000, 60000), (0, 64), (64, 0)]:
+        p = lbm.lbm_params(nx, ny, 0, 0, 0, 0, 0, 0, 0, 0.7, 0.1, 0.0126, 1.0, 1.64, 1.54, 1.9,
+                           0, 0, 0, 0, None)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(p)
+        assert e.value.status == lbm.LBM_ERR_ARG, (nx, ny)
+
+
 def test_null_context_is_an_error_not_a_crash():
     from paper_2202_06516_gb300 import lbm
     L = lbm.lib()

@@ -281,3 +281,20 @@ def test_striped_wetting_and_pendent_gravity(lbm, oracle_mod):
     gl, gr = lat.measure()
     ol, orr, _ = ref.measure()
     assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-12)])
+def test_uniform_coexistence_state_stays_uniform(lbm, oracle_mod, precision, tol):
+    """Degenerate case: a uniform liquid at the coexistence density next to neutral walls is an
+    exact equilibrium; after 500 steps the density stays uniform to round-off and no flow
+    appears."""
+    O = oracle_mod
+    cfg, mx, _ = oracle_config(O, W.plain_small(), nx=64, ny=48, cx=32.0, R=12.0)
+    rho0 = np.full((cfg.ny, cfg.nx), mx["rho_l"])
+    lat = gpu_lattice(lbm, cfg, precision=precision, rho0=rho0)
+    lat.step(500)
+    flags = lat.geometry()[0][2:-2]
+    r = lat.rho()[flags == 0]
+    assert np.abs(r - mx["rho_l"]).max() / mx["rho_l"] < tol
+    ux, uy = lat.velocity()
+    assert max(np.abs(ux[flags == 0]).max(), np.abs(uy[flags == 0]).max()) < tol

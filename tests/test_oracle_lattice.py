@@ -189,6 +189,25 @@ def test_mass_conservation(oracle_mod):
     assert np.isfinite(s.rho()).all()
 
 
+@pytest.mark.parametrize("phase", ["liquid", "gas"])
+def test_uniform_coexistence_state_is_fixed_point(oracle_mod, phase):
+    """A uniform fluid at a coexistence density next to neutral walls (mu_w = k^2 psi'(rho_sat))
+    is an exact equilibrium: psi' of either coexistence density equals the wall value, so mu is
+    uniform, the Eq. 14 layers copy the fluid density, the force vanishes and the equilibrium
+    populations are a fixed point of collision and streaming."""
+    O = oracle_mod
+    cfg, mx, neutral = oracle_config(O, W.plain_small(), nx=64, ny=48, cx=32.0, R=12.0)
+    rho_c = mx["rho_l"] if phase == "liquid" else mx["rho_g"]
+    rho0 = np.full((cfg.ny, cfg.nx), rho_c)
+    s = O.Sim(cfg, rho0)
+    s.step(200)
+    r = s.rho()
+    fluid = s.ext()[2][2:-2] == 0
+    assert np.abs(r[fluid] - rho_c).max() / rho_c < 1e-10
+    ux, uy, _, _ = s.velocity_force()
+    assert np.abs(ux[fluid]).max() < 1e-12 and np.abs(uy[fluid]).max() < 1e-12
+
+
 # ------------------------------------------------------ thermodynamics (Eq. 7, 12, Maxwell)
 def test_flat_interface_coexistence(oracle_mod):
     """A flat liquid slab equilibrates at the Maxwell liquid density (0.5 %). The gas density
