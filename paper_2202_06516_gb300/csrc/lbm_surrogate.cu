@@ -434,26 +434,30 @@ bool tc_timed_out() {
     return t;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool AMN, bool BMN>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
-    using TS = lbm::sgtc::TcShape<BN, STAGES>;
+    using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
     static bool configured = false;
     if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            lbm::sgtc::k_gemm_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
+        const cudaError_t e =
+            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     int* flag = tc_flag().dev;
     if (!flag) return cudaErrorMemoryAllocation;
     dim3 grid((a.N + BN - 1) / BN, (a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM, splits);
-    lbm::sgtc::k_gemm_tc<BN, STAGES><<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
+    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN>
+        <<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
     return cudaGetLastError();
 }
 
-// C = A B^T with both operands K-major on the tcgen05 tensor cores. The N tile is the compiled
-// width that covers N with the fewest computed columns (ties: fewer tiles); wide tiles keep two
-// stages so that two CTAs share an SM and one's epilogue overlaps the other's MMAs.
+// C = A B on the tcgen05 tensor cores, each operand K-major or MN-major (AMN, BMN). The N tile
+// is the compiled width that covers N with the fewest computed columns (ties: fewer tiles);
+// wide tiles keep two stages so that two CTAs share an SM and one's epilogue overlaps the
+// other's MMAs.
+template <bool AMN, bool BMN>
 cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
     static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
     int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
@@ -466,29 +470,28 @@ cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
         }
     }
     switch (best) {
-        case 32: return launch_tc<32, 3>(st, a, splits);
-        case 64: return launch_tc<64, 3>(st, a, splits);
-        case 80: return launch_tc<80, 4>(st, a, splits);
-        case 128: return launch_tc<128, 3>(st, a, splits);
-        case 144: return launch_tc<144, 2>(st, a, splits);
-        case 192: return launch_tc<192, 2>(st, a, splits);
-        default: return launch_tc<256, 2>(st, a, splits);
+        case 32: return launch_tc<32, 3, AMN, BMN>(st, a, splits);
+        case 64: return launch_tc<64, 3, AMN, BMN>(st, a, splits);
+        case 80: return launch_tc<80, 4, AMN, BMN>(st, a, splits);
+        case 128: return launch_tc<128, 3, AMN, BMN>(st, a, splits);
+        case 144: return launch_tc<144, 2, AMN, BMN>(st, a, splits);
+        case 192: return launch_tc<192, 2, AMN, BMN>(st, a, splits);
+        default: return launch_tc<256, 2, AMN, BMN>(st, a, splits);
     }
 }
 
+// AK / BK: operand stored K-major (else MN-major)
 template <bool AK, bool BK>
 cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
-    if (AK && BK) return gemm_tc(st, a);
-    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
-    k_gemm_bf16<AK, BK><<<grid, GTHREADS, 0, st>>>(a);
-    return cudaGetLastError();
+    return gemm_tc<!AK, !BK>(st, a);
 }
 
-// Weight-gradient GEMM (C_out x 9 C_in, K = pixels): few output tiles and a very long K, so K
-// is split over up to 128 CTA slices whose FP32 partials are summed in a fixed order.
+// Weight-gradient GEMM (C_out x 9 C_in, K = pixels, both operands MN-major): few output tiles
+// and a very long K, so K is split over up to 128 CTA slices whose FP32 partials are summed in a
+// fixed order.
 cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
                        float* out) {
-    const int tiles = ((a.N + GBN - 1) / GBN) * ((a.M + GBM - 1) / GBM);
+    const int tiles = ((a.N + 255) / 256) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
     int splits = std::max(1, std::min(128, 2 * 152 / std::max(1, tiles)));
     const long long stride = (long long)a.M * a.ldc;
     while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
@@ -497,13 +500,13 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
         return gemm<false, false>(st, a);
     }
     int chunk = (a.K + splits - 1) / splits;
-    chunk = (chunk + GBK - 1) / GBK * GBK;
+    chunk = (chunk + lbm::sgtc::BK - 1) / lbm::sgtc::BK * lbm::sgtc::BK;
     splits = (a.K + chunk - 1) / chunk;
     a.Cf = scratch;
     a.kchunk = chunk;
     a.split_stride = stride;
-    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM, splits);
-    k_gemm_bf16<false, false><<<grid, GTHREADS, 0, st>>>(a);
+    cudaError_t e = gemm_tc<true, true>(st, a, splits);
+    if (e != cudaSuccess) return e;
     k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
     return cudaGetLastError();
 }

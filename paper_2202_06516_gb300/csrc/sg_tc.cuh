@@ -1,6 +1,8 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory) for the
-// surrogate network: C[M x N] = A[M x K] B[N x K]^T with both operands K-major (the forward
-// convolution Xcol W^T and, with a transposed weight copy, the data gradient dY W).
+// surrogate network: C[M x N] = sum_k A(m, k) B(n, k), each operand K-major (A[m][k], B[n][k])
+// or MN-major (A[k][m], B[k][n]): the forward convolution Xcol W^T and, with a transposed
+// weight copy, the data gradient dY W (both K-major), and the weight gradient dY^T Xcol (both
+// MN-major, K = pixels).
 //
 // One CTA of 128 threads computes a 128 x BN tile. All threads stage K-slices of 64 elements
 // into shared memory with cp.async, in the 128-byte-swizzled K-major layout the tensor core
@@ -30,14 +32,18 @@ __host__ __device__ constexpr int tmem_cols(int bn) {
     return bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool BMN = false>
 struct TcShape {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N of kind::f16 at M = 128");
     static constexpr int A_BYTES = BM * BK * 2;  // 16 KB
-    static constexpr int B_BYTES = BN * BK * 2;
+    // MN-major slices are whole 64-element swizzle atoms wide along M or N
+    static constexpr int B_BYTES = BMN ? (BN + 63) / 64 * 64 * BK * 2 : BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     // 1 KB alignment slack for the swizzle atoms, then the stages, mbarriers and the TMEM slot
-    static constexpr int RAW_BYTES = 1024 + STAGES * STAGE_BYTES + 8 * (STAGES + 1) + 16;
+    // (MN-major B: 16 KB of slack after the last slice, so that every address a slice
+    // descriptor can form stays inside this CTA's shared memory)
+    static constexpr int RAW_BYTES =
+        1024 + STAGES * STAGE_BYTES + 8 * (STAGES + 1) + 16 + (BMN ? 16384 : 0);
     // at least enough shared memory that the CTAs resident on one SM never ask for more than
     // the 512 tensor-memory columns together (an allocation beyond them would wait)
     static constexpr int TMEM_CTAS = 512 / tmem_cols(BN);
@@ -55,10 +61,19 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
            ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+// shared-memory descriptor: MN-major operand, 128-byte swizzle; atoms of 64 (M or N) x 8 (K)
+// elements, the 8 K-groups of one 64-wide block 1 KB apart (stride offset), blocks 8 KB apart
+// along M or N (leading offset)
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(8192 >> 4) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, each K-major (0) or
+// MN-major (1: the operand's transpose bit), M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn = 0, int b_mn = 0) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -152,9 +167,29 @@ __device__ __forceinline__ void load_slice(uint8_t* s, const __nv_bfloat16* g, i
     }
 }
 
-template <int BN, int STAGES>
+// one K-slice of 64 (K) x ROWS (M or N) elements of an MN-major operand (row k of the stored
+// matrix holds consecutive M or N indices) into the swizzled MN-major layout: element (mn, k) in
+// block mn / 64, K-group k / 8 (1 KB apart), row k % 8, 16-byte chunk ((mn % 64) / 8) ^ (k % 8);
+// positions past nrows or ke are zero-filled
+template <int ROWS>
+__device__ __forceinline__ void load_slice_mn(uint8_t* s, const __nv_bfloat16* g, int ld,
+                                              int row0, int nrows, int k0, int ke) {
+    constexpr int CPR = ROWS / 8;  // 16-byte chunks per stored row (ROWS % 8 == 0)
+    constexpr int CHUNKS = BK * CPR;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < CHUNKS; i += TC_THREADS) {
+        const int k = i / CPR, c = i - k * CPR;
+        const bool ok = (row0 + c * 8 < nrows) && (k0 + k < ke);
+        const __nv_bfloat16* src = ok ? g + (size_t)(k0 + k) * ld + row0 + c * 8 : g;
+        uint8_t* dst = s + (c >> 3) * (BK / 8 * 1024) + (k >> 3) * 1024 + (k & 7) * 128 +
+                       (((c & 7) ^ (k & 7)) << 4);
+        sg::cp_async16(dst, src, ok);
+    }
+}
+
+template <int BN, int STAGES, bool AMN = false, bool BMN = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
-    using S = TcShape<BN, STAGES>;
+    using S = TcShape<BN, STAGES, BMN>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     // 1 KB-aligned base of the stages (the swizzle pattern follows shared-memory address bits)
     const uint32_t raw = su32(smem_raw);
@@ -184,17 +219,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+    constexpr uint32_t IDESC = idesc_bf16(BM, BN, AMN ? 1 : 0, BMN ? 1 : 0);
 
     auto stage_a = [&](int s) { return base + s * S::STAGE_BYTES; };
     auto stage_b = [&](int s) { return base + s * S::STAGE_BYTES + S::A_BYTES; };
+    auto load = [&](int s, int k0) {
+        if (AMN)
+            load_slice_mn<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
+        else
+            load_slice<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
+        if (BMN)
+            load_slice_mn<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);
+        else
+            load_slice<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);
+    };
 
 #pragma unroll 1
     for (int p = 0; p < STAGES - 1; ++p) {
-        if (p < nk) {
-            load_slice<BM>(stage_a(p), g.A, g.lda, m0, g.M, kb + p * BK, ke);
-            load_slice<BN>(stage_b(p), g.B, g.ldb, n0, g.N, kb + p * BK, ke);
-        }
+        if (p < nk) load(p, kb + p * BK);
         sg::cp_async_commit();
     }
     bool ok = true;
@@ -208,9 +250,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
             tc_fence_after();
             const uint32_t a0 = su32(stage_a(s)), b0 = su32(stage_b(s));
 #pragma unroll
-            for (int j = 0; j < BK / 16; ++j)
-                tc_mma(tmem, desc_sw128(a0 + 32 * j), desc_sw128(b0 + 32 * j), IDESC,
-                       (kt > 0 || j > 0) ? 1u : 0u);
+            for (int j = 0; j < BK / 16; ++j) {
+                // K = 16 per MMA: 32 bytes along a K-major swizzle row, two 1 KB K-groups of an
+                // MN-major block
+                const uint64_t ad = AMN ? desc_sw128_mn(a0 + 2048 * j) : desc_sw128(a0 + 32 * j);
+                const uint64_t bd = BMN ? desc_sw128_mn(b0 + 2048 * j) : desc_sw128(b0 + 32 * j);
+                tc_mma(tmem, ad, bd, IDESC, (kt > 0 || j > 0) ? 1u : 0u);
+            }
             tc_commit(su32(bars + s));
         }
         const int nxt = kt + STAGES - 1;
@@ -224,10 +270,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                 break;
             }
         }
-        if (nxt < nk) {
-            load_slice<BM>(stage_a(nxt % STAGES), g.A, g.lda, m0, g.M, kb + nxt * BK, ke);
-            load_slice<BN>(stage_b(nxt % STAGES), g.B, g.ldb, n0, g.N, kb + nxt * BK, ke);
-        }
+        if (nxt < nk) load(nxt % STAGES, kb + nxt * BK);
         sg::cp_async_commit();
     }
     sg::cp_async_wait<0>();

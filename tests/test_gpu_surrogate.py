@@ -58,6 +58,26 @@ def test_gemm_tensor_core_shapes(env, M, N, K):
     assert err < max(2e-6, 2e-7 * np.sqrt(K)), err
 
 
+@pytest.mark.parametrize("ak,bk", [(0, 0), (1, 0), (0, 1)])
+@pytest.mark.parametrize("M,N,K", [(256, 576, 4096), (32, 288, 20000), (1000, 80, 200)])
+def test_gemm_tensor_core_mn_major(env, ak, bk, M, N, K):
+    """MN-major operands (the weight gradient's layout, K = pixels) on the tcgen05 kernel:
+    several 64-wide swizzle blocks along M and N, partial blocks, long and ragged K."""
+    torch, lbm = env
+    g = torch.Generator().manual_seed(3 * M + N + 7 * K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    want = A.double() @ B.double()
+    Ad = (A if ak else A.t()).contiguous().cuda()
+    Bd = (B.t() if bk else B).contiguous().cuda()
+    Cd = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    lbm.lbm_sg_gemm(Ad.data_ptr(), Bd.data_ptr(), M, N, K, ak, bk, K if ak else M,
+                    K if bk else N, Cd.data_ptr(), N)
+    torch.cuda.synchronize()
+    err = (Cd.double().cpu() - want).abs().max().item() / max(1.0, want.abs().max().item())
+    assert err < max(2e-6, 2e-7 * np.sqrt(K)), err
+
+
 def _case(seed=0, B=2, H=32, Wd=32, base=8):
     rng = np.random.default_rng(seed)
     x = np.zeros((B, H, Wd, 8), dtype=np.float32)
