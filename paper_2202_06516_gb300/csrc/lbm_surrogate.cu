@@ -434,13 +434,13 @@ bool tc_timed_out() {
     return t;
 }
 
-template <int BN, int STAGES, bool AMN, bool BMN>
+template <int BN, int STAGES, bool AMN, bool BMN, bool GATHER>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
     static bool configured = false;
     if (!configured) {
         const cudaError_t e =
-            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN>,
+            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GATHER>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -448,7 +448,7 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     int* flag = tc_flag().dev;
     if (!flag) return cudaErrorMemoryAllocation;
     dim3 grid((a.N + BN - 1) / BN, (a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM, splits);
-    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN>
+    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GATHER>
         <<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
     return cudaGetLastError();
 }
@@ -456,8 +456,8 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
 // C = A B on the tcgen05 tensor cores, each operand K-major or MN-major (AMN, BMN). The N tile
 // is the compiled width that covers N with the fewest computed columns (ties: fewer tiles);
 // wide tiles keep two stages so that two CTAs share an SM and one's epilogue overlaps the
-// other's MMAs.
-template <bool AMN, bool BMN>
+// other's MMAs. GATHER: A is the implicit im2col of a.conv (K-major operands only).
+template <bool AMN, bool BMN, bool GATHER = false>
 cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
     static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
     int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
@@ -470,13 +470,13 @@ cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
         }
     }
     switch (best) {
-        case 32: return launch_tc<32, 3, AMN, BMN>(st, a, splits);
-        case 64: return launch_tc<64, 3, AMN, BMN>(st, a, splits);
-        case 80: return launch_tc<80, 4, AMN, BMN>(st, a, splits);
-        case 128: return launch_tc<128, 3, AMN, BMN>(st, a, splits);
-        case 144: return launch_tc<144, 2, AMN, BMN>(st, a, splits);
-        case 192: return launch_tc<192, 2, AMN, BMN>(st, a, splits);
-        default: return launch_tc<256, 2, AMN, BMN>(st, a, splits);
+        case 32: return launch_tc<32, 3, AMN, BMN, GATHER>(st, a, splits);
+        case 64: return launch_tc<64, 3, AMN, BMN, GATHER>(st, a, splits);
+        case 80: return launch_tc<80, 4, AMN, BMN, GATHER>(st, a, splits);
+        case 128: return launch_tc<128, 3, AMN, BMN, GATHER>(st, a, splits);
+        case 144: return launch_tc<144, 2, AMN, BMN, GATHER>(st, a, splits);
+        case 192: return launch_tc<192, 2, AMN, BMN, GATHER>(st, a, splits);
+        default: return launch_tc<256, 2, AMN, BMN, GATHER>(st, a, splits);
     }
 }
 
@@ -630,20 +630,27 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         if (a.y == nullptr) return sfail(s, LBM_ERR_STATE, "surrogate: missing activation");
         const int Cin = c.C1 + c.C2;
         const long long P = (long long)B * c.H * c.W;
-        SCUDA(s, launch_im2col(s, c, B));
+        // implicit GEMM: the 3 x 3 neighbourhoods are gathered from the activations by the
+        // tensor-core kernel's loader (no im2col buffer)
         GemmArgs g{};
-        g.A = s->col;
+        g.conv.x1 = a.y;
+        g.conv.x2 = c.src2 >= 0 ? s->t[c.src2].y : nullptr;
+        g.conv.C1 = c.C1;
+        g.conv.C2 = c.C2;
+        g.conv.up1 = c.up1;
+        g.conv.H = c.H;
+        g.conv.W = c.W;
+        g.conv.lc = ilog2_exact(Cin);
         g.B = s->wb + c.w_off;
         g.M = (int)P;
         g.N = c.Cout;
         g.K = 9 * Cin;
-        g.lda = 9 * Cin;
         g.ldb = 9 * Cin;
         g.Cb = s->t[c.out].y;
         g.ldc = c.Cout;
         g.bias = s->w + c.b_off;
         g.relu = 1;
-        SCUDA(s, (gemm<true, true>(s->stream, g)));
+        SCUDA(s, (gemm_tc<false, false, true>(s->stream, g)));
         // a pool whose source is this conv's output runs right after it
         for (const auto& pl : s->pools)
             if (pl.first == c.out) {

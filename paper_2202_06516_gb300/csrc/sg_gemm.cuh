@@ -12,6 +12,18 @@
 namespace lbm {
 namespace sg {
 
+// A operand gathered straight from NHWC activations (implicit im2col of a 3 x 3, pad-1
+// convolution): A[p][(ky * 3 + kx) * C + c] = x(n, y + ky - 1, x + kx - 1, c) for output pixel
+// p = (n, y, x), with channels [source 1 | source 2]; source 1 may be stored at half resolution
+// (nearest 2x upsampling). C = C1 + C2 = 2^lc; C1 and C2 multiples of 8.
+struct ConvGather {
+    const __nv_bfloat16* x1;
+    const __nv_bfloat16* x2;  // nullptr when C2 = 0
+    int C1, C2, up1;
+    int H, W;                 // output (full) resolution
+    int lc;
+};
+
 struct GemmArgs {
     const __nv_bfloat16* A;
     const __nv_bfloat16* B;
@@ -26,6 +38,7 @@ struct GemmArgs {
     int kchunk;        // split-K: blockIdx.z covers K range [z kchunk, (z + 1) kchunk); its FP32
                        // result goes to Cf + z * split_stride (0: no split)
     long long split_stride;
+    ConvGather conv;   // used instead of A by the gathering (implicit-convolution) kernel
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -187,7 +187,36 @@ __device__ __forceinline__ void load_slice_mn(uint8_t* s, const __nv_bfloat16* g
     }
 }
 
-template <int BN, int STAGES, bool AMN = false, bool BMN = false>
+// One K-slice of 128 rows (output pixels m0 ..) x 64 (K) of the gathered convolution operand
+// (see sg::ConvGather), in the K-major swizzled layout of load_slice. Thread t always fills the
+// 16-byte chunk column t % 8 of rows t / 8 + 16 j (j = 0..7), whose pixel coordinates it keeps
+// in yx[j] (y | x << 16) and nn[j] (image index, -1 past M).
+__device__ __forceinline__ void load_slice_conv(uint8_t* s, const sg::ConvGather& cv,
+                                                const int* yx, const int* nn, int k0, int ke) {
+    const int c = threadIdx.x & 7;
+    const int k = k0 + c * 8;
+    const bool kok = k < ke;
+    const int tap = k >> cv.lc, ci = k & ((1 << cv.lc) - 1);
+    const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+    const int h1 = cv.H >> cv.up1, w1 = cv.W >> cv.up1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int r = (threadIdx.x >> 3) + 16 * j;
+        const int y = (yx[j] & 0xFFFF) + dy, x = (yx[j] >> 16) + dx, n = nn[j];
+        const bool ok = kok && n >= 0 && y >= 0 && y < cv.H && x >= 0 && x < cv.W;
+        const __nv_bfloat16* src = cv.x1;
+        if (ok) {
+            if (ci < cv.C1)
+                src = cv.x1 + ((((size_t)n * h1 + (y >> cv.up1)) * w1 + (x >> cv.up1)) * cv.C1 + ci);
+            else
+                src = cv.x2 + ((((size_t)n * cv.H + y) * cv.W + x) * cv.C2 + (ci - cv.C1));
+        }
+        uint8_t* dst = s + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+        sg::cp_async16(dst, src, ok);
+    }
+}
+
+template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GATHER = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
     using S = TcShape<BN, STAGES, BMN>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -223,8 +252,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
 
     auto stage_a = [&](int s) { return base + s * S::STAGE_BYTES; };
     auto stage_b = [&](int s) { return base + s * S::STAGE_BYTES + S::A_BYTES; };
+    // GATHER: pixel coordinates of the thread's eight A rows, fixed for all K-slices
+    int yx[8], nn[8];
+    if (GATHER) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int p = m0 + (tid >> 3) + 16 * j;
+            const int x = p % g.conv.W, q = p / g.conv.W, y = q % g.conv.H;
+            yx[j] = y | (x << 16);
+            nn[j] = p < g.M ? q / g.conv.H : -1;
+        }
+    }
     auto load = [&](int s, int k0) {
-        if (AMN)
+        if (GATHER)
+            load_slice_conv(stage_a(s), g.conv, yx, nn, k0, ke);
+        else if (AMN)
             load_slice_mn<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
         else
             load_slice<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
