@@ -434,13 +434,13 @@ bool tc_timed_out() {
     return t;
 }
 
-template <int BN, int STAGES, bool AMN, bool BMN, bool GATHER>
+template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GB>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
     static bool configured = false;
     if (!configured) {
         const cudaError_t e =
-            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GATHER>,
+            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -448,7 +448,7 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     int* flag = tc_flag().dev;
     if (!flag) return cudaErrorMemoryAllocation;
     dim3 grid((a.N + BN - 1) / BN, (a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM, splits);
-    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GATHER>
+    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB>
         <<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
     return cudaGetLastError();
 }
@@ -456,8 +456,8 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
 // C = A B on the tcgen05 tensor cores, each operand K-major or MN-major (AMN, BMN). The N tile
 // is the compiled width that covers N with the fewest computed columns (ties: fewer tiles);
 // wide tiles keep two stages so that two CTAs share an SM and one's epilogue overlaps the
-// other's MMAs. GATHER: A is the implicit im2col of a.conv (K-major operands only).
-template <bool AMN, bool BMN, bool GATHER = false>
+// other's MMAs. GA / GB: A (K-major) / B (MN-major) is the implicit im2col of a.conv.
+template <bool AMN, bool BMN, bool GA = false, bool GB = false>
 cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
     static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
     int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
@@ -470,13 +470,13 @@ cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
         }
     }
     switch (best) {
-        case 32: return launch_tc<32, 3, AMN, BMN, GATHER>(st, a, splits);
-        case 64: return launch_tc<64, 3, AMN, BMN, GATHER>(st, a, splits);
-        case 80: return launch_tc<80, 4, AMN, BMN, GATHER>(st, a, splits);
-        case 128: return launch_tc<128, 3, AMN, BMN, GATHER>(st, a, splits);
-        case 144: return launch_tc<144, 2, AMN, BMN, GATHER>(st, a, splits);
-        case 192: return launch_tc<192, 2, AMN, BMN, GATHER>(st, a, splits);
-        default: return launch_tc<256, 2, AMN, BMN, GATHER>(st, a, splits);
+        case 32: return launch_tc<32, 3, AMN, BMN, GA, GB>(st, a, splits);
+        case 64: return launch_tc<64, 3, AMN, BMN, GA, GB>(st, a, splits);
+        case 80: return launch_tc<80, 4, AMN, BMN, GA, GB>(st, a, splits);
+        case 128: return launch_tc<128, 3, AMN, BMN, GA, GB>(st, a, splits);
+        case 144: return launch_tc<144, 2, AMN, BMN, GA, GB>(st, a, splits);
+        case 192: return launch_tc<192, 2, AMN, BMN, GA, GB>(st, a, splits);
+        default: return launch_tc<256, 2, AMN, BMN, GA, GB>(st, a, splits);
     }
 }
 
@@ -489,15 +489,16 @@ cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
 // Weight-gradient GEMM (C_out x 9 C_in, K = pixels, both operands MN-major): few output tiles
 // and a very long K, so K is split over up to 128 CTA slices whose FP32 partials are summed in a
 // fixed order.
+// gather: B is the implicit im2col of a.conv (else the im2col buffer a.B).
 cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
-                       float* out) {
+                       float* out, bool gather) {
     const int tiles = ((a.N + 255) / 256) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
     int splits = std::max(1, std::min(128, 2 * 152 / std::max(1, tiles)));
     const long long stride = (long long)a.M * a.ldc;
     while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
     if (splits == 1) {
         a.Cf = out;
-        return gemm<false, false>(st, a);
+        return gather ? gemm_tc<true, true, false, true>(st, a) : gemm_tc<true, true>(st, a);
     }
     int chunk = (a.K + splits - 1) / splits;
     chunk = (chunk + lbm::sgtc::BK - 1) / lbm::sgtc::BK * lbm::sgtc::BK;
@@ -505,7 +506,8 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     a.Cf = scratch;
     a.kchunk = chunk;
     a.split_stride = stride;
-    cudaError_t e = gemm_tc<true, true>(st, a, splits);
+    cudaError_t e = gather ? gemm_tc<true, true, false, true>(st, a, splits)
+                           : gemm_tc<true, true>(st, a, splits);
     if (e != cudaSuccess) return e;
     k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
     return cudaGetLastError();
@@ -650,7 +652,7 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         g.ldc = c.Cout;
         g.bias = s->w + c.b_off;
         g.relu = 1;
-        SCUDA(s, (gemm_tc<false, false, true>(s->stream, g)));
+        SCUDA(s, (gemm_tc<false, false, true, false>(s->stream, g)));
         // a pool whose source is this conv's output runs right after it
         for (const auto& pl : s->pools)
             if (pl.first == c.out) {
@@ -855,9 +857,21 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         const int cb = std::min<long long>(s->part_blocks, Pc);
         k_colsum_partial<<<cb, kT, 0, s->stream>>>(s->gmask, Pc, c.Cout, s->part);
         k_colsum_final<<<c.Cout, kT, 0, s->stream>>>(s->part, cb, c.Cout, s->g + c.b_off);
-        // weight gradient: dW[co][k] = sum_p g[p][co] col[p][k]
-        SCUDA(s, launch_im2col(s, c, B));
+        // weight gradient: dW[co][k] = sum_p g[p][co] col[p][k], the im2col columns gathered by
+        // the GEMM's loader when the resolution allows (powers of two), else from a buffer
         GemmArgs gw{};
+        gw.conv.x1 = s->t[c.src1].y;
+        gw.conv.x2 = c.src2 >= 0 ? s->t[c.src2].y : nullptr;
+        gw.conv.C1 = c.C1;
+        gw.conv.C2 = c.C2;
+        gw.conv.up1 = c.up1;
+        gw.conv.H = c.H;
+        gw.conv.W = c.W;
+        gw.conv.lc = ilog2_exact(Cin);
+        gw.conv.lh = ilog2_exact(c.H);
+        gw.conv.lw = ilog2_exact(c.W);
+        const bool gather = gw.conv.lh >= 0 && gw.conv.lw >= 0;
+        if (!gather) SCUDA(s, launch_im2col(s, c, B));
         gw.A = s->gmask;
         gw.B = s->col;
         gw.M = c.Cout;
@@ -866,7 +880,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         gw.lda = c.Cout;
         gw.ldb = 9 * Cin;
         gw.ldc = 9 * Cin;
-        SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off));
+        SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off, gather));
         // data gradient (not needed for the input tensor)
         if (c.src1 == 0) continue;
         GemmArgs gd{};

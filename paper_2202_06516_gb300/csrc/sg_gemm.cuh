@@ -22,6 +22,7 @@ struct ConvGather {
     int C1, C2, up1;
     int H, W;                 // output (full) resolution
     int lc;
+    int lh, lw;               // log2 H, log2 W (the pixel-major gather needs powers of two)
 };
 
 struct GemmArgs {
@@ -38,7 +39,7 @@ struct GemmArgs {
     int kchunk;        // split-K: blockIdx.z covers K range [z kchunk, (z + 1) kchunk); its FP32
                        // result goes to Cf + z * split_stride (0: no split)
     long long split_stride;
-    ConvGather conv;   // used instead of A by the gathering (implicit-convolution) kernel
+    ConvGather conv;   // used instead of A (or B) by the gathering (implicit-convolution) kernel
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -216,7 +216,40 @@ __device__ __forceinline__ void load_slice_conv(uint8_t* s, const sg::ConvGather
     }
 }
 
-template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GATHER = false>
+// One K-slice of 64 pixels (K) x ROWS im2col columns (N: (tap, channel) of the gathered
+// convolution operand, see sg::ConvGather) in the MN-major swizzled layout of load_slice_mn:
+// the B operand of the weight gradient, whose K runs over the pixels. H and W are powers of two.
+template <int ROWS>
+__device__ __forceinline__ void load_slice_mn_conv(uint8_t* s, const sg::ConvGather& cv,
+                                                   int row0, int nrows, int k0, int ke) {
+    constexpr int CPR = ROWS / 8;
+    constexpr int CHUNKS = BK * CPR;
+    const int h1 = cv.H >> cv.up1, w1 = cv.W >> cv.up1;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < CHUNKS; i += TC_THREADS) {
+        const int k = i / CPR, c = i - k * CPR;
+        const int p = k0 + k, col = row0 + c * 8;
+        const int tap = col >> cv.lc, ci = col & ((1 << cv.lc) - 1);
+        const int y = ((p >> cv.lw) & (cv.H - 1)) + tap / 3 - 1;
+        const int x = (p & (cv.W - 1)) + tap - (tap / 3) * 3 - 1;
+        const int n = p >> (cv.lw + cv.lh);
+        const bool ok = p < ke && col < nrows && y >= 0 && y < cv.H && x >= 0 && x < cv.W;
+        const __nv_bfloat16* src = cv.x1;
+        if (ok) {
+            if (ci < cv.C1)
+                src = cv.x1 + ((((size_t)n * h1 + (y >> cv.up1)) * w1 + (x >> cv.up1)) * cv.C1 + ci);
+            else
+                src = cv.x2 + ((((size_t)n * cv.H + y) * cv.W + x) * cv.C2 + (ci - cv.C1));
+        }
+        uint8_t* dst = s + (c >> 3) * (BK / 8 * 1024) + (k >> 3) * 1024 + (k & 7) * 128 +
+                       (((c & 7) ^ (k & 7)) << 4);
+        sg::cp_async16(dst, src, ok);
+    }
+}
+
+// GA: A is the gathered convolution operand (K-major, rows = output pixels); GB: B is the
+// gathered operand (MN-major, K = pixels).
+template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GB = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
     using S = TcShape<BN, STAGES, BMN>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -252,9 +285,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
 
     auto stage_a = [&](int s) { return base + s * S::STAGE_BYTES; };
     auto stage_b = [&](int s) { return base + s * S::STAGE_BYTES + S::A_BYTES; };
-    // GATHER: pixel coordinates of the thread's eight A rows, fixed for all K-slices
+    // GA: pixel coordinates of the thread's eight A rows, fixed for all K-slices
     int yx[8], nn[8];
-    if (GATHER) {
+    if (GA) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int p = m0 + (tid >> 3) + 16 * j;
@@ -264,13 +297,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
         }
     }
     auto load = [&](int s, int k0) {
-        if (GATHER)
+        if (GA)
             load_slice_conv(stage_a(s), g.conv, yx, nn, k0, ke);
         else if (AMN)
             load_slice_mn<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
         else
             load_slice<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
-        if (BMN)
+        if (GB)
+            load_slice_mn_conv<BN>(stage_b(s), g.conv, n0, g.N, k0, ke);
+        else if (BMN)
             load_slice_mn<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);
         else
             load_slice<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);

@@ -96,7 +96,7 @@ def _bf16(a):
     return torch.tensor(a).to(torch.bfloat16).double().numpy()
 
 
-@pytest.mark.parametrize("base,H", [(8, 32), (16, 64), (32, 64)])
+@pytest.mark.parametrize("base,H", [(8, 32), (8, 48), (16, 64), (32, 64)])
 def test_forward_loss_gradients_match_oracle(env, base, H):
     torch, lbm = env
     from oracle import surrogate as S
