@@ -8,8 +8,11 @@
 //   decoder   2x upsampling folded into the next conv3x3 (nearest), the skip concatenation folded
 //             into the following conv3x3 (two-source im2col), conv3x3 + leaky ReLU twice per level
 //   head      1x1 conv to one channel, sigmoid: phi = (rho - rho_g) / (rho_l - rho_g)
-// Activations BF16 NHWC, weights FP32 masters with BF16 copies, all contractions on tensor cores
-// through one BF16 GEMM with FP32 accumulation (sg_gemm.cuh) over im2col / col2im buffers.
+// Activations BF16 NHWC, weights FP32 masters with BF16 copies, all contractions on the tcgen05
+// tensor cores with FP32 accumulation in tensor memory (sg_tc.cuh), as implicit GEMMs whose
+// loaders gather the 3 x 3 neighbourhoods from the activations: the forward convolution, the
+// weight gradient (pixels as K; an im2col buffer only when the resolution is not a power of two)
+// and the data gradient (output gradients gathered around each source pixel).
 // Loss: masked mean squared error on phi. Optimiser: Adam.
 #include <math.h>
 
@@ -60,28 +63,6 @@ __device__ __forceinline__ void pix_split(int p, const PixDims& d, int& n, int& 
     }
 }
 
-__device__ __forceinline__ void add8(float* s, const uint4& v) {
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float2 f = __bfloat1622float2(h[i]);
-        s[2 * i] += f.x;
-        s[2 * i + 1] += f.y;
-    }
-}
-
-__device__ __forceinline__ void store8(float* dst, const float* s, int acc) {
-    float4* d = reinterpret_cast<float4*>(dst);
-    float4 a = make_float4(s[0], s[1], s[2], s[3]), b = make_float4(s[4], s[5], s[6], s[7]);
-    if (acc) {
-        const float4 o0 = d[0], o1 = d[1];
-        a.x += o0.x; a.y += o0.y; a.z += o0.z; a.w += o0.w;
-        b.x += o1.x; b.y += o1.y; b.z += o1.z; b.w += o1.w;
-    }
-    d[0] = a;
-    d[1] = b;
-}
-
 // im2col of a 3x3, pad-1 convolution whose input channels are [source 1 | source 2]:
 // col[p][(ky*3+kx)*C + c] = x(n, y+ky-1, x+kx-1, c). Source 1 may be stored at half resolution
 // (up1 = 1: nearest 2x upsampling on the fly). Eight channels per thread (16-byte accesses); the
@@ -112,53 +93,6 @@ __global__ void k_im2col(const bf16* x1, int C1, int up1, const bf16* x2, int C2
             }
         }
         *reinterpret_cast<uint4*>(col + (size_t)t * 8) = v;
-    }
-}
-
-// col2im (adjoint of k_im2col) into FP32 gradients of the two sources; accumulates when asked.
-// Eight channels per thread: (C1 / 8) = 2^l1 groups per pixel of source 1 (at d1 resolution),
-// (C2 / 8) = 2^l2 of source 2 (C2 = 0: none). Taps are summed in the order of k_im2col's
-// columns, so every element is the same sum as a scalar gather.
-template <bool P2>
-__global__ void k_col2im(const bf16* dcol, int C1, int up1, float* dx1, int acc1, int C2,
-                         float* dx2, int acc2, PixDims d, PixDims d1, int B, int l1, int l2) {
-    const int C = C1 + C2;
-    const long long n1 = (long long)B * d1.H * d1.W << l1;
-    const long long n2 = C2 > 0 ? (long long)B * d.H * d.W << l2 : 0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n1 + n2;
-         t += (long long)gridDim.x * blockDim.x) {
-        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (t < n1) {
-            const int q = (int)(t >> l1), c = (int)(t & ((1 << l1) - 1)) * 8;
-            int n, Y, X;
-            pix_split<P2>(q, d1, n, Y, X);
-            const int f = up1 ? 2 : 1;
-            for (int dy = 0; dy < f; ++dy)
-                for (int dxo = 0; dxo < f; ++dxo) {
-                    const int yy = Y * f + dy, xx = X * f + dxo;
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int py = yy - (tap / 3 - 1), px = xx - (tap % 3 - 1);
-                        if (py < 0 || py >= d.H || px < 0 || px >= d.W) continue;
-                        add8(s, *reinterpret_cast<const uint4*>(
-                                    dcol + (((size_t)n * d.H + py) * d.W + px) * 9 * C + tap * C + c));
-                    }
-                }
-            store8(dx1 + t * 8, s, acc1);
-        } else {
-            const long long u = t - n1;
-            const int q = (int)(u >> l2), c = (int)(u & ((1 << l2) - 1)) * 8;
-            int n, yy, xx;
-            pix_split<P2>(q, d, n, yy, xx);
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int py = yy - (tap / 3 - 1), px = xx - (tap % 3 - 1);
-                if (py < 0 || py >= d.H || px < 0 || px >= d.W) continue;
-                add8(s, *reinterpret_cast<const uint4*>(
-                            dcol + (((size_t)n * d.H + py) * d.W + px) * 9 * C + tap * C + C1 + c));
-            }
-            store8(dx2 + u * 8, s, acc2);
-        }
     }
 }
 
@@ -322,13 +256,15 @@ __global__ void k_to_bf16(const float* x, bf16* y, long long n) {
         y[t] = __float2bfloat16_rn(x[t]);
 }
 
-// W^T of one convolution: wt[k * cout + co] = w[co * kc + k] (kc = 9 C_in)
-__global__ void k_transpose_w(const bf16* w, bf16* wt, int cout, int kc) {
-    const long long n = (long long)cout * kc;
+// Data-gradient weights of one convolution: wd[ci][tap][co] = w[co][tap][ci], i.e. for each
+// input channel the 9 C_out weights it contributes to, (tap, co) contiguous.
+__global__ void k_dgrad_weights(const bf16* w, bf16* wd, int cout, int cin) {
+    const long long n = (long long)cin * 9 * cout;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / cout), co = (int)(i - (long long)k * cout);
-        wt[i] = w[(size_t)co * kc + k];
+        const int ci = (int)(i / (9 * cout)), rem = (int)(i - (long long)ci * 9 * cout);
+        const int tap = rem / cout, co = rem - tap * cout;
+        wd[i] = w[(size_t)co * 9 * cin + tap * cin + ci];
     }
 }
 
@@ -363,8 +299,8 @@ struct lbm_surrogate {
     size_t nparams = 0;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     bf16* wb = nullptr;
-    bf16* wbt = nullptr;        // per convolution W^T [9 C_in][C_out] (data-gradient operand)
-    bf16 *col = nullptr, *dcol = nullptr, *gmask = nullptr;
+    bf16* wbd = nullptr;        // per convolution [C_in][tap][C_out] (data-gradient operand)
+    bf16 *col = nullptr, *gmask = nullptr;
     size_t col_elems = 0, act_elems = 0;
     float* part = nullptr;  // reduction partials
     float* phi = nullptr;   // head output
@@ -434,13 +370,13 @@ bool tc_timed_out() {
     return t;
 }
 
-template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GB>
+template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GB, bool GD>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
     static bool configured = false;
     if (!configured) {
         const cudaError_t e =
-            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB>,
+            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB, GD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -448,7 +384,7 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     int* flag = tc_flag().dev;
     if (!flag) return cudaErrorMemoryAllocation;
     dim3 grid((a.N + BN - 1) / BN, (a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM, splits);
-    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB>
+    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB, GD>
         <<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
     return cudaGetLastError();
 }
@@ -456,8 +392,9 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
 // C = A B on the tcgen05 tensor cores, each operand K-major or MN-major (AMN, BMN). The N tile
 // is the compiled width that covers N with the fewest computed columns (ties: fewer tiles);
 // wide tiles keep two stages so that two CTAs share an SM and one's epilogue overlaps the
-// other's MMAs. GA / GB: A (K-major) / B (MN-major) is the implicit im2col of a.conv.
-template <bool AMN, bool BMN, bool GA = false, bool GB = false>
+// other's MMAs. GA / GB: A (K-major) / B (MN-major) is the implicit im2col of a.conv; GD: A is
+// the gathered data-gradient operand a.dg.
+template <bool AMN, bool BMN, bool GA = false, bool GB = false, bool GD = false>
 cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
     static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
     int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
@@ -470,13 +407,13 @@ cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
         }
     }
     switch (best) {
-        case 32: return launch_tc<32, 3, AMN, BMN, GA, GB>(st, a, splits);
-        case 64: return launch_tc<64, 3, AMN, BMN, GA, GB>(st, a, splits);
-        case 80: return launch_tc<80, 4, AMN, BMN, GA, GB>(st, a, splits);
-        case 128: return launch_tc<128, 3, AMN, BMN, GA, GB>(st, a, splits);
-        case 144: return launch_tc<144, 2, AMN, BMN, GA, GB>(st, a, splits);
-        case 192: return launch_tc<192, 2, AMN, BMN, GA, GB>(st, a, splits);
-        default: return launch_tc<256, 2, AMN, BMN, GA, GB>(st, a, splits);
+        case 32: return launch_tc<32, 3, AMN, BMN, GA, GB, GD>(st, a, splits);
+        case 64: return launch_tc<64, 3, AMN, BMN, GA, GB, GD>(st, a, splits);
+        case 80: return launch_tc<80, 4, AMN, BMN, GA, GB, GD>(st, a, splits);
+        case 128: return launch_tc<128, 3, AMN, BMN, GA, GB, GD>(st, a, splits);
+        case 144: return launch_tc<144, 2, AMN, BMN, GA, GB, GD>(st, a, splits);
+        case 192: return launch_tc<192, 2, AMN, BMN, GA, GB, GD>(st, a, splits);
+        default: return launch_tc<256, 2, AMN, BMN, GA, GB, GD>(st, a, splits);
     }
 }
 
@@ -513,15 +450,15 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     return cudaGetLastError();
 }
 
-// BF16 copies of the weights (after the FP32 masters changed): W for the forward pass, W^T for
-// the data gradient
+// BF16 copies of the weights (after the FP32 masters changed): W for the forward pass and the
+// weight gradient, the rearranged copy for the data gradient
 cudaError_t refresh_bf16_weights(lbm_surrogate* s) {
     k_to_bf16<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(s->w, s->wb,
                                                                        (long long)s->nparams);
     for (const Conv& c : s->convs) {
-        const int kc = 9 * (c.C1 + c.C2);
-        k_transpose_w<<<blocks_for((long long)c.Cout * kc), kT, 0, s->stream>>>(
-            s->wb + c.w_off, s->wbt + c.w_off, c.Cout, kc);
+        const int cin = c.C1 + c.C2;
+        k_dgrad_weights<<<blocks_for((long long)c.Cout * 9 * cin), kT, 0, s->stream>>>(
+            s->wb + c.w_off, s->wbd + c.w_off, c.Cout, cin);
     }
     return cudaGetLastError();
 }
@@ -548,25 +485,6 @@ cudaError_t launch_im2col(lbm_surrogate* s, const Conv& c, int B) {
     else
         k_im2col<false><<<blocks_for(total), kT, 0, s->stream>>>(x1, c.C1, c.up1, x2, c.C2, d, P,
                                                                  lc8, s->col);
-    return cudaGetLastError();
-}
-
-// col2im of convolution c from s->dcol, accumulated into the sources' gradients
-cudaError_t launch_col2im(lbm_surrogate* s, const Conv& c, int B) {
-    const PixDims d = pix_dims(c.H, c.W);
-    const PixDims d1 = c.up1 ? pix_dims(c.H / 2, c.W / 2) : d;
-    const int l1 = ilog2_exact(c.C1 / 8), l2 = c.C2 > 0 ? ilog2_exact(c.C2 / 8) : 0;
-    const long long n = ((long long)B * d1.H * d1.W << l1) +
-                        (c.C2 > 0 ? ((long long)B * d.H * d.W << l2) : 0);
-    float* dx2 = c.src2 >= 0 ? s->t[c.src2].dy : nullptr;
-    if (d.lh >= 0 && d.lw >= 0 && d1.lh >= 0 && d1.lw >= 0)
-        k_col2im<true><<<blocks_for(n), kT, 0, s->stream>>>(s->dcol, c.C1, c.up1,
-                                                            s->t[c.src1].dy, 1, c.C2, dx2, 1, d,
-                                                            d1, B, l1, l2);
-    else
-        k_col2im<false><<<blocks_for(n), kT, 0, s->stream>>>(s->dcol, c.C1, c.up1,
-                                                             s->t[c.src1].dy, 1, c.C2, dx2, 1, d,
-                                                             d1, B, l1, l2);
     return cudaGetLastError();
 }
 
@@ -710,9 +628,8 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->m, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->v, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->wb, np * sizeof(bf16));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->wbt, np * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->wbd, np * sizeof(bf16));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->col, colmax * sizeof(bf16));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->dcol, colmax * sizeof(bf16));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->gmask, s->act_elems * sizeof(bf16));
     if (e == cudaSuccess)
         e = cudaMalloc((void**)&s->part, (size_t)s->part_blocks * 8 * base * sizeof(float));
@@ -727,7 +644,7 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, np * sizeof(float), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, np * sizeof(float), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->wb, 0, np * sizeof(bf16), s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->wbt, 0, np * sizeof(bf16), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->wbd, 0, np * sizeof(bf16), s->stream);
     if (e != cudaSuccess) return cleanup(cudaGetErrorString(e));
     *out = s;
     return LBM_OK;
@@ -883,18 +800,30 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off, gather));
         // data gradient (not needed for the input tensor)
         if (c.src1 == 0) continue;
+        // implicit GEMM over the source pixels: dX_src[q][ci] += sum over (sub-pixel, tap, co)
+        // of dY gathered around q times the rearranged weights (no col buffer, no col2im)
+        if (c.up1 && c.C2 > 0) return sfail(s, LBM_ERR_STATE, "surrogate: upsampled cat source");
         GemmArgs gd{};
-        gd.A = s->gmask;
-        gd.B = s->wbt + c.w_off;   // W^T [9 C_in][C_out]: both operands K-major
-        gd.M = (int)Pc;
-        gd.N = 9 * Cin;
-        gd.K = c.Cout;
-        gd.lda = c.Cout;
-        gd.ldb = c.Cout;
-        gd.Cb = s->dcol;
-        gd.ldc = 9 * Cin;
-        SCUDA(s, (gemm<true, true>(s->stream, gd)));
-        SCUDA(s, launch_col2im(s, c, B));
+        gd.dg.dy = s->gmask;
+        gd.dg.H = c.H;
+        gd.dg.W = c.W;
+        gd.dg.lco = ilog2_exact(c.Cout);
+        gd.dg.up1 = c.up1;
+        gd.B = s->wbd + c.w_off;
+        gd.ldb = 9 * c.Cout;
+        gd.kperiod = c.up1 ? 9 * c.Cout : 0;
+        gd.M = (int)((long long)B * (c.H >> c.up1) * (c.W >> c.up1));
+        gd.N = Cin;
+        gd.K = (c.up1 ? 36 : 9) * c.Cout;
+        gd.Cf = s->t[c.src1].dy;
+        gd.ldc = c.C1;
+        gd.accumulate = 1;
+        if (c.C2 > 0) {
+            gd.Cf2 = s->t[c.src2].dy;
+            gd.ldc2 = c.C2;
+            gd.nsplit = c.C1;
+        }
+        SCUDA(s, (gemm_tc<false, false, false, false, true>(s->stream, gd)));
     }
     if (lr > 0.f) {
         ++s->adam_t;
@@ -972,9 +901,8 @@ void lbm_surrogate_destroy(lbm_surrogate* s) {
     cudaFree(s->m);
     cudaFree(s->v);
     cudaFree(s->wb);
-    cudaFree(s->wbt);
+    cudaFree(s->wbd);
     cudaFree(s->col);
-    cudaFree(s->dcol);
     cudaFree(s->gmask);
     cudaFree(s->part);
     cudaFree(s->phi);

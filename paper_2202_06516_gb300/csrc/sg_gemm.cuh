@@ -25,6 +25,18 @@ struct ConvGather {
     int lh, lw;               // log2 H, log2 W (the pixel-major gather needs powers of two)
 };
 
+// A operand of the data gradient gathered from the output gradient dY (NHWC, full resolution
+// H x W, Cout = 2^lco channels): rows are pixels q of the source (full resolution, or half
+// resolution when up1) and A[q][((s * 9) + tap) * Cout + co] = dY(f q + s - off(tap))[co], with
+// off(tap) = (tap / 3 - 1, tap % 3 - 1), f = 2 and the 2 x 2 sub-pixel s = (sy, sx) when up1
+// (the nearest upsampling's adjoint sums them), f = 1 and s = 0 otherwise; 0 outside the image.
+struct DgradGather {
+    const __nv_bfloat16* dy;
+    int H, W;      // output resolution of the convolution
+    int lco;       // log2 Cout
+    int up1;
+};
+
 struct GemmArgs {
     const __nv_bfloat16* A;
     const __nv_bfloat16* B;
@@ -40,6 +52,10 @@ struct GemmArgs {
                        // result goes to Cf + z * split_stride (0: no split)
     long long split_stride;
     ConvGather conv;   // used instead of A (or B) by the gathering (implicit-convolution) kernel
+    DgradGather dg;    // used instead of A by the data-gradient kernel
+    int kperiod;       // K-major B read at column k % kperiod (0: no wrap)
+    float* Cf2;        // FP32 output columns n >= nsplit go to Cf2[m * ldc2 + n - nsplit]
+    int ldc2, nsplit;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -155,13 +155,14 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
 // nrows and k past ke are zero-filled
 template <int ROWS>
 __device__ __forceinline__ void load_slice(uint8_t* s, const __nv_bfloat16* g, int ld, int row0,
-                                           int nrows, int k0, int ke) {
+                                           int nrows, int k0, int ke, int kperiod = 0) {
     constexpr int CHUNKS = ROWS * (BK / 8);
 #pragma unroll 4
     for (int i = threadIdx.x; i < CHUNKS; i += TC_THREADS) {
         const int r = i >> 3, c = i & 7;
         const bool ok = (row0 + r < nrows) && (k0 + c * 8 < ke);
-        const __nv_bfloat16* src = ok ? g + (size_t)(row0 + r) * ld + k0 + c * 8 : g;
+        const int kc = kperiod ? (k0 + c * 8) % kperiod : k0 + c * 8;
+        const __nv_bfloat16* src = ok ? g + (size_t)(row0 + r) * ld + kc : g;
         uint8_t* dst = s + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
         sg::cp_async16(dst, src, ok);
     }
@@ -247,9 +248,34 @@ __device__ __forceinline__ void load_slice_mn_conv(uint8_t* s, const sg::ConvGat
     }
 }
 
+// One K-slice of 128 source pixels x 64 (K) of the data-gradient operand (see
+// sg::DgradGather) in the K-major swizzled layout; rows as in load_slice_conv (yx, nn).
+__device__ __forceinline__ void load_slice_dgrad(uint8_t* s, const sg::DgradGather& dg,
+                                                 const int* yx, const int* nn, int k0, int ke) {
+    const int c = threadIdx.x & 7;
+    const int k = k0 + c * 8;
+    const bool kok = k < ke;
+    const int co = k & ((1 << dg.lco) - 1), t = k >> dg.lco;  // t = s * 9 + tap
+    const int sub = t / 9, tap = t - sub * 9;
+    const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+    const int oy = (sub >> 1) - dy, ox = (sub & 1) - dx;  // sub = 0 unless up1
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int r = (threadIdx.x >> 3) + 16 * j;
+        const int y = ((yx[j] & 0xFFFF) << dg.up1) + oy, x = ((yx[j] >> 16) << dg.up1) + ox;
+        const int n = nn[j];
+        const bool ok = kok && n >= 0 && y >= 0 && y < dg.H && x >= 0 && x < dg.W;
+        const __nv_bfloat16* src =
+            ok ? dg.dy + ((((size_t)n * dg.H + y) * dg.W + x) << dg.lco) + co : dg.dy;
+        uint8_t* dst = s + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+        sg::cp_async16(dst, src, ok);
+    }
+}
+
 // GA: A is the gathered convolution operand (K-major, rows = output pixels); GB: B is the
-// gathered operand (MN-major, K = pixels).
-template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GB = false>
+// gathered operand (MN-major, K = pixels); GD: A is the gathered data-gradient operand.
+template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GB = false,
+          bool GD = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
     using S = TcShape<BN, STAGES, BMN>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -285,20 +311,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
 
     auto stage_a = [&](int s) { return base + s * S::STAGE_BYTES; };
     auto stage_b = [&](int s) { return base + s * S::STAGE_BYTES + S::A_BYTES; };
-    // GA: pixel coordinates of the thread's eight A rows, fixed for all K-slices
+    // GA / GD: pixel coordinates of the thread's eight A rows, fixed for all K-slices (rows are
+    // output pixels, or source pixels at the source's resolution)
     int yx[8], nn[8];
-    if (GA) {
+    if (GA || GD) {
+        const int RH = GA ? g.conv.H : g.dg.H >> g.dg.up1, RWd = GA ? g.conv.W : g.dg.W >> g.dg.up1;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int p = m0 + (tid >> 3) + 16 * j;
-            const int x = p % g.conv.W, q = p / g.conv.W, y = q % g.conv.H;
+            const int x = p % RWd, q = p / RWd, y = q % RH;
             yx[j] = y | (x << 16);
-            nn[j] = p < g.M ? q / g.conv.H : -1;
+            nn[j] = p < g.M ? q / RH : -1;
         }
     }
     auto load = [&](int s, int k0) {
         if (GA)
             load_slice_conv(stage_a(s), g.conv, yx, nn, k0, ke);
+        else if (GD)
+            load_slice_dgrad(stage_a(s), g.dg, yx, nn, k0, ke);
         else if (AMN)
             load_slice_mn<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
         else
@@ -308,7 +338,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
         else if (BMN)
             load_slice_mn<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);
         else
-            load_slice<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);
+            load_slice<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke, g.kperiod);
     };
 
 #pragma unroll 1
@@ -369,9 +399,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
         // the output allows (no accumulation or split, aligned rows), else one column per lane
         float* ep = reinterpret_cast<float*>(base) + warp * (32 * 36);
         const size_t zoff = g.kchunk ? (size_t)blockIdx.z * g.split_stride : 0;
-        const bool vec = !g.accumulate && !g.kchunk &&
-                         (g.Cb ? (g.ldc % 8 == 0 && ((uintptr_t)g.Cb & 15) == 0)
-                               : (g.ldc % 4 == 0 && ((uintptr_t)g.Cf & 15) == 0));
+        // FP32 outputs may accumulate and may be split at column nsplit into two tensors; the
+        // vector path then takes a 32-column chunk that lies on one side of the split
+        const bool vec = !g.kchunk &&
+                         (g.Cb ? (!g.accumulate && g.ldc % 8 == 0 && ((uintptr_t)g.Cb & 15) == 0)
+                               : (g.ldc % 4 == 0 && ((uintptr_t)g.Cf & 15) == 0 &&
+                                  (!g.Cf2 || (g.ldc2 % 4 == 0 && g.nsplit % 4 == 0 &&
+                                              ((uintptr_t)g.Cf2 & 15) == 0))));
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
             if (n0 + c0 >= g.N) break;
@@ -392,7 +426,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                     *reinterpret_cast<float4*>(ep + lane * 36 + j) =
                         make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             __syncwarp();
-            if (vec && w == 32 && n0 + c0 + 32 <= g.N) {
+            const bool one_side = !g.Cf2 || n0 + c0 + 32 <= g.nsplit || n0 + c0 >= g.nsplit;
+            if (vec && w == 32 && n0 + c0 + 32 <= g.N && one_side) {
                 if (g.Cb) {
                     // lane: row it * 8 + lane / 4, columns 8 (lane % 4) .. + 7
                     const int cc = 8 * (lane & 3), n = n0 + c0 + cc;
@@ -440,7 +475,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                             x.z = fmaxf(x.z, 0.1f * x.z);
                             x.w = fmaxf(x.w, 0.1f * x.w);
                         }
-                        *reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n) = x;
+                        float4* dst =
+                            (g.Cf2 && n >= g.nsplit)
+                                ? reinterpret_cast<float4*>(g.Cf2 + (size_t)m * g.ldc2 + (n - g.nsplit))
+                                : reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n);
+                        if (g.accumulate) {
+                            const float4 o = *dst;
+                            x.x += o.x;
+                            x.y += o.y;
+                            x.z += o.z;
+                            x.w += o.w;
+                        }
+                        *dst = x;
                     }
                 }
             } else {
@@ -453,12 +499,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                     if (!col_ok || m >= g.M) continue;
                     float x = ep[r * 36 + lane] + bn;
                     if (g.relu) x = fmaxf(x, 0.1f * x);
-                    const size_t o = (size_t)m * g.ldc + n + zoff;
-                    if (g.Cf) {
+                    float* cf = g.Cf;
+                    size_t o = (size_t)m * g.ldc + n + zoff;
+                    if (g.Cf2 && n >= g.nsplit) {
+                        cf = g.Cf2;
+                        o = (size_t)m * g.ldc2 + (n - g.nsplit);
+                    }
+                    if (cf) {
                         if (g.accumulate)
-                            g.Cf[o] += x;
+                            cf[o] += x;
                         else
-                            g.Cf[o] = x;
+                            cf[o] = x;
                     } else {
                         g.Cb[o] = __float2bfloat16_rn(x);
                     }
