@@ -370,13 +370,13 @@ bool tc_timed_out() {
     return t;
 }
 
-template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GB, bool GD>
+template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GD, bool GAM>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
     static bool configured = false;
     if (!configured) {
         const cudaError_t e =
-            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB, GD>,
+            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GD, GAM>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -384,7 +384,7 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     int* flag = tc_flag().dev;
     if (!flag) return cudaErrorMemoryAllocation;
     dim3 grid((a.N + BN - 1) / BN, (a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM, splits);
-    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GB, GD>
+    lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GD, GAM>
         <<<grid, lbm::sgtc::TC_THREADS, TS::SMEM_BYTES, st>>>(a, flag);
     return cudaGetLastError();
 }
@@ -392,9 +392,9 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
 // C = A B on the tcgen05 tensor cores, each operand K-major or MN-major (AMN, BMN). The N tile
 // is the compiled width that covers N with the fewest computed columns (ties: fewer tiles);
 // wide tiles keep two stages so that two CTAs share an SM and one's epilogue overlaps the
-// other's MMAs. GA / GB: A (K-major) / B (MN-major) is the implicit im2col of a.conv; GD: A is
-// the gathered data-gradient operand a.dg.
-template <bool AMN, bool BMN, bool GA = false, bool GB = false, bool GD = false>
+// other's MMAs. GA / GAM: A (K-major / MN-major) is the implicit im2col of a.conv; GD: A is the
+// gathered data-gradient operand a.dg.
+template <bool AMN, bool BMN, bool GA = false, bool GD = false, bool GAM = false>
 cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
     static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
     int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
@@ -407,13 +407,13 @@ cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
         }
     }
     switch (best) {
-        case 32: return launch_tc<32, 3, AMN, BMN, GA, GB, GD>(st, a, splits);
-        case 64: return launch_tc<64, 3, AMN, BMN, GA, GB, GD>(st, a, splits);
-        case 80: return launch_tc<80, 4, AMN, BMN, GA, GB, GD>(st, a, splits);
-        case 128: return launch_tc<128, 3, AMN, BMN, GA, GB, GD>(st, a, splits);
-        case 144: return launch_tc<144, 2, AMN, BMN, GA, GB, GD>(st, a, splits);
-        case 192: return launch_tc<192, 2, AMN, BMN, GA, GB, GD>(st, a, splits);
-        default: return launch_tc<256, 2, AMN, BMN, GA, GB, GD>(st, a, splits);
+        case 32: return launch_tc<32, 3, AMN, BMN, GA, GD, GAM>(st, a, splits);
+        case 64: return launch_tc<64, 3, AMN, BMN, GA, GD, GAM>(st, a, splits);
+        case 80: return launch_tc<80, 4, AMN, BMN, GA, GD, GAM>(st, a, splits);
+        case 128: return launch_tc<128, 3, AMN, BMN, GA, GD, GAM>(st, a, splits);
+        case 144: return launch_tc<144, 2, AMN, BMN, GA, GD, GAM>(st, a, splits);
+        case 192: return launch_tc<192, 2, AMN, BMN, GA, GD, GAM>(st, a, splits);
+        default: return launch_tc<256, 2, AMN, BMN, GA, GD, GAM>(st, a, splits);
     }
 }
 
@@ -423,19 +423,32 @@ cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
     return gemm_tc<!AK, !BK>(st, a);
 }
 
-// Weight-gradient GEMM (C_out x 9 C_in, K = pixels, both operands MN-major): few output tiles
-// and a very long K, so K is split over up to 128 CTA slices whose FP32 partials are summed in a
-// fixed order.
-// gather: B is the implicit im2col of a.conv (else the im2col buffer a.B).
+// Weight-gradient GEMM dW[co][k] = sum_p dY[p][co] col[p][k] (K = pixels, both operands
+// MN-major): few output tiles and a very long K, so K is split over up to 128 CTA slices whose
+// FP32 partials are summed in a fixed order. gather: computed transposed, dW^T = col^T dY with
+// the im2col columns gathered by the loader as the 128-row operand (each thread decodes its tap
+// and channel once) and stored transposed; else from the im2col buffer a.B.
 cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
                        float* out, bool gather) {
+    if (gather) {
+        // rows: the 9 C_in im2col columns; columns: C_out; a.ldc (= 9 C_in) stays the row
+        // length of dW, written at dW[n * ldc + m]
+        GemmArgs t = a;
+        t.M = a.N;
+        t.N = a.M;
+        t.B = a.A;
+        t.ldb = a.lda;
+        t.tout = 1;
+        a = t;
+    }
     const int tiles = ((a.N + 255) / 256) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
     int splits = std::max(1, std::min(128, 2 * 152 / std::max(1, tiles)));
-    const long long stride = (long long)a.M * a.ldc;
+    const long long stride = gather ? (long long)a.N * a.ldc : (long long)a.M * a.ldc;
     while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
     if (splits == 1) {
         a.Cf = out;
-        return gather ? gemm_tc<true, true, false, true>(st, a) : gemm_tc<true, true>(st, a);
+        return gather ? gemm_tc<true, true, false, false, true>(st, a)
+                      : gemm_tc<true, true>(st, a);
     }
     int chunk = (a.K + splits - 1) / splits;
     chunk = (chunk + lbm::sgtc::BK - 1) / lbm::sgtc::BK * lbm::sgtc::BK;
@@ -443,7 +456,7 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     a.Cf = scratch;
     a.kchunk = chunk;
     a.split_stride = stride;
-    cudaError_t e = gather ? gemm_tc<true, true, false, true>(st, a, splits)
+    cudaError_t e = gather ? gemm_tc<true, true, false, false, true>(st, a, splits)
                            : gemm_tc<true, true>(st, a, splits);
     if (e != cudaSuccess) return e;
     k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
@@ -570,7 +583,7 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         g.ldc = c.Cout;
         g.bias = s->w + c.b_off;
         g.relu = 1;
-        SCUDA(s, (gemm_tc<false, false, true, false>(s->stream, g)));
+        SCUDA(s, (gemm_tc<false, false, true>(s->stream, g)));
         // a pool whose source is this conv's output runs right after it
         for (const auto& pl : s->pools)
             if (pl.first == c.out) {
@@ -823,7 +836,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
             gd.ldc2 = c.C2;
             gd.nsplit = c.C1;
         }
-        SCUDA(s, (gemm_tc<false, false, false, false, true>(s->stream, gd)));
+        SCUDA(s, (gemm_tc<false, false, false, true>(s->stream, gd)));
     }
     if (lr > 0.f) {
         ++s->adam_t;

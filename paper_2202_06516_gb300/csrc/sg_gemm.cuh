@@ -56,6 +56,7 @@ struct GemmArgs {
     int kperiod;       // K-major B read at column k % kperiod (0: no wrap)
     float* Cf2;        // FP32 output columns n >= nsplit go to Cf2[m * ldc2 + n - nsplit]
     int ldc2, nsplit;
+    int tout;          // FP32 output stored transposed: Cf[n * ldc + m] (no bias / ReLU)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

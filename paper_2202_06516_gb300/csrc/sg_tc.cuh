@@ -217,37 +217,6 @@ __device__ __forceinline__ void load_slice_conv(uint8_t* s, const sg::ConvGather
     }
 }
 
-// One K-slice of 64 pixels (K) x ROWS im2col columns (N: (tap, channel) of the gathered
-// convolution operand, see sg::ConvGather) in the MN-major swizzled layout of load_slice_mn:
-// the B operand of the weight gradient, whose K runs over the pixels. H and W are powers of two.
-template <int ROWS>
-__device__ __forceinline__ void load_slice_mn_conv(uint8_t* s, const sg::ConvGather& cv,
-                                                   int row0, int nrows, int k0, int ke) {
-    constexpr int CPR = ROWS / 8;
-    constexpr int CHUNKS = BK * CPR;
-    const int h1 = cv.H >> cv.up1, w1 = cv.W >> cv.up1;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < CHUNKS; i += TC_THREADS) {
-        const int k = i / CPR, c = i - k * CPR;
-        const int p = k0 + k, col = row0 + c * 8;
-        const int tap = col >> cv.lc, ci = col & ((1 << cv.lc) - 1);
-        const int y = ((p >> cv.lw) & (cv.H - 1)) + tap / 3 - 1;
-        const int x = (p & (cv.W - 1)) + tap - (tap / 3) * 3 - 1;
-        const int n = p >> (cv.lw + cv.lh);
-        const bool ok = p < ke && col < nrows && y >= 0 && y < cv.H && x >= 0 && x < cv.W;
-        const __nv_bfloat16* src = cv.x1;
-        if (ok) {
-            if (ci < cv.C1)
-                src = cv.x1 + ((((size_t)n * h1 + (y >> cv.up1)) * w1 + (x >> cv.up1)) * cv.C1 + ci);
-            else
-                src = cv.x2 + ((((size_t)n * cv.H + y) * cv.W + x) * cv.C2 + (ci - cv.C1));
-        }
-        uint8_t* dst = s + (c >> 3) * (BK / 8 * 1024) + (k >> 3) * 1024 + (k & 7) * 128 +
-                       (((c & 7) ^ (k & 7)) << 4);
-        sg::cp_async16(dst, src, ok);
-    }
-}
-
 // One K-slice of 128 source pixels x 64 (K) of the data-gradient operand (see
 // sg::DgradGather) in the K-major swizzled layout; rows as in load_slice_conv (yx, nn).
 __device__ __forceinline__ void load_slice_dgrad(uint8_t* s, const sg::DgradGather& dg,
@@ -272,10 +241,42 @@ __device__ __forceinline__ void load_slice_dgrad(uint8_t* s, const sg::DgradGath
     }
 }
 
-// GA: A is the gathered convolution operand (K-major, rows = output pixels); GB: B is the
-// gathered operand (MN-major, K = pixels); GD: A is the gathered data-gradient operand.
-template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GB = false,
-          bool GD = false>
+// One K-slice of 64 pixels (K) x 128 im2col columns (M: (tap, channel) of the gathered
+// convolution operand) in the MN-major swizzled layout, as the A operand of the transposed
+// weight gradient. Thread t always fills the 16-byte column chunk t % 16 (columns
+// m0 + 8 (t % 16) ..), whose tap and channel it decodes once (tc, cc: ci | tap << 16, -1 past
+// M); its pixels are k0 + t / 16 + 8 j (j = 0..7). H and W are powers of two.
+__device__ __forceinline__ void load_slice_mn_conv_a(uint8_t* s, const sg::ConvGather& cv,
+                                                     int tc, int k0, int ke) {
+    const int c = threadIdx.x & 15;
+    const int ci = tc & 0xFFFF, tap = tc >> 16;
+    const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+    const int h1 = cv.H >> cv.up1, w1 = cv.W >> cv.up1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int k = (threadIdx.x >> 4) + 8 * j;
+        const int p = k0 + k;
+        const int y = ((p >> cv.lw) & (cv.H - 1)) + dy, x = (p & (cv.W - 1)) + dx;
+        const int n = p >> (cv.lw + cv.lh);
+        const bool ok = tc >= 0 && p < ke && y >= 0 && y < cv.H && x >= 0 && x < cv.W;
+        const __nv_bfloat16* src = cv.x1;
+        if (ok) {
+            if (ci < cv.C1)
+                src = cv.x1 + ((((size_t)n * h1 + (y >> cv.up1)) * w1 + (x >> cv.up1)) * cv.C1 + ci);
+            else
+                src = cv.x2 + ((((size_t)n * cv.H + y) * cv.W + x) * cv.C2 + (ci - cv.C1));
+        }
+        uint8_t* dst = s + (c >> 3) * (BK / 8 * 1024) + (k >> 3) * 1024 + (k & 7) * 128 +
+                       (((c & 7) ^ (k & 7)) << 4);
+        sg::cp_async16(dst, src, ok);
+    }
+}
+
+// GA: A is the gathered convolution operand (K-major, rows = output pixels); GD: A is the
+// gathered data-gradient operand; GAM: A is the gathered convolution operand MN-major (K =
+// pixels, M = im2col columns).
+template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GD = false,
+          bool GAM = false>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
     using S = TcShape<BN, STAGES, BMN>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -324,8 +325,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
             nn[j] = p < g.M ? q / RH : -1;
         }
     }
+    // GAM: tap and channel of the thread's A column chunk
+    int tcol = -1;
+    if (GAM) {
+        const int col = m0 + 8 * (tid & 15);
+        if (col < g.M) {
+            const int tap = col >> g.conv.lc;
+            tcol = (col & ((1 << g.conv.lc) - 1)) | (tap << 16);
+        }
+    }
     auto load = [&](int s, int k0) {
-        if (GA)
+        if (GAM)
+            load_slice_mn_conv_a(stage_a(s), g.conv, tcol, k0, ke);
+        else if (GA)
             load_slice_conv(stage_a(s), g.conv, yx, nn, k0, ke);
         else if (GD)
             load_slice_dgrad(stage_a(s), g.dg, yx, nn, k0, ke);
@@ -333,9 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
             load_slice_mn<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
         else
             load_slice<BM>(stage_a(s), g.A, g.lda, m0, g.M, k0, ke);
-        if (GB)
-            load_slice_mn_conv<BN>(stage_b(s), g.conv, n0, g.N, k0, ke);
-        else if (BMN)
+        if (BMN)
             load_slice_mn<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke);
         else
             load_slice<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke, g.kperiod);
@@ -419,6 +429,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                 tc_ld32(ta, v);
             } else {
                 tc_ld16(ta, v);
+            }
+            if (g.tout) {
+                // transposed FP32 store: for each column, the warp's 32 rows are consecutive
+                const int m = m0 + warp * 32 + lane;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (j >= w || n >= g.N || m >= g.M) continue;
+                    float* o = g.Cf + (size_t)n * g.ldc + m + zoff;
+                    *o = g.accumulate ? *o + v[j] : v[j];
+                }
+                continue;
             }
 #pragma unroll
             for (int j = 0; j < 32; j += 4)
