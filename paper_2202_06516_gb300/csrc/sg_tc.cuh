@@ -40,10 +40,7 @@ struct TcShape {
     static constexpr int B_BYTES = BMN ? (BN + 63) / 64 * 64 * BK * 2 : BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     // 1 KB alignment slack for the swizzle atoms, then the stages, mbarriers and the TMEM slot
-    // (MN-major B: 16 KB of slack after the last slice, so that every address a slice
-    // descriptor can form stays inside this CTA's shared memory)
-    static constexpr int RAW_BYTES =
-        1024 + STAGES * STAGE_BYTES + 8 * (STAGES + 1) + 16 + (BMN ? 16384 : 0);
+    static constexpr int RAW_BYTES = 1024 + STAGES * STAGE_BYTES + 8 * (STAGES + 1) + 16;
     // at least enough shared memory that the CTAs resident on one SM never ask for more than
     // the 512 tensor-memory columns together (an allocation beyond them would wait)
     static constexpr int TMEM_CTAS = 512 / tmem_cols(BN);
