@@ -436,8 +436,9 @@ def run_surrogate(args):
             "forward": {"ms": t_fwd * 1e3, "tflops": f / t_fwd / 1e12},
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "traffic": None, "peak_kind": kind,
-                         "note": "whole training step; most layers have 32-128 channels and "
-                                 "are limited by HBM traffic of the im2col/col2im buffers"}}
+                         "note": "whole training step; the 32-128-channel layers with short K "
+                                 "leave the implicit-GEMM loaders, not the tensor cores, as "
+                                 "the limit"}}
 
 
 def run_warmstart(args):

@@ -814,7 +814,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         // data gradient (not needed for the input tensor)
         if (c.src1 == 0) continue;
         // implicit GEMM over the source pixels: dX_src[q][ci] += sum over (sub-pixel, tap, co)
-        // of dY gathered around q times the rearranged weights (no col buffer, no col2im)
+        // of dY gathered around q times the rearranged weights (no column buffer)
         if (c.up1 && c.C2 > 0) return sfail(s, LBM_ERR_STATE, "surrogate: upsampled cat source");
         GemmArgs gd{};
         gd.dg.dy = s->gmask;
