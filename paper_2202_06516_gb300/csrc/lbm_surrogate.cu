@@ -24,6 +24,7 @@
 #include "sg_gemm.cuh"
 #include "sg_tc.cuh"
 
+#include <atomic>
 #include <mutex>
 
 namespace lbm {
@@ -373,13 +374,18 @@ bool tc_timed_out() {
 template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GD, bool GAM>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
     using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
-    static bool configured = false;
-    if (!configured) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GD, GAM>,
+    // the shared-memory opt-in is per device: one bit per device ordinal that has it (setting it
+    // twice from racing host threads is harmless)
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(lbm::sgtc::k_gemm_tc<BN, STAGES, AMN, BMN, GA, GD, GAM>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.fetch_or(bit);
     }
     int* flag = tc_flag().dev;
     if (!flag) return cudaErrorMemoryAllocation;
