@@ -151,9 +151,11 @@ def _make_lattice(lbm, w, stream=None, tile=(0, 0), min_blocks=0):
     co, neutral = _resolve(w, lbm)
     lat = lbm.Lattice(w.nx, w.ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
                       tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"], gx=w.g[0],
-                      gy=w.g[1], stream=stream, tile=tile, min_blocks=min_blocks)
+                      gy=w.g[1], stream=stream, tile=tile, min_blocks=min_blocks,
+                      g_rho_ref=co["rho_g"] if w.buoyant else 0.0)
     geo = dict(circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
-               mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top, drop=w.drop)
+               mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top, drop=w.drop,
+               stripes=(w.stripes[0], neutral + w.stripes[1]) if w.stripes else None)
     return lat, geo
 
 
@@ -393,6 +395,76 @@ def unet_flops(H, Wd, base):
     return f + 2 * H * Wd * base
 
 
+def run_hysteresis(args):
+    """Dynamic contact-angle hysteresis on the striped (or uniform) 4096 x 1024 cylinder: the
+    drop is driven along the surface and the advancing (right) and receding (left) angles are
+    measured on the device every 100 steps. Reports the stepping rate including the measurements
+    and the angle statistics once the initial cap has relaxed (after 10k steps)."""
+    import torch
+    from paper_2202_06516_gb300 import lbm, workloads as W
+    w = W.hysteresis(heterogeneous=not args.homogeneous)
+    steps, every = args.hyst_steps, w.measure_every
+    stream = torch.cuda.Stream()
+    lat, geo = _make_lattice(lbm, w, stream=stream, tile=(lbm.LBM_TILE_AUTO, 0))
+    lat.set_geometry(**geo)
+    lat.step(max(2, args.warmup // 2 * 2))   # autotunes, then a few steps
+    m0 = lat.mass()
+    rows, diverged = [], None
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    with ClockSampler(0) as clk:
+        try:
+            for k in range(steps // every):
+                lat.step(every)
+                st, (l, r) = lbm.lbm_measure_contact_angle(lat.ctx)
+                m = lat.mass()
+                rows.append((l.status, l.theta_deg, r.status, r.theta_deg, l.contact_x,
+                             r.contact_x, m["mass"], m["cx"], m["cy"]))
+        except lbm.LbmError as e:
+            diverged = {"after_step": (len(rows) + 1) * every, "error": str(e)}
+        t1.record(stream)
+        t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    lat.close()
+    arr = np.array(rows, dtype=np.float64).reshape(-1, 9)
+    if args.series:
+        step = (np.arange(len(rows)) + 1) * every
+        np.savetxt(args.series, np.column_stack([step, arr]), delimiter=",", fmt="%.6f",
+                   header="step,left_status,theta_left,right_status,theta_right,"
+                          "contact_x_left,contact_x_right,mass,liquid_cx,liquid_cy",
+                   comments="")
+    steps = len(rows) * every
+    # statistics after the initial 90-degree cap has relaxed (first 10k steps left out)
+    late = arr[10000 // every:]
+    ok = (late[:, 0] == 0) & (late[:, 2] == 0)
+    adv, rec = late[ok, 3], late[ok, 1]
+
+    def stats(v):
+        if v.size == 0:
+            return None
+        p05, p50, p95 = np.percentile(v, [5, 50, 95])
+        return {"mean": float(v.mean()), "min": float(v.min()), "p05": float(p05),
+                "median": float(p50), "p95": float(p95), "max": float(v.max())}
+    return {"metric": "MLUPS", "value": w.nx * w.ny * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / max(steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "measure_every": every,
+                       "g": list(w.g), "body_force": "(rho - rho_g) g",
+                       "timing": "CUDA events around stepping plus one synchronous angle "
+                                 "measurement and mass sum every 100 steps"},
+            "clocks": clk.summary(),
+            "hysteresis": {"samples": len(rows), "valid_after_10k_steps": int(ok.sum()),
+                           "theta_advancing": stats(adv), "theta_receding": stats(rec),
+                           "hysteresis": stats(adv - rec),
+                           "no_contact_samples": int(((arr[:, 0] != 0) | (arr[:, 2] != 0)).sum()),
+                           "liquid_centroid_travel_lu": (float(arr[-1, 7] - m0["cx"])
+                                                         if len(rows) else None),
+                           "mass_drift_rel": (float(arr[-1, 6] / m0["mass"] - 1.0)
+                                              if len(rows) else None),
+                           "diverged": diverged}}
+
+
 def run_surrogate(args):
     """Warm-start U-Net alone (base 32, 256 x 256, batch args.batch, seeded synthetic inputs):
     args.steps training steps (forward, loss, backward, Adam) and as many forward passes, timed
@@ -497,7 +569,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "warmstart", "surrogate"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "warmstart", "surrogate",
+                                                    "hysteresis"])
     ap.add_argument("--train-cases", type=int, default=1024)
     ap.add_argument("--eval-cases", type=int, default=64)
     ap.add_argument("--gen-steps", type=int, default=20000)
@@ -506,6 +579,11 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--converge", action="store_true")
+    ap.add_argument("--hyst-steps", type=int, default=200000)
+    ap.add_argument("--series", default=None,
+                    help="hysteresis workload: write the angle series to this CSV file")
+    ap.add_argument("--homogeneous", action="store_true",
+                    help="hysteresis workload on a uniform 120-degree wall")
     ap.add_argument("--min-blocks", type=int, default=0,
                     help="step-kernel CTAs per SM to fit registers to (0: none)")
     args = ap.parse_args()
@@ -539,6 +617,10 @@ def main():
     if args.workload == "surrogate":
         if rank == 0:
             print(json.dumps(run_surrogate(args)), flush=True)
+        return
+    if args.workload == "hysteresis":
+        if rank == 0:
+            print(json.dumps(run_hysteresis(args)), flush=True)
         return
     if dist:
         dist.barrier()

@@ -47,7 +47,11 @@ enum { LBM_TILE_AUTO = -1 };                  /* lbm_params.tile_x: choose by au
  *  k2, kappa: k^2 and kappa-hat of the mesh-space chemical potential, Eq. 12.
  *  tau: s_v = 1/tau (Sec. 2.1) and the BGK relaxation time (Eq. 3).
  *  s_e, s_eps, s_q: MRT rates of S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_v, s_v) (Sec. 2.1).
- *  gx, gy: body acceleration; the force rho*g acts on gas and liquid (Sec. 4).
+ *  gx, gy: body acceleration; the force (rho - g_rho_ref) g acts on gas and liquid (Sec. 4).
+ *  g_rho_ref: reference density of the body force. 0 (default): the full weight rho g. rho_g:
+ *    the gas carries no load, which stands in for a closed container whose gas weight is
+ *    borne by its hydrostatic pressure; needed when g points along the periodic x axis,
+ *    where rho g on the gas would drive an unbounded channel flow.
  *  rho_g, rho_l: coexistence densities; <= 0 selects the library's Maxwell construction.
  *  tile_x, tile_y, min_blocks: step-kernel variant: tile shape and the CTAs per SM the register
  *    budget is fitted to (0 = no constraint); all three 0 selects 32x16/5 in FP32 and 32x16/0 in
@@ -68,6 +72,7 @@ typedef struct lbm_params {
     double gx, gy;
     double rho_g, rho_l;
     void *stream;
+    double g_rho_ref;  /* appended: positional initialisers of the older layout stay valid */
 } lbm_params;
 
 /* Geometry and initial state (Sec. 3.1, Fig. 1, Fig. 9, Eq. 16).

@@ -47,7 +47,8 @@ class _Cfg(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("eos", C.c_int32), ("collision", C.c_int32),
         ("Tr", C.c_double), ("k2", C.c_double), ("kappa", C.c_double), ("tau", C.c_double),
         ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double),
-        ("gx", C.c_double), ("gy", C.c_double), ("rho_g", C.c_double), ("rho_l", C.c_double),
+        ("gx", C.c_double), ("gy", C.c_double), ("g_rho_ref", C.c_double),
+        ("rho_g", C.c_double), ("rho_l", C.c_double),
         ("has_circle", C.c_int32), ("cx", C.c_double), ("cy", C.c_double), ("R", C.c_double),
         ("mu_circle", C.c_double), ("stripes", C.c_int32), ("stripe_arc", C.c_double),
         ("mu_stripe_b", C.c_double), ("mu_bottom", C.c_double), ("mu_top", C.c_double),
@@ -81,6 +82,7 @@ class Config:
     s_q: float = 1.9
     gx: float = 0.0
     gy: float = 0.0
+    g_rho_ref: float = 0.0
     rho_g: float = 0.0
     rho_l: float = 0.0
     has_circle: int = 0

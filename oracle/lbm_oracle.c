@@ -66,7 +66,8 @@ typedef struct {
     double kappa;      /* kappa-hat of Eq. 12 */
     double tau;        /* s_v = 1/tau; BGK relaxation time */
     double s_e, s_eps, s_q;
-    double gx, gy;     /* body acceleration; force rho*g */
+    double gx, gy;     /* body acceleration; force (rho - g_rho_ref) g */
+    double g_rho_ref;  /* reference density of the body force (0: full weight) */
     double rho_g, rho_l; /* coexistence densities (<= 0: Maxwell construction) */
     int32_t has_circle;
     double cx, cy, R;  /* circle centre and radius, multiples of 1/2 */
@@ -528,8 +529,8 @@ void orc_step(orc_sim *s, int nsteps) {
                 double drx = (8.0 * (R_[exp1] - R_[exm1]) - (R_[exp2] - R_[exm2])) / 12.0;
                 double dry = (8.0 * (R_[eyp1] - R_[eym1]) - (R_[eyp2] - R_[eym2])) / 12.0;
                 double rho = R_[e];
-                double Fx = -rho * dmux + drx / 3.0 + rho * c->gx;
-                double Fy = -rho * dmuy + dry / 3.0 + rho * c->gy;
+                double Fx = -rho * dmux + drx / 3.0 + (rho - c->g_rho_ref) * c->gx;
+                double Fy = -rho * dmuy + dry / 3.0 + (rho - c->g_rho_ref) * c->gy;
                 const double *fn = &s->f[n * 9];
                 double jx = 0, jy = 0;
                 for (int q = 0; q < 9; ++q) {

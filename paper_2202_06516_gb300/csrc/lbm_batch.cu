@@ -378,6 +378,8 @@ lbm_status lbm_batch_create(const lbm_params* model, int32_t n, const int32_t* n
     a.kappa = (float)c0->p.kappa;
     a.gx = (float)c0->p.gx;
     a.gy = (float)c0->p.gy;
+    a.gbx = (float)(-c0->p.g_rho_ref * c0->p.gx);
+    a.gby = (float)(-c0->p.g_rho_ref * c0->p.gy);
     a.s_e = (float)c0->p.s_e;
     a.s_eps = (float)c0->p.s_eps;
     a.s_q = (float)c0->p.s_q;

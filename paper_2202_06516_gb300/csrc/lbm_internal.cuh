@@ -64,6 +64,7 @@ struct StepArgs {
     int nx, ny, P;
     int plane;         // elements per plane: (ny + 2 kPadY + 1) * P
     T k2, kappa, gx, gy;
+    T gbx, gby;        // -g_rho_ref * g: constant part of the body force
     T s_e, s_eps, s_q, s_v, inv_tau;
     int bgk;
     int eos;

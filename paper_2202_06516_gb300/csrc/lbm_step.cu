@@ -72,6 +72,8 @@ StepArgs<T> make_args(lbm_ctx* c, int src) {
     a.kappa = (T)c->p.kappa;
     a.gx = (T)c->p.gx;
     a.gy = (T)c->p.gy;
+    a.gbx = (T)(-c->p.g_rho_ref * c->p.gx);
+    a.gby = (T)(-c->p.g_rho_ref * c->p.gy);
     a.s_e = (T)c->p.s_e;
     a.s_eps = (T)c->p.s_eps;
     a.s_q = (T)c->p.s_q;

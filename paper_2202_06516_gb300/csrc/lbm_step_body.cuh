@@ -342,8 +342,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
                              sub_rn(s_rho[o - 2], s_rho[o + 2]));
         const T Gry = fma_rn((T)8, sub_rn(s_rho[o + RW], s_rho[o - RW]),
                              sub_rn(s_rho[o - 2 * RW], s_rho[o + 2 * RW]));
-        const T Fx = fma_rn(rho, fma_rn(Gmx, (T)-1 / (T)12, a.gx), mul_rn(Grx, (T)1 / (T)36));
-        const T Fy = fma_rn(rho, fma_rn(Gmy, (T)-1 / (T)12, a.gy), mul_rn(Gry, (T)1 / (T)36));
+        const T Fx = fma_rn(rho, fma_rn(Gmx, (T)-1 / (T)12, a.gx), fma_rn(Grx, (T)1 / (T)36, a.gbx));
+        const T Fy = fma_rn(rho, fma_rn(Gmy, (T)-1 / (T)12, a.gy), fma_rn(Gry, (T)1 / (T)36, a.gby));
         // pull the populations of time t (Eq. 4) with half-way bounce-back
         const unsigned us = (unsigned)self;
         const T* hb = a.h_in + us;

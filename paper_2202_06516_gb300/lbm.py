@@ -35,7 +35,8 @@ class lbm_params(C.Structure):
                 ("Tr", C.c_double), ("k2", C.c_double), ("kappa", C.c_double),
                 ("tau", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double),
                 ("s_q", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
-                ("rho_g", C.c_double), ("rho_l", C.c_double), ("stream", C.c_void_p)]
+                ("rho_g", C.c_double), ("rho_l", C.c_double), ("stream", C.c_void_p),
+                ("g_rho_ref", C.c_double)]
 
 
 class lbm_geometry(C.Structure):
@@ -269,11 +270,11 @@ class Lattice:
     def __init__(self, nx, ny, *, eos=LBM_EOS_PR, Tr=0.7, k2=0.1, kappa=0.0126, tau=1.0,
                  s_e=1.64, s_eps=1.54, s_q=1.9, gx=0.0, gy=0.0, rho_g=0.0, rho_l=0.0,
                  precision=LBM_FP32, collision=LBM_MRT, device=0, tile=(0, 0), min_blocks=0,
-                 stream=None):
+                 stream=None, g_rho_ref=0.0):
         handle = getattr(stream, "cuda_stream", stream)
         self.params = lbm_params(nx, ny, precision, eos, collision, device, tile[0], tile[1],
                                  min_blocks, Tr, k2, kappa, tau, s_e, s_eps, s_q, gx, gy, rho_g,
-                                 rho_l, C.c_void_p(handle) if handle else None)
+                                 rho_l, C.c_void_p(handle) if handle else None, g_rho_ref)
         self.nx, self.ny = nx, ny
         self.ctx = lbm_create(self.params)
 

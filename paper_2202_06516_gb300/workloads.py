@@ -21,6 +21,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field, asdict
 
+import math
+
 import numpy as np
 
 # model parameters common to every workload
@@ -40,6 +42,7 @@ class Workload:
     mu_rel_top: float = 0.0
     stripes: tuple | None = None  # (arc length, mu_rel of the odd stripes)
     g: tuple = (0.0, 0.0)
+    buoyant: bool = False         # body force (rho - rho_g) g instead of rho g
     steps: int = 3000
     measure_every: int = 0
     model: dict = field(default_factory=lambda: dict(MODEL))
@@ -87,6 +90,28 @@ def plain_large(seed: int = 0, pendent: bool = False) -> Workload:
                     2048, 1024, (1024.0, 0.0, 300.0), cap_drop(1024, 0, 300, 150),
                     mu_rel_circle=mu_rel_for_angle(theta), g=(0.0, gy), steps=50000,
                     measure_every=500)
+
+
+def hysteresis(heterogeneous: bool = True) -> Workload:
+    """Dynamic contact-angle hysteresis on a curved surface (Sec. 4.4): 4096 x 1024, periodic in
+    x, cylinder R = 800 whose wall alternates 60- and 120-degree stripes of arc length 40
+    (heterogeneous) or is uniformly 120 degrees, drop r = 120 started as a 90-degree cap on top.
+    The substrate is tilted by the slope angle 20 degrees: gravity makes 20 degrees with the
+    vertical, g = G (sin 20, -cos 20) with G sin 20 = 5e-7 (the tangential component at the top),
+    so the normal component keeps the drop pressed to the cylinder while it slides right; at this
+    G the uniform-wall drop reaches the foot of the cylinder near the end of the 200k steps. The
+    force acts on the density above the gas density (the full weight rho g along the periodic
+    axis would drive the gas through the channel without bound). The cylinder centre sits 100 lu
+    below the bottom boundary so that the drop fits under the top wall. Advancing (right) and
+    receding (left) angles every 100 steps for 200k steps."""
+    cx, cy, R, r = 2048.0, -100.0, 800.0, 120.0
+    phi = math.radians(20.0)
+    G = 5e-7 / math.sin(phi)
+    stripes = (40.0, mu_rel_for_angle(60.0)) if heterogeneous else None
+    name = "hysteresis-4096x1024-cyl800-" + ("stripes60-120" if heterogeneous else "uniform120")
+    return Workload(name, 4096, 1024, (cx, cy, R), cap_drop(cx, cy, R, r),
+                    mu_rel_circle=mu_rel_for_angle(120.0), stripes=stripes,
+                    g=(G * math.sin(phi), -G * math.cos(phi)), buoyant=True, steps=200000, measure_every=100)
 
 
 def flat_drop(nx=160, ny=80, r=20.0, theta_rel=0.0) -> Workload:

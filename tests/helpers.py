@@ -13,7 +13,7 @@ def oracle_config(O, w, **over):
     neutral = m["k2"] * mx["mu_sat"]
     kw = dict(nx=w.nx, ny=w.ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
               tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"], gx=w.g[0], gy=w.g[1],
-              rho_g=mx["rho_g"], rho_l=mx["rho_l"],
+              rho_g=mx["rho_g"], rho_l=mx["rho_l"], g_rho_ref=mx["rho_g"] if w.buoyant else 0.0,
               mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top,
               drop_x=w.drop[0], drop_y=w.drop[1], drop_r=w.drop[2], drop_W=w.drop[3])
     if w.circle is not None:
@@ -99,7 +99,8 @@ def gpu_lattice(lbm, cfg, precision=0, tile=(0, 0), rho0=None, stream=None):
     lat = lbm.Lattice(cfg.nx, cfg.ny, eos=cfg.eos, Tr=cfg.Tr, k2=cfg.k2, kappa=cfg.kappa,
                       tau=cfg.tau, s_e=cfg.s_e, s_eps=cfg.s_eps, s_q=cfg.s_q, gx=cfg.gx,
                       gy=cfg.gy, rho_g=cfg.rho_g, rho_l=cfg.rho_l, precision=precision,
-                      collision=cfg.collision, tile=tile, stream=stream)
+                      collision=cfg.collision, tile=tile, stream=stream,
+                      g_rho_ref=cfg.g_rho_ref)
     lat.set_geometry(circle=(cfg.cx, cfg.cy, cfg.R) if cfg.has_circle else None,
                      mu_circle=cfg.mu_circle,
                      stripes=(cfg.stripe_arc, cfg.mu_stripe_b) if cfg.stripes else None,

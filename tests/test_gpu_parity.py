@@ -223,6 +223,26 @@ def test_full_size_sampled(lbm, oracle_mod):
     assert abs(m1 - m0) / m0 < 1e-6
 
 
+@pytest.mark.parametrize("heterogeneous", [True, False])
+def test_hysteresis_full_size(lbm, oracle_mod, heterogeneous):
+    """4096 x 1024 hysteresis workload (cylinder R = 800, 40-lu stripes of 60 and 120 degrees or
+    uniform 120 degrees, tangential body force), bench launch config: wall chemical potentials
+    bit-exact in FP32, 50 FP32 steps vs the oracle on every node."""
+    O = oracle_mod
+    w = W.hysteresis(heterogeneous)
+    cfg = oracle_config(O, w)[0]
+    ref = O.Sim(cfg)
+    lat = gpu_lattice(lbm, cfg, tile=(lbm.LBM_TILE_AUTO, 0))
+    flags, muw, links = lat.geometry()
+    _, _, oflag, omuw = ref.ext()
+    assert np.array_equal(flags, oflag)
+    assert np.array_equal(muw.astype(np.float32), omuw.astype(np.float32))
+    ref.step(50)
+    lat.step(50)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < 2e-5, err
+
+
 def test_stream_from_torch(lbm, oracle_mod):
     """The library runs on a caller's torch stream."""
     import torch
@@ -281,6 +301,33 @@ def test_striped_wetting_and_pendent_gravity(lbm, oracle_mod):
     gl, gr = lat.measure()
     ol, orr, _ = ref.measure()
     assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 3e-5), (1, 1e-9)])
+def test_buoyant_body_force_along_periodic_axis(lbm, oracle_mod, precision, tol):
+    """Body force (rho - rho_g) g with g along the periodic x axis (plus a normal component) on
+    a striped cylinder: density and the reported velocity v = u + F / 2 rho against the oracle
+    after 1000 steps, so the reference density enters both the stepping and the force output."""
+    O = oracle_mod
+    w = W.Workload("buoyant", 160, 110, (80.0, 0.0, 35.0), W.tangent_drop(80, 0, 35, 20),
+                   mu_rel_circle=0.02, stripes=(9.0, -0.03), g=(2e-5, -1e-5), buoyant=True)
+    cfg = oracle_config(O, w)[0]
+    assert cfg.g_rho_ref == cfg.rho_g > 0
+    ref = O.Sim(cfg)
+    ref.step(1000)
+    lat = gpu_lattice(lbm, cfg, precision=precision)
+    lat.step(1000)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < tol, err
+    # the oracle reports the velocity of the state before its last step: step it once more
+    ref.step(1)
+    oux, ouy, _, _ = ref.velocity_force()
+    ux, uy = lat.velocity()
+    fluid = ref.ext()[2][2:-2] == 0
+    umax = max(np.abs(oux[fluid]).max(), np.abs(ouy[fluid]).max())
+    assert umax > 1e-5
+    du = max(np.abs(ux - oux)[fluid].max(), np.abs(uy - ouy)[fluid].max())
+    assert du < (1e-2 * umax if precision == 0 else 1e-9), (du, umax)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-12)])

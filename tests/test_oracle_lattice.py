@@ -138,22 +138,26 @@ def test_force_gradient_fourth_order(oracle_mod):
 
 
 # --------------------------------------------------- collision and forcing (Eq. 1, 3, 13)
-def test_body_force_momentum(oracle_mod):
-    """Exact-difference forcing adds exactly rho * delta-u of momentum and no mass: a uniform
-    fluid at rest under acceleration g has velocity g after one step."""
+@pytest.mark.parametrize("g_rho_ref", [0.0, 0.1, 0.3])
+def test_body_force_momentum(oracle_mod, g_rho_ref):
+    """Exact-difference forcing adds exactly the force as momentum and no mass: a uniform fluid of
+    density 0.3 at rest under acceleration g with body-force reference density rho_ref has
+    velocity (1 - rho_ref / 0.3) g after one step (g itself for rho_ref = 0, rest for 0.3)."""
     O = oracle_mod
     m = _model()
     rho0 = np.full((24, 16), 0.3)
-    s = O.Sim(O.Config(nx=16, ny=24, **m, gx=3e-4, gy=-2e-4, mu_bottom=0.0, mu_top=0.0), rho0)
+    s = O.Sim(O.Config(nx=16, ny=24, **m, gx=3e-4, gy=-2e-4, g_rho_ref=g_rho_ref,
+                       mu_bottom=0.0, mu_top=0.0), rho0)
     s.step(1)
     f = s.f()
     ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
     ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
     rho = f.sum(-1)
     mid = slice(4, 20)
+    scale = 1.0 - g_rho_ref / 0.3
     assert np.allclose(rho[mid], 0.3, rtol=1e-13)
-    assert np.allclose((f @ ex)[mid] / rho[mid], 3e-4, rtol=1e-10)
-    assert np.allclose((f @ ey)[mid] / rho[mid], -2e-4, rtol=1e-10)
+    assert np.allclose((f @ ex)[mid] / rho[mid], 3e-4 * scale, rtol=1e-10, atol=1e-14)
+    assert np.allclose((f @ ey)[mid] / rho[mid], -2e-4 * scale, rtol=1e-10, atol=1e-14)
 
 
 @pytest.mark.parametrize("tau", [1.0, 0.8])
