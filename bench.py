@@ -395,15 +395,41 @@ def unet_flops(H, Wd, base):
     return f + 2 * H * Wd * base
 
 
+def _young_summary(mech, tension, skip, theta_c, stripes, scatter):
+    """Eq. 17 force statistics per contact line and wall region (after `skip` samples)."""
+    names = {0: "theta_%g" % theta_c, 1: "theta_%g" % stripes[1] if stripes else "-", 2: "border"}
+    out = {"gamma": tension["gamma"], "laplace_spread": tension["spread"],
+           "interface_width_10_90": tension["width_10_90"],
+           "equilibrium_angles": {"circle": theta_c, "stripes": stripes[1] if stripes else None},
+           "equilibrium_angle_scatter": scatter}
+    for side, label in (("right", "advancing"), ("left", "receding")):
+        f, reg = mech[side]["force"][skip:], mech[side]["region"][skip:]
+        d = {}
+        for k, nm in names.items():
+            v = f[reg == k]
+            if v.size:
+                d[nm] = {"samples": int(v.size), "mean": float(v.mean()),
+                         "min": float(v.min()), "max": float(v.max())}
+        out[label] = d
+    return out
+
+
 def run_hysteresis(args):
     """Dynamic contact-angle hysteresis on the striped (or uniform) 4096 x 1024 cylinder: the
     drop is driven along the surface and the advancing (right) and receding (left) angles are
     measured on the device every 100 steps. Reports the stepping rate including the measurements
     and the angle statistics once the initial cap has relaxed (after 10k steps)."""
     import torch
-    from paper_2202_06516_gb300 import lbm, workloads as W
+    from paper_2202_06516_gb300 import lbm, workloads as W, contact_mechanics as CM
     w = W.hysteresis(heterogeneous=not args.homogeneous)
     steps, every = args.hyst_steps, w.measure_every
+    # Eq. 17-18 inputs, untimed: liquid-gas tension (free drops) and the intrinsic angle of each
+    # wall wettability (uniform-wall equilibrium drops)
+    tension = CM.laplace_tension(w.model)
+    R_c, r_d = w.circle[2], w.drop[2]
+    intrinsic = [CM.intrinsic_angle(w.model, w.mu_rel_circle, R=R_c, r=r_d)]
+    if w.stripes:
+        intrinsic.append(CM.intrinsic_angle(w.model, w.stripes[1], R=R_c, r=r_d))
     stream = torch.cuda.Stream()
     lat, geo = _make_lattice(lbm, w, stream=stream, tile=(lbm.LBM_TILE_AUTO, 0))
     lat.set_geometry(**geo)
@@ -419,20 +445,29 @@ def run_hysteresis(args):
                 st, (l, r) = lbm.lbm_measure_contact_angle(lat.ctx)
                 m = lat.mass()
                 rows.append((l.status, l.theta_deg, r.status, r.theta_deg, l.contact_x,
-                             r.contact_x, m["mass"], m["cx"], m["cy"]))
+                             r.contact_x, l.contact_y, r.contact_y, m["mass"], m["cx"],
+                             m["cy"]))
         except lbm.LbmError as e:
             diverged = {"after_step": (len(rows) + 1) * every, "error": str(e)}
         t1.record(stream)
         t1.synchronize()
     ms = t0.elapsed_time(t1)
     lat.close()
-    arr = np.array(rows, dtype=np.float64).reshape(-1, 9)
+    arr = np.array(rows, dtype=np.float64).reshape(-1, 11)
+    theta_c = intrinsic[0]["theta"]
+    stripes = (w.stripes[0], intrinsic[1]["theta"]) if w.stripes else None
+    mech = CM.analyse_series(arr[:, :8], w.circle, theta_c, stripes, tension["gamma"],
+                             tension["width_10_90"])
     if args.series:
         step = (np.arange(len(rows)) + 1) * every
-        np.savetxt(args.series, np.column_stack([step, arr]), delimiter=",", fmt="%.6f",
+        cols = [step, arr]
+        for side in ("left", "right"):
+            cols += [mech[side]["theta_eq"], mech[side]["phi_d"], mech[side]["force"]]
+        np.savetxt(args.series, np.column_stack(cols), delimiter=",", fmt="%.6f",
                    header="step,left_status,theta_left,right_status,theta_right,"
-                          "contact_x_left,contact_x_right,mass,liquid_cx,liquid_cy",
-                   comments="")
+                          "contact_x_left,contact_x_right,contact_y_left,contact_y_right,"
+                          "mass,liquid_cx,liquid_cy,theta_eq_left,phi_d_left,force_x_left,"
+                          "theta_eq_right,phi_d_right,force_x_right", comments="")
     steps = len(rows) * every
     # statistics after the initial 90-degree cap has relaxed (first 10k steps left out)
     late = arr[10000 // every:]
@@ -458,11 +493,13 @@ def run_hysteresis(args):
                            "theta_advancing": stats(adv), "theta_receding": stats(rec),
                            "hysteresis": stats(adv - rec),
                            "no_contact_samples": int(((arr[:, 0] != 0) | (arr[:, 2] != 0)).sum()),
-                           "liquid_centroid_travel_lu": (float(arr[-1, 7] - m0["cx"])
+                           "liquid_centroid_travel_lu": (float(arr[-1, 9] - m0["cx"])
                                                          if len(rows) else None),
-                           "mass_drift_rel": (float(arr[-1, 6] / m0["mass"] - 1.0)
+                           "mass_drift_rel": (float(arr[-1, 8] / m0["mass"] - 1.0)
                                               if len(rows) else None),
-                           "diverged": diverged}}
+                           "diverged": diverged},
+            "young_force": _young_summary(mech, tension, 10000 // every, theta_c, stripes,
+                                          [t["scatter"] for t in intrinsic])}
 
 
 def run_surrogate(args):

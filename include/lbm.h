@@ -124,6 +124,13 @@ typedef struct lbm_info {
  * LBM_ERR_ARG above the critical temperature or for an unknown EOS. */
 lbm_status lbm_coexistence(int32_t eos, double Tr, double out[4]);
 
+/* Bulk equation of state at density rho (Eq. 10 for Peng-Robinson, or Carnahan-Starling),
+ * evaluated on the host in FP64: out[0] = p0(rho), out[1] = psi'(rho), the bulk chemical
+ * potential at k = 1 (Eq. 11). The model's pressure and chemical potential are k^2 times these
+ * (Eq. 12). Used for Laplace-law surface tensions (Delta p = k^2 (p0(rho_in) - p0(rho_out))).
+ * LBM_ERR_ARG for an unknown EOS, Tr outside (0, 1), or rho outside (0, rho_max). */
+lbm_status lbm_eos_eval(int32_t eos, double Tr, double rho, double out[2]);
+
 /* Allocate a lattice on p->device (2 x 9 population planes, 2 density planes, flags, wall
  * chemical potential, reduction and measurement scratch). *out receives the context; on failure
  * *out is NULL and nothing is leaked. */

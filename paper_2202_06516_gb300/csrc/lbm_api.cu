@@ -248,6 +248,19 @@ lbm_status lbm_coexistence(int32_t eos, double Tr, double out[4]) {
     return LBM_OK;
 }
 
+lbm_status lbm_eos_eval(int32_t eos, double Tr, double rho, double out[2]) {
+    HostEos e;
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "lbm_eos_eval: out is NULL");
+    if (!make_eos(eos, Tr, &e)) return fail(nullptr, LBM_ERR_ARG, "lbm_eos_eval: unknown EOS");
+    if (!(Tr > 0.0 && Tr < 1.0))
+        return fail(nullptr, LBM_ERR_ARG, "lbm_eos_eval: Tr must lie in (0, 1)");
+    if (!(rho > 0.0 && rho < e.rho_max()))
+        return fail(nullptr, LBM_ERR_ARG, "lbm_eos_eval: rho outside (0, rho_max)");
+    out[0] = e.p(rho);
+    out[1] = e.mu(rho);
+    return LBM_OK;
+}
+
 lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "lbm_create: out is NULL");
     *out = nullptr;

@@ -78,6 +78,7 @@ def lib() -> C.CDLL:
     if _sig is None:
         vp, dp, i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)
         L.lbm_coexistence.argtypes = [C.c_int32, C.c_double, dp]
+        L.lbm_eos_eval.argtypes = [C.c_int32, C.c_double, C.c_double, dp]
         L.lbm_create.argtypes = [C.POINTER(lbm_params), C.POINTER(vp)]
         L.lbm_set_geometry.argtypes = [vp, C.POINTER(lbm_geometry)]
         L.lbm_step.argtypes = [vp, C.c_int64]
@@ -111,7 +112,7 @@ def lib() -> C.CDLL:
         for n in ("lbm_batch_create", "lbm_batch_set_geometry", "lbm_batch_run",
                   "lbm_batch_measure", "lbm_batch_instance"):
             getattr(L, n).restype = C.c_int
-        for n in ("lbm_coexistence", "lbm_create", "lbm_set_geometry", "lbm_step",
+        for n in ("lbm_coexistence", "lbm_eos_eval", "lbm_create", "lbm_set_geometry", "lbm_step",
                   "lbm_measure_contact_angle", "lbm_read_fields", "lbm_mass", "lbm_read_geometry",
                   "lbm_read_candidates", "lbm_get_info", "lbm_synchronize"):
             getattr(L, n).restype = C.c_int
@@ -135,6 +136,13 @@ def lbm_coexistence(eos: int, Tr: float) -> dict:
     out = np.zeros(4)
     _check(lib().lbm_coexistence(eos, Tr, _dp(out)))
     return {"rho_g": out[0], "rho_l": out[1], "p_sat": out[2], "mu_sat": out[3]}
+
+
+def lbm_eos_eval(eos: int, Tr: float, rho: float) -> dict:
+    """Bulk EOS at rho (host, FP64): p0 and psi' (the model's values are k^2 times these)."""
+    out = np.zeros(2)
+    _check(lib().lbm_eos_eval(eos, Tr, rho, _dp(out)))
+    return {"p0": out[0], "dpsi": out[1]}
 
 
 def lbm_create(params: lbm_params) -> C.c_void_p:

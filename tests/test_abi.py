@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -38,6 +39,22 @@ def test_coexistence_agrees_with_oracle(oracle_mod):
         b = oracle_mod.maxwell(eos, Tr)
         for k in ("rho_g", "rho_l", "p_sat", "mu_sat"):
             assert a[k] == pytest.approx(b[k], rel=1e-9), (eos, Tr, k)
+
+
+def test_eos_eval_agrees_with_oracle(oracle_mod):
+    """The library's host EOS (used for Laplace tensions) against the oracle's p0 and psi'."""
+    from paper_2202_06516_gb300 import lbm
+    for eos, Tr in [(0, 0.6), (0, 0.7), (1, 0.7)]:
+        mx = oracle_mod.maxwell(eos, Tr)
+        for rho in np.linspace(0.5 * mx["rho_g"], 1.1 * mx["rho_l"], 7):
+            a = lbm.lbm_eos_eval(eos, Tr, rho)
+            b = oracle_mod.eos_eval(eos, Tr, rho)
+            assert a["p0"] == pytest.approx(b["p0"], rel=1e-12, abs=1e-15)
+            assert a["dpsi"] == pytest.approx(b["mu0"], rel=1e-12, abs=1e-15)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_eos_eval(0, 0.7, -1.0)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_eos_eval(0, 0.7, 21.0 / 2.0 + 1.0)
 
 
 def test_coexistence_rejects_supercritical():

@@ -1,0 +1,85 @@
+"""GPU: the Laplace-law surface tension measured with the CUDA library (free drops through the C
+ABI) against the same experiment run by the FP64 oracle, and Laplace's law itself at the radii
+the hysteresis analysis uses."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2202_06516_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2202_06516_gb300 import lbm as L
+    L.lib()
+    return L
+
+
+def _oracle_drop(O, m, r0, N, steps, W_):
+    mx = O.maxwell(m["eos"], m["Tr"])
+    neutral = m["k2"] * mx["mu_sat"]
+    cfg = O.Config(nx=N, ny=N, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
+                   tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"],
+                   rho_g=mx["rho_g"], rho_l=mx["rho_l"], mu_bottom=neutral, mu_top=neutral,
+                   drop_x=N / 2, drop_y=N / 2 - 0.5, drop_r=r0, drop_W=W_)
+    s = O.Sim(cfg)
+    s.step(steps)
+    r = s.rho()
+    c = N // 2
+    rin, rout = r[c, c], r[c, 2]
+    dp = m["k2"] * (O.eos_eval(m["eos"], m["Tr"], rin)["p0"]
+                    - O.eos_eval(m["eos"], m["Tr"], rout)["p0"])
+    Rm = math.sqrt(((r - rout) / (rin - rout)).sum() / math.pi)
+    return dp * Rm
+
+
+@pytest.mark.parametrize("precision,rel", [(1, 1e-6), (0, 2e-2)])
+def test_laplace_tension_matches_oracle(lbm, oracle_mod, precision, rel):
+    from paper_2202_06516_gb300 import contact_mechanics as CM
+    m = W.MODEL
+    got = CM.laplace_tension(m, radii=(16.0,), steps=4000, W=4.0, margin=24,
+                             precision=precision)
+    want = _oracle_drop(oracle_mod, m, 16.0, 80, 4000, 4.0)
+    assert got["drops"][0]["N"] == 80
+    assert got["gamma"] == pytest.approx(want, rel=rel)
+
+
+def test_laplace_law_at_analysis_radii(lbm):
+    """Delta p R agrees between r = 20 and 30 (FP32 library runs), and the interface width is
+    the several-lattice-unit diffuse band of this model."""
+    from paper_2202_06516_gb300 import contact_mechanics as CM
+    t = CM.laplace_tension(W.MODEL)
+    assert t["spread"] < 0.03, t
+    assert t["gamma"] > 0
+    assert 4.0 < t["width_10_90"] < 15.0, t
+
+
+def test_intrinsic_angle_matches_oracle(lbm, oracle_mod):
+    """The uniform-wall equilibrium angle the library measures (theta_s of Eq. 18) against the
+    oracle's measurement of the same run (R = 60, r = 30, 15k steps), both sides within 0.5
+    degrees; the 120-degree wall is hydrophobic and the 60-degree wall hydrophilic."""
+    from paper_2202_06516_gb300 import contact_mechanics as CM
+    O = oracle_mod
+    m = W.MODEL
+    mx = O.maxwell(m["eos"], m["Tr"])
+    neutral = m["k2"] * mx["mu_sat"]
+    for target in (120.0, 60.0):
+        mu_rel = W.mu_rel_for_angle(target)
+        got = CM.intrinsic_angle(m, mu_rel, R=60.0, r=30.0, steps=15000, samples=1)
+        nx, ny = got["nx"], got["ny"]
+        cfg = O.Config(nx=nx, ny=ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
+                       tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"],
+                       rho_g=mx["rho_g"], rho_l=mx["rho_l"], has_circle=1, cx=nx / 2.0, cy=0.0,
+                       R=60.0, mu_circle=neutral + mu_rel, mu_bottom=neutral, mu_top=neutral,
+                       drop_x=nx / 2.0, drop_y=60.5, drop_r=30.0, drop_W=5.6)
+        ref = O.Sim(cfg)
+        ref.step(15000)
+        ol, orr, _ = ref.measure()
+        assert abs(got["left"] - ol.theta) <= 0.5 and abs(got["right"] - orr.theta) <= 0.5
+        assert (got["theta"] > 95.0) if target > 90 else (got["theta"] < 85.0), got
