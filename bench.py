@@ -155,7 +155,8 @@ def _make_lattice(lbm, w, stream=None, tile=(0, 0), min_blocks=0):
                       g_rho_ref=co["rho_g"] if w.buoyant else 0.0)
     geo = dict(circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
                mu_bottom=neutral + w.mu_rel_bottom, mu_top=neutral + w.mu_rel_top, drop=w.drop,
-               stripes=(w.stripes[0], neutral + w.stripes[1]) if w.stripes else None)
+               stripes=(w.stripes[0], neutral + w.stripes[1]) if w.stripes else None,
+               concave=w.concave)
     return lat, geo
 
 
@@ -385,6 +386,88 @@ def run_batched(args):
     return line
 
 
+def run_sweep(args):
+    """Grid-independence and curvature sweep (Sec. 4.1-4.2): drops of 30-100 lu on convex
+    cylinders and in cavities of radius 150-400 lu for five wall potentials, all instances
+    advanced together by the persistent batched kernel until their angles settle (two
+    consecutive readings 1,000 steps apart within 0.05 degrees) or args.sweep_steps; then the
+    device measurement against the spherical-cap method (Sec. 4.1) on the same fields."""
+    import torch
+    from paper_2202_06516_gb300 import lbm, workloads as W, contact_mechanics as CM
+    ws = W.curvature_sweep()
+    m = ws[0].model
+    co = lbm.lbm_coexistence(m["eos"], m["Tr"])
+    neutral = m["k2"] * co["mu_sat"]
+    b = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
+                  kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"],
+                  tile_auto=True)
+    for i, w in enumerate(ws):
+        b.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+                       mu_bottom=neutral, mu_top=neutral, drop=w.drop, concave=w.concave)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    steps, conv, res = b.run(args.sweep_steps, check_every=1000, tol=0.0, angle_tol=0.05)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    ang = b.measure()
+    rows = []
+    for i, w in enumerate(ws):
+        l, r = ang[i]
+        row = {"name": w.name, "concave": w.concave, "R": w.circle[2], "r": w.drop[2],
+               "target": float(w.name.rsplit("theta", 1)[1]), "steps": int(steps[i]),
+               "converged": bool(conv[i]), "ok": l.status == 0 and r.status == 0}
+        if row["ok"]:
+            row.update(left=l.theta, right=r.theta, theta=0.5 * (l.theta + r.theta),
+                       alpha=0.5 * (l.alpha + r.alpha), beta=0.5 * (l.beta + r.beta))
+            ctx = lbm.lbm_batch_instance(b.b, i)
+            _, pd = lbm.lbm_read_candidates(ctx, w.nx, w.ny)
+            try:
+                row["cap"] = CM.cap_angle(pd[:, :2], pd[:, 2], w.circle, concave=w.concave)["theta"]
+            except ValueError:
+                row["cap"] = None
+        rows.append(row)
+    b.close()
+    updates = sum(w.nx * w.ny * int(s) for w, s in zip(ws, steps))
+    groups = {}
+    for row in rows:
+        if row["ok"]:
+            groups.setdefault(("cavity" if row["concave"] else "cylinder", row["target"]),
+                              []).append(row)
+    by_group = {}
+    for (kind, target), g in sorted(groups.items()):
+        th = np.array([x["theta"] for x in g])
+        by_group[f"{kind}-{target:g}"] = {"n": len(g), "mean": float(th.mean()),
+                                          "std": float(th.std()), "min": float(th.min()),
+                                          "max": float(th.max())}
+    errs = {}
+    for kind in ("cylinder", "cavity"):
+        for subset in ("all", "converged"):
+            pairs = [(x["theta"], x["cap"]) for x in rows
+                     if x["ok"] and x.get("cap") is not None and
+                     ("cavity" if x["concave"] else "cylinder") == kind and
+                     (subset == "all" or x["converged"])]
+            if pairs:
+                a = np.array(pairs)
+                errs[f"{kind}-{subset}"] = {
+                    "n": len(a),
+                    "E": float(np.sqrt(((a[:, 0] - a[:, 1]) ** 2).sum() / (a[:, 1] ** 2).sum())),
+                    "mean_diff_deg": float((a[:, 0] - a[:, 1]).mean()),
+                    "max_abs_deg": float(np.abs(a[:, 0] - a[:, 1]).max())}
+    return {"metric": "MLUPS", "value": updates / dt / 1e6, "unit": "MLUPS", "n_gpus": 1,
+            "steps": int(steps.max()), "warmup": 0, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"curvature-sweep-{len(ws)}-instances",
+                       "total_nodes": sum(w.nx * w.ny for w in ws),
+                       "timing": "host wall clock around the synchronous batch run (autotune, "
+                                 "angle checks every 1,000 steps included)"},
+            "sweep": {"seconds": dt, "converged": int(conv.sum()), "instances": len(ws),
+                      "angles_ok": int(sum(x["ok"] for x in rows)),
+                      "steps_mean": float(steps.mean()), "by_group": by_group,
+                      "present_vs_cap": errs,
+                      "instances_detail": rows if args.sweep_detail else None}}
+
+
 def unet_flops(H, Wd, base):
     """Multiply-add FLOPs of one forward pass (2 per MAC) of the U-Net."""
     from paper_2202_06516_gb300 import workloads as W
@@ -607,7 +690,7 @@ def main():
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "warmstart", "surrogate",
-                                                    "hysteresis"])
+                                                    "hysteresis", "sweep"])
     ap.add_argument("--train-cases", type=int, default=1024)
     ap.add_argument("--eval-cases", type=int, default=64)
     ap.add_argument("--gen-steps", type=int, default=20000)
@@ -617,6 +700,9 @@ def main():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--converge", action="store_true")
     ap.add_argument("--hyst-steps", type=int, default=200000)
+    ap.add_argument("--sweep-steps", type=int, default=60000)
+    ap.add_argument("--sweep-detail", action="store_true",
+                    help="sweep workload: include every instance's angles in the JSON line")
     ap.add_argument("--series", default=None,
                     help="hysteresis workload: write the angle series to this CSV file")
     ap.add_argument("--homogeneous", action="store_true",
@@ -658,6 +744,10 @@ def main():
     if args.workload == "hysteresis":
         if rank == 0:
             print(json.dumps(run_hysteresis(args)), flush=True)
+        return
+    if args.workload == "sweep":
+        if rank == 0:
+            print(json.dumps(run_sweep(args)), flush=True)
         return
     if dist:
         dist.barrier()

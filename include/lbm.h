@@ -75,11 +75,13 @@ typedef struct lbm_params {
     double g_rho_ref;  /* appended: positional initialisers of the older layout stay valid */
 } lbm_params;
 
-/* Geometry and initial state (Sec. 3.1, Fig. 1, Fig. 9, Eq. 16).
- *  Circle: solid nodes are those with (i - cx)^2 + (j - cy)^2 <= R^2, evaluated exactly in
- *    doubled-integer coordinates, so cx, cy, R must be multiples of 1/2. Its wall surface is
- *    taken at radius R + 1/2 for the measurement.
- *  Wall chemical potential of a wetting-layer node: mu_circle inside the disc (or, with stripes,
+/* Geometry and initial state (Sec. 3.1, Fig. 1, Fig. 2, Fig. 9, Eq. 16).
+ *  Circle: solid nodes are those with (i - cx)^2 + (j - cy)^2 <= R^2 (convex substrate, the
+ *    default) or, with concave = 1, those with (i - cx)^2 + (j - cy)^2 > R^2 (a circular cavity:
+ *    the concave substrate of Fig. 2b), evaluated exactly in doubled-integer coordinates, so cx,
+ *    cy, R must be multiples of 1/2. In both cases the wall surface is taken at radius R + 1/2
+ *    (half a link between the last fluid and the first solid node) for the measurement.
+ *  Wall chemical potential of a wetting-layer node: mu_circle in the circle's solid (or, with stripes,
  *    alternating mu_circle / mu_stripe_b by arc length R*(phi - pi/2) in units of stripe_arc,
  *    phi = atan2(j - cy, i - cx)); mu_bottom below the domain; mu_top above it.
  *  Initial density: rho0 (host, (ny, nx), read at fluid nodes) if non-NULL, else the Eq. 16 drop
@@ -92,12 +94,16 @@ typedef struct lbm_geometry {
     double mu_bottom, mu_top;
     double drop_x, drop_y, drop_r, drop_W;
     const double *rho0;
+    int32_t concave;   /* appended: 0 = solid disc (convex), 1 = solid outside the circle */
 } lbm_geometry;
 
 /* One side of the contact-angle measurement (Sec. 3.2, Eq. 15, Fig. 1, Fig. 2). Angles in
  * degrees. theta is measured through the liquid between the line through p1 and p2 and the
  * substrate tangent at the contact point; alpha is the tangent's inclination to the horizontal;
- * beta = theta + alpha on the convex circle (theta on a flat wall). d1, d2: distances of p1, p2
+ * beta = theta + alpha on the convex circle, theta - alpha on the concave one (Fig. 2), theta on
+ * a flat wall. The left (out[0]) and right (out[1]) sides are seen from the liquid standing on
+ * the wall: split by the sign of the cross product between the wall normal into the fluid at the
+ * liquid centroid and the direction of the point from the circle centre. d1, d2: distances of p1, p2
  * from the substrate. link1, link2: (node index * 4 + slot) of the chosen liquid/gas links, slot
  * 0..3 = link to (i+1, j), (i, j+1), (i+1, j+1), (i-1, j+1). */
 typedef struct lbm_angle {

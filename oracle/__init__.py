@@ -53,7 +53,7 @@ class _Cfg(C.Structure):
         ("mu_circle", C.c_double), ("stripes", C.c_int32), ("stripe_arc", C.c_double),
         ("mu_stripe_b", C.c_double), ("mu_bottom", C.c_double), ("mu_top", C.c_double),
         ("drop_x", C.c_double), ("drop_y", C.c_double), ("drop_r", C.c_double),
-        ("drop_W", C.c_double), ("nthreads", C.c_int32),
+        ("drop_W", C.c_double), ("nthreads", C.c_int32), ("concave", C.c_int32),
     ]
 
 
@@ -100,6 +100,7 @@ class Config:
     drop_r: float = 10.0
     drop_W: float = 2.0
     nthreads: int = 0
+    concave: int = 0
 
     def _c(self) -> _Cfg:
         c = _Cfg()

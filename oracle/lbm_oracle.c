@@ -77,6 +77,7 @@ typedef struct {
     double mu_bottom, mu_top; /* wall chemical potential on the flat wall rows */
     double drop_x, drop_y, drop_r, drop_W; /* Eq. 16 initial drop */
     int32_t nthreads;  /* OpenMP threads (<= 0: runtime default) */
+    int32_t concave;   /* 1: the circle is a cavity, solid outside it (Fig. 2b) */
 } orc_cfg;
 
 typedef struct {
@@ -267,25 +268,26 @@ int orc_maxwell(int eos, double Tr, double out[4]) {
 
 static inline int wrapx(int i, int nx) { return ((i % nx) + nx) % nx; }
 
-/* Solid test in doubled-integer coordinates, exact: wall rows, or inside the closed disc. */
-static int is_solid_node(const orc_cfg *c, int i, int j) {
-    if (j < 0 || j >= c->ny) return 1;
-    if (!c->has_circle) return 0;
-    long long cx2 = llround(2.0 * c->cx), cy2 = llround(2.0 * c->cy), r2 = llround(2.0 * c->R);
-    long long dx = 2LL * i - cx2, dy = 2LL * j - cy2;
-    return dx * dx + dy * dy <= r2 * r2;
-}
-
+/* Node in the circle's solid, exact in doubled-integer coordinates: inside the closed disc for a
+ * convex substrate, outside it for a concave one (a circular cavity, Fig. 2b). */
 static int in_disc(const orc_cfg *c, int i, int j) {
     if (!c->has_circle) return 0;
     long long cx2 = llround(2.0 * c->cx), cy2 = llround(2.0 * c->cy), r2 = llround(2.0 * c->R);
     long long dx = 2LL * i - cx2, dy = 2LL * j - cy2;
-    return dx * dx + dy * dy <= r2 * r2;
+    int inside = dx * dx + dy * dy <= r2 * r2;
+    return c->concave ? !inside : inside;
+}
+
+/* Solid test: wall rows, or the circle's solid. */
+static int is_solid_node(const orc_cfg *c, int i, int j) {
+    if (j < 0 || j >= c->ny) return 1;
+    return in_disc(c, i, j);
 }
 
 /* Wall chemical potential of a wetting-layer node: the circle's (uniform or alternating stripes
  * of arc length stripe_arc, counted counter-clockwise from the apex) if the node lies in the
- * disc, else the flat wall row's (bottom below the domain, top above it). */
+ * circle's solid (the disc, or its outside for a cavity), else the flat wall row's (bottom
+ * below the domain, top above it). */
 static double wall_mu(const orc_cfg *c, int i, int j) {
     if (in_disc(c, i, j)) {
         if (!c->stripes) return c->mu_circle;
@@ -685,15 +687,16 @@ typedef struct {
     int side;
 } cand_t;
 
-/* Substrate distance of point (px, py): to the circle of radius R + 1/2 (the wall lies half a
- * link outside the solid disc) or to the bottom wall plane y = -1/2. Evaluated with separate
- * rounded operations (the library is built without contraction) so that both implementations
- * reach the same bits. */
+/* Substrate distance of point (px, py), measured from the wall into the fluid: to the circle of
+ * radius R + 1/2 (the wall lies half a link between the last fluid and the first solid node;
+ * outward for a convex disc, inward for a concave cavity) or to the bottom wall plane y = -1/2.
+ * Evaluated with separate rounded operations (the library is built without contraction) so that
+ * both implementations reach the same bits. */
 static double substrate_dist(const orc_cfg *c, double px, double py) {
     if (c->has_circle) {
         double dx = px - c->cx, dy = py - c->cy;
         double r2 = dx * dx + dy * dy;
-        return sqrt(r2) - (c->R + 0.5);
+        return c->concave ? (c->R + 0.5) - sqrt(r2) : sqrt(r2) - (c->R + 0.5);
     }
     return py - (-0.5);
 }
@@ -787,7 +790,9 @@ void orc_measure(const orc_cfg *c, const double *rho, double rho_m, orc_angle ou
             double ax = qx - c->cx, ay = qy - c->cy;
             double bx = cd[k].px - c->cx, by = cd[k].py - c->cy;
             double cr = ax * by - ay * bx;
-            side = cr > 0 ? 0 : 1;
+            /* left = counter-clockwise from the wall normal into the fluid at the centroid:
+             * (ax, ay) on a convex circle, -(ax, ay) in a concave cavity */
+            side = (c->concave ? cr < 0 : cr > 0) ? 0 : 1;
         } else
             side = cd[k].px < qx ? 0 : 1;
         cd[k].side = side;
@@ -834,6 +839,10 @@ void orc_measure(const orc_cfg *c, const double *rho, double rho_m, orc_angle ou
             double nxr = Cx - c->cx, nyr = Cy - c->cy, nl = sqrt(nxr * nxr + nyr * nyr);
             nxr /= nl;
             nyr /= nl;
+            if (c->concave) { /* normal into the fluid points to the centre */
+                nxr = -nxr;
+                nyr = -nyr;
+            }
             /* tangent pointing into the liquid: clockwise on the left side, counter-clockwise
              * on the right side */
             if (side == 0) {
@@ -861,7 +870,9 @@ void orc_measure(const orc_cfg *c, const double *rho, double rho_m, orc_angle ou
         double ca = fabs(tx);
         if (ca > 1) ca = 1;
         o->alpha = acos(ca) * 180.0 / M_PI;
-        o->beta = c->has_circle ? o->theta + o->alpha : o->theta;
+        /* Fig. 2: beta = theta + alpha on a convex, theta - alpha on a concave substrate */
+        o->beta = !c->has_circle ? o->theta
+                  : (c->concave ? o->theta - o->alpha : o->theta + o->alpha);
         o->cx = Cx;
         o->cy = Cy;
         o->status = 0;
@@ -894,7 +905,8 @@ long long orc_candidates(const orc_cfg *c, const double *rho, double rho_m, int6
  * dmin from the substrate (algebraic least squares), intersect it with the substrate to get the
  * base length L and the height H above the base chord, then R0 = (4H^2 + L^2) / (8H),
  * tan(beta) = L / (2 (R0 - H)), alpha = asin(L / (2 Rs)) on a circle (0 on a flat wall) and
- * theta = beta - alpha (convex substrate, Fig. 2). out: theta, beta, alpha, L, H, R0, fitted
+ * theta = beta - alpha on a convex, beta + alpha on a concave substrate (Fig. 2; H is measured
+ * from the chord along the wall normal into the fluid). out: theta, beta, alpha, L, H, R0, fitted
  * centre x, y, fitted radius. Returns 0, or -1 if the fit or the intersection fails. */
 int orc_cap_angle(const orc_cfg *c, const double *rho, double rho_m, double dmin, double out[9]) {
     uint8_t *flag = (uint8_t *)calloc((size_t)c->nx * (c->ny + 4), 1);
@@ -980,6 +992,10 @@ int orc_cap_angle(const orc_cfg *c, const double *rho, double rho_m, double dmin
         double nl = sqrt(nx_ * nx_ + ny_ * ny_);
         nx_ /= nl;
         ny_ /= nl;
+        if (c->concave) {
+            nx_ = -nx_;
+            ny_ = -ny_;
+        }
         alpha = asin(L / (2.0 * (c->R + 0.5)));
     } else {
         nx_ = 0;
@@ -989,7 +1005,7 @@ int orc_cap_angle(const orc_cfg *c, const double *rho, double rho_m, double dmin
     double H = rr + ((qx - mx) * nx_ + (qy - my) * ny_);
     double R0 = (4.0 * H * H + L * L) / (8.0 * H);
     double beta = atan2(L, 2.0 * (R0 - H));
-    out[0] = (beta - alpha) * 180.0 / M_PI;
+    out[0] = (c->has_circle && c->concave ? beta + alpha : beta - alpha) * 180.0 / M_PI;
     out[1] = beta * 180.0 / M_PI;
     out[2] = alpha * 180.0 / M_PI;
     out[3] = L;

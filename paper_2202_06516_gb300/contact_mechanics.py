@@ -153,28 +153,88 @@ def laplace_tension(model: dict, radii=(20.0, 30.0), steps: int = 20000, W: floa
             "drops": out}
 
 
+# ---------------------------------------------------------------- spherical-cap method (4.1)
+def cap_angle(points, d, circle, concave=False, dmin=3.0) -> dict:
+    """Spherical-cap estimate of the contact angle (Sec. 4.1), the benchmark the measurement is
+    compared with: a circle fitted (algebraic least squares, x^2 + y^2 + D x + E y + F = 0) to
+    the drop's interface points farther than dmin from the wall, its chord with the wall
+    surface (radius R + 1/2) of length L, the drop height H above the chord along the wall
+    normal into the fluid, R0 = (4 H^2 + L^2) / (8 H), tan(beta) = L / (2 (R0 - H)),
+    alpha = asin(L / (2 (R + 1/2))) and theta = beta - alpha on a convex wall, beta + alpha in a
+    cavity (Fig. 2). circle = (cx, cy, R) or None for the flat bottom wall y = -1/2 (alpha = 0).
+
+    points: (n, 2) interface points (Eq. 15 link points); d: their distances from the wall."""
+    p = np.asarray(points, float)[np.asarray(d, float) >= dmin]
+    if len(p) < 3:
+        raise ValueError("cap_angle: fewer than three interface points away from the wall")
+    A = np.column_stack([p[:, 0], p[:, 1], np.ones(len(p))])
+    z = -(p[:, 0] ** 2 + p[:, 1] ** 2)
+    (Dc, Ec, Fc), *_ = np.linalg.lstsq(A, z, rcond=None)
+    qx, qy = -0.5 * Dc, -0.5 * Ec
+    rr = math.sqrt(qx * qx + qy * qy - Fc)
+    if circle is not None:
+        cx, cy, R = circle
+        Rs = R + 0.5
+        dx, dy = qx - cx, qy - cy
+        D = math.hypot(dx, dy)
+        if not (abs(Rs - rr) < D < Rs + rr):
+            raise ValueError("cap_angle: fitted drop does not cut the wall")
+        a = (Rs * Rs - rr * rr + D * D) / (2.0 * D)
+        h = math.sqrt(Rs * Rs - a * a)
+        mx, my = cx + a * dx / D, cy + a * dy / D          # chord midpoint
+        L = 2.0 * h
+        nx_, ny_ = (mx - cx) / a, (my - cy) / a            # outward normal of the circle
+        if concave:
+            nx_, ny_ = -nx_, -ny_
+        alpha = math.asin(min(1.0, L / (2.0 * Rs)))
+    else:
+        dy = -0.5 - qy
+        if abs(dy) >= rr:
+            raise ValueError("cap_angle: fitted drop does not cut the wall")
+        L = 2.0 * math.sqrt(rr * rr - dy * dy)
+        mx, my, nx_, ny_, alpha = qx, -0.5, 0.0, 1.0, 0.0
+    H = rr + (qx - mx) * nx_ + (qy - my) * ny_
+    R0 = (4.0 * H * H + L * L) / (8.0 * H)
+    beta = math.atan2(L, 2.0 * (R0 - H))
+    theta = beta + alpha if (circle is not None and concave) else beta - alpha
+    return {"theta": math.degrees(theta), "beta": math.degrees(beta),
+            "alpha": math.degrees(alpha), "L": L, "H": H, "R0": R0, "qx": qx, "qy": qy, "r": rr,
+            "points": int(len(p))}
+
+
 # ------------------------------------------------------------------ intrinsic contact angle
 def intrinsic_angle(model: dict, mu_rel: float, R: float = 800.0, r: float = 120.0,
                     steps: int = 40000, samples: int = 10, every: int = 2000,
-                    precision: int = L.LBM_FP32) -> dict:
+                    precision: int = L.LBM_FP32, concave: bool = False) -> dict:
     """Equilibrium contact angle a uniform wall of chemical potential neutral + mu_rel produces
     (theta_s of Eq. 18): a drop of radius r started as a 90-degree cap on a cylinder of radius R
-    centred on the bottom boundary, no body force. After `steps` steps the device measures both
-    angles `samples` times, `every` steps apart (the contact lines creep across the staircase
-    wall, so single readings scatter by a few degrees); returns the means and the scatter."""
+    centred on the bottom boundary (convex), or at the bottom of a circular cavity of radius R
+    whose lowest wall point sits 5.5 lu above the bottom boundary (concave, Fig. 2b); no body
+    force. After `steps` steps the device measures both angles `samples` times, `every` steps
+    apart (the contact lines creep across the staircase wall, so single readings scatter by a
+    few degrees); returns the means and the scatter."""
     co = L.lbm_coexistence(model["eos"], model["Tr"])
     neutral = model["k2"] * co["mu_sat"]
-    nx, ny = int(2 * R + 4 * r + 40), int(R + 3 * r + 40)
-    nx += nx % 2
-    cx, cy = nx / 2.0, 0.0
+    if concave:
+        nx, ny = int(2 * R + 20), int(3 * r + 40)
+        nx += nx % 2
+        cx, cy = nx / 2.0, R + 6.0
+        drop_c = (cx, cy - R - 0.5)
+    else:
+        nx, ny = int(2 * R + 4 * r + 40), int(R + 3 * r + 40)
+        nx += nx % 2
+        cx, cy = nx / 2.0, 0.0
+        drop_c = (cx, cy + R + 0.5)
     lat = L.Lattice(nx, ny, eos=model["eos"], Tr=model["Tr"], k2=model["k2"],
                     kappa=model["kappa"], tau=model["tau"], s_e=model["s_e"],
                     s_eps=model["s_eps"], s_q=model["s_q"], precision=precision)
     readings = []
     try:
-        # 90-degree cap: centre on the wall surface R + 1/2 straight above the cylinder centre
+        # 90-degree cap: centre on the wall surface R + 1/2 straight above (convex) or below
+        # (concave) the circle centre
         lat.set_geometry(circle=(cx, cy, R), mu_circle=neutral + mu_rel, mu_bottom=neutral,
-                         mu_top=neutral, drop=(cx, cy + R + 0.5, float(r), 5.6))
+                         mu_top=neutral, drop=(drop_c[0], drop_c[1], float(r), 5.6),
+                         concave=concave)
         lat.step(steps)
         for k in range(samples):
             if k:
@@ -188,7 +248,8 @@ def intrinsic_angle(model: dict, mu_rel: float, R: float = 800.0, r: float = 120
     a = np.array(readings)
     return {"left": float(a[:, 0].mean()), "right": float(a[:, 1].mean()),
             "theta": float(a.mean()), "scatter": float(a.mean(axis=1).std()),
-            "nx": nx, "ny": ny, "R": R, "r": r, "steps": steps + (samples - 1) * every}
+            "nx": nx, "ny": ny, "R": R, "r": r, "concave": concave,
+            "steps": steps + (samples - 1) * every}
 
 
 # ------------------------------------------------------------------------ series analysis

@@ -381,6 +381,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     a.plane = (int)c->plane;
     a.has_circle = g->has_circle;
     a.stripes = g->stripes;
+    a.concave = g->has_circle && g->concave;
     a.cx2 = llround(2.0 * g->cx);
     a.cy2 = llround(2.0 * g->cy);
     a.r2 = llround(2.0 * g->R);
@@ -413,6 +414,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     c->geom = *g;
     c->geom.rho0 = nullptr;
     c->sub.circle = g->has_circle ? 1 : 0;
+    c->sub.concave = g->has_circle && g->concave ? 1 : 0;
     c->sub.cx = g->cx;
     c->sub.cy = g->cy;
     c->sub.Rs = g->R + 0.5;

@@ -1,7 +1,8 @@
 // Geometry and initial-state kernels (Sec. 3.1, Fig. 1, Fig. 9, Eq. 16).
 //
-// Classification is integer-exact: a node is solid when it lies in a wall row or inside the
-// closed disc, tested in doubled-integer coordinates. Wetting layers follow Sec. 3.1: layer 1 is
+// Classification is integer-exact: a node is solid when it lies in a wall row or in the circle's
+// solid (inside the closed disc, or outside it for a concave cavity), tested in doubled-integer
+// coordinates. Wetting layers follow Sec. 3.1: layer 1 is
 // a solid node with a fluid node among its 8 neighbours, layer 2 a remaining solid node with a
 // layer-1 node among its 8 neighbours. Both passes update flags in place: layer 1 only reads the
 // fluid/solid distinction, which it never changes, and layer 2 only reads "is layer 1", which it
@@ -20,6 +21,14 @@ __device__ __forceinline__ int wrap(int i, int nx) {
     return i < 0 ? i + nx : i;
 }
 
+// node in the circle's solid: the closed disc (convex) or its complement (concave)
+__device__ __forceinline__ bool in_circle_solid(const GeomArgs& g, int i, int j) {
+    if (!g.has_circle) return false;
+    const long long dx = 2LL * i - g.cx2, dy = 2LL * j - g.cy2;
+    const bool in_disc = dx * dx + dy * dy <= g.r2 * g.r2;
+    return g.concave ? !in_disc : in_disc;
+}
+
 // Classification on the canonical nodes (0 <= x < nx, -2 <= j < ny + 2); the remaining pad rows
 // stay inner solid (memset by the caller) and the pad columns are filled afterwards.
 __global__ void k_classify(uint8_t* flags, GeomArgs g) {
@@ -28,11 +37,7 @@ __global__ void k_classify(uint8_t* flags, GeomArgs g) {
          e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e / g.nx), i = (int)(e % g.nx);
         const int j = r - 2;
-        bool solid = j < 0 || j >= g.ny;
-        if (!solid && g.has_circle) {
-            const long long dx = 2LL * i - g.cx2, dy = 2LL * j - g.cy2;
-            solid = dx * dx + dy * dy <= g.r2 * g.r2;
-        }
+        const bool solid = j < 0 || j >= g.ny || in_circle_solid(g, i, j);
         flags[lidx(g.P, i, j)] = solid ? kSolid : kFluid;
     }
 }
@@ -66,12 +71,7 @@ __global__ void k_muw(const uint8_t* flags, T* muw, GeomArgs g) {
         const uint8_t f = flags[lidx(g.P, i, j)];
         double mu = 0.0;
         if (f == kLayer1 || f == kLayer2) {
-            bool in_disc = false;
-            if (g.has_circle) {
-                const long long dx = 2LL * i - g.cx2, dy = 2LL * j - g.cy2;
-                in_disc = dx * dx + dy * dy <= g.r2 * g.r2;
-            }
-            if (in_disc) {
+            if (in_circle_solid(g, i, j)) {
                 mu = g.mu_circle;
                 if (g.stripes) {
                     const double phi = atan2((double)j - g.cy, (double)i - g.cx);

@@ -73,7 +73,7 @@ struct StepArgs {
 
 struct GeomArgs {
     int nx, ny, P, plane;
-    int has_circle, stripes;
+    int has_circle, stripes, concave;
     long long cx2, cy2, r2;  // doubled-integer circle
     double cx, cy, R, stripe_arc;
     double mu_circle, mu_stripe_b, mu_bottom, mu_top;
@@ -86,6 +86,7 @@ struct ReduceOut {
 
 struct Substrate {
     int circle;       // 1: circle (cx, cy, Rs), 0: flat bottom wall at y = -1/2
+    int concave;      // circle only: 1 = the fluid lies inside the circle
     double cx, cy, Rs;
 };
 

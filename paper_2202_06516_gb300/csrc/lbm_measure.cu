@@ -115,10 +115,12 @@ __device__ __forceinline__ bool link_point(const T* rho, const uint8_t* flags, i
     return true;
 }
 
+// distance from the wall surface into the fluid
 __device__ __forceinline__ double substrate_dist(const Substrate& s, double px, double py) {
     if (s.circle) {
         const double dx = __dsub_rn(px, s.cx), dy = __dsub_rn(py, s.cy);
-        return __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), s.Rs);
+        const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        return s.concave ? __dsub_rn(s.Rs, r) : __dsub_rn(r, s.Rs);
     }
     return __dsub_rn(py, -0.5);
 }
@@ -143,7 +145,10 @@ __global__ void k_meas_cand(const T* rho, const uint8_t* flags, int nx, int ny, 
             if (sub.circle) {
                 const double ax = __dsub_rn(qxc, sub.cx), ay = __dsub_rn(qyc, sub.cy);
                 const double bx = __dsub_rn(px, sub.cx), by = __dsub_rn(py, sub.cy);
-                side = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx)) > 0.0 ? 0 : 1;
+                const double cr = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
+                // the wall normal into the fluid at the centroid is (ax, ay) on the convex
+                // circle and -(ax, ay) on the concave one
+                side = (sub.concave ? cr < 0.0 : cr > 0.0) ? 0 : 1;
             } else {
                 side = px < qxc ? 0 : 1;
             }
@@ -203,6 +208,10 @@ __device__ void finish_side(const Best& b1, const Best& b2, const Substrate& sub
         const double nl = sqrt(nxr * nxr + nyr * nyr);
         nxr /= nl;
         nyr /= nl;
+        if (sub.concave) {  // wall normal into the fluid points to the centre
+            nxr = -nxr;
+            nyr = -nyr;
+        }
         // tangent toward the liquid: clockwise on the left side, counter-clockwise on the right
         if (side == 0) {
             tx = nyr;
@@ -225,7 +234,8 @@ __device__ void finish_side(const Best& b1, const Best& b2, const Substrate& sub
     const double ct = fmin(1.0, fmax(-1.0, tx * vx + ty * vy));
     o->theta_deg = acos(ct) * (180.0 / M_PI);
     o->alpha_deg = acos(fmin(1.0, fabs(tx))) * (180.0 / M_PI);
-    o->beta_deg = sub.circle ? o->theta_deg + o->alpha_deg : o->theta_deg;
+    o->beta_deg = !sub.circle ? o->theta_deg
+                  : (sub.concave ? o->theta_deg - o->alpha_deg : o->theta_deg + o->alpha_deg);
     o->contact_x = Cx;
     o->contact_y = Cy;
 }

@@ -45,7 +45,8 @@ class lbm_geometry(C.Structure):
                 ("mu_circle", C.c_double), ("stripe_arc", C.c_double),
                 ("mu_stripe_b", C.c_double), ("mu_bottom", C.c_double), ("mu_top", C.c_double),
                 ("drop_x", C.c_double), ("drop_y", C.c_double), ("drop_r", C.c_double),
-                ("drop_W", C.c_double), ("rho0", C.POINTER(C.c_double))]
+                ("drop_W", C.c_double), ("rho0", C.POINTER(C.c_double)),
+                ("concave", C.c_int32)]
 
 
 class lbm_angle(C.Structure):
@@ -298,11 +299,12 @@ class Lattice:
             pass
 
     def set_geometry(self, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
-                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None):
+                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False):
         g = lbm_geometry()
         if circle is not None:
             g.has_circle = 1
             g.cx, g.cy, g.R = circle
+            g.concave = 1 if concave else 0
         g.mu_circle = mu_circle
         if stripes is not None:
             g.stripes = 1
@@ -428,11 +430,12 @@ class Batch:
             pass
 
     def set_geometry(self, i, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
-                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None):
+                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False):
         g = lbm_geometry()
         if circle is not None:
             g.has_circle = 1
             g.cx, g.cy, g.R = circle
+            g.concave = 1 if concave else 0
         g.mu_circle = mu_circle
         if stripes is not None:
             g.stripes = 1

@@ -43,6 +43,7 @@ class Workload:
     stripes: tuple | None = None  # (arc length, mu_rel of the odd stripes)
     g: tuple = (0.0, 0.0)
     buoyant: bool = False         # body force (rho - rho_g) g instead of rho g
+    concave: bool = False         # the circle is a cavity (solid outside it, Fig. 2b)
     steps: int = 3000
     measure_every: int = 0
     model: dict = field(default_factory=lambda: dict(MODEL))
@@ -119,6 +120,48 @@ def hysteresis(heterogeneous: bool = True) -> Workload:
     return Workload(name, 4096, 1024, (cx, cy, R), cap_drop(cx, cy, R, r),
                     mu_rel_circle=mu_rel_for_angle(120.0), stripes=stripes,
                     g=(G * math.sin(phi), -G * math.cos(phi)), buoyant=True, steps=200000, measure_every=100)
+
+
+def sweep_instance(R: float, r: float, target_deg: float, concave: bool) -> Workload:
+    """One drop of radius r at rest on a convex cylinder of radius R centred on the bottom
+    boundary, or at the bottom of a circular cavity of radius R whose lowest wall point sits
+    5.5 lu above the bottom boundary (Fig. 2b). The drop starts where an exact circle of radius
+    r meets the wall surface (R + 1/2) at the target angle (law of cosines; |D| from the
+    circle-circle angle), and the wall potential is mu_rel_for_angle(target)."""
+    Rs, t = R + 0.5, math.radians(target_deg)
+    if concave:
+        nx, ny = int(2 * R + 20), int(3 * r + 40)
+        nx += nx % 2
+        cx, cy = nx / 2.0, R + 6.0
+        D = math.sqrt(Rs * Rs + r * r + 2.0 * Rs * r * math.cos(t))
+        drop = (cx, cy - D, r, W_INIT)
+    else:
+        nx, ny = int(2 * R + 4 * r + 40), int(R + 3 * r + 40)
+        nx += nx % 2
+        cx, cy = nx / 2.0, 0.0
+        D = math.sqrt(Rs * Rs + r * r - 2.0 * Rs * r * math.cos(t))
+        drop = (cx, cy + D, r, W_INIT)
+    kind = "cavity" if concave else "cyl"
+    return Workload(f"{kind}{R:g}-r{r:g}-theta{target_deg:g}", nx, ny, (cx, cy, R), drop,
+                    mu_rel_circle=mu_rel_for_angle(target_deg), concave=concave,
+                    steps=30000, measure_every=1000)
+
+
+def curvature_sweep(targets=(70.0, 90.0, 110.0, 130.0, 150.0), radii=(150.0, 250.0, 400.0),
+                    drops=(30.0, 50.0, 70.0, 100.0)) -> list[Workload]:
+    """Grid-independence / curvature sweep (Sec. 4.1-4.2: drops of 30-100 lu on substrates of
+    radius 150-400 lu, hydrophilic to superhydrophobic), on convex cylinders and in cavities.
+    Drops larger than half the substrate radius are left out so that no wetted arc reaches the
+    foot of the cylinder. (A 50-degree target wets the small cylinders into films: the drop
+    spreads down the sides and neither the measurement nor a cap fit describes a drop.)"""
+    out = []
+    for concave in (False, True):
+        for t in targets:
+            for R in radii:
+                for r in drops:
+                    if r <= 0.5 * R:
+                        out.append(sweep_instance(R, r, t, concave))
+    return out
 
 
 def flat_drop(nx=160, ny=80, r=20.0, theta_rel=0.0) -> Workload:

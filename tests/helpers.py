@@ -21,6 +21,8 @@ def oracle_config(O, w, **over):
                   mu_circle=neutral + w.mu_rel_circle)
     if w.stripes is not None:
         kw.update(stripes=1, stripe_arc=w.stripes[0], mu_stripe_b=neutral + w.stripes[1])
+    if w.concave:
+        kw.update(concave=1)
     kw.update(over)
     return O.Config(**kw), mx, neutral
 
@@ -33,12 +35,14 @@ def tanh_drop(nx, ny, x0, y0, r, rho_g, rho_l, W):
     return 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * np.tanh(2.0 * (d - r) / W)
 
 
-def cap_angle_on_circle(Rs, r, D):
+def cap_angle_on_circle(Rs, r, D, concave=False):
     """Contact angle (degrees, through the liquid) of a circular drop of radius r whose centre is
-    at distance D from the centre of a circular substrate of radius Rs: law of cosines in the
-    triangle (substrate centre, drop centre, contact point)."""
+    at distance D from the centre of a circular substrate of radius Rs: cos theta is the dot
+    product of the wall normal into the fluid and the drop's outward normal at the contact point,
+    which the law of cosines in the triangle (substrate centre, drop centre, contact point) gives
+    as (Rs^2 + r^2 - D^2) / (2 Rs r) on a convex circle and its negative in a cavity."""
     c = (Rs**2 + r**2 - D**2) / (2.0 * Rs * r)
-    return float(np.degrees(np.arccos(np.clip(c, -1, 1))))
+    return float(np.degrees(np.arccos(np.clip(-c if concave else c, -1, 1))))
 
 
 def drop_centre_for_angle(Rs, r, theta_deg, cx=0.0, cy=0.0):
@@ -51,23 +55,27 @@ def exact_secant_angle(substrate, drop_c, r, d1, d2, side):
     """Closed-form result of the Fig. 1 construction on an exact circular interface: the points
     of the drop circle (centre drop_c, radius r) at distances d1 and d2 from the substrate, the
     line through them, its intersection with the substrate and the angle (degrees) between that
-    line and the substrate tangent pointing into the liquid. substrate = ("circle", cx, cy, Rs)
-    or ("flat", y_wall). side 0 = left, 1 = right (as seen from the drop centre)."""
+    line and the substrate tangent pointing into the liquid. substrate = ("circle", cx, cy, Rs),
+    ("concave", cx, cy, Rs) (fluid inside the circle) or ("flat", y_wall). side 0 = left,
+    1 = right (as seen from the liquid standing on the wall)."""
     qx, qy = drop_c
+    concave = substrate[0] == "concave"
 
     def point_at(d):
-        if substrate[0] == "circle":
+        if substrate[0] in ("circle", "concave"):
             _, cx, cy, Rs = substrate
-            a = Rs + d
+            a = Rs - d if concave else Rs + d
             dx, dy = qx - cx, qy - cy
             D = np.hypot(dx, dy)
             l = (a * a - r * r + D * D) / (2 * D)
             h = np.sqrt(max(a * a - l * l, 0.0))
             mx, my = cx + l * dx / D, cy + l * dy / D
             cands = [(mx + h * dy / D, my - h * dx / D), (mx - h * dy / D, my + h * dx / D)]
-            # left = counter-clockwise from the drop-centre direction
+            # left = counter-clockwise from the wall normal into the fluid, which is the
+            # drop-centre direction on a convex circle and its opposite in a cavity
             def cross(p):
-                return dx * (p[1] - cy) - dy * (p[0] - cx)
+                c = dx * (p[1] - cy) - dy * (p[0] - cx)
+                return -c if concave else c
             return max(cands, key=cross) if side == 0 else min(cands, key=cross)
         yw = substrate[1]
         y = yw + d
@@ -76,14 +84,14 @@ def exact_secant_angle(substrate, drop_c, r, d1, d2, side):
 
     p1, p2 = np.array(point_at(d1)), np.array(point_at(d2))
     v = (p2 - p1) / np.linalg.norm(p2 - p1)
-    if substrate[0] == "circle":
+    if substrate[0] in ("circle", "concave"):
         _, cx, cy, Rs = substrate
         w = p1 - np.array([cx, cy])
         wv = w @ v
         disc = wv * wv - (w @ w - Rs * Rs)
         s = min([-wv - np.sqrt(disc), -wv + np.sqrt(disc)], key=abs)
         C = p1 + s * v
-        n = (C - np.array([cx, cy])) / Rs
+        n = (C - np.array([cx, cy])) / Rs * (-1.0 if concave else 1.0)
         t = np.array([n[1], -n[0]]) if side == 0 else np.array([-n[1], n[0]])
     else:
         t = np.array([1.0, 0.0]) if side == 0 else np.array([-1.0, 0.0])
@@ -105,5 +113,6 @@ def gpu_lattice(lbm, cfg, precision=0, tile=(0, 0), rho0=None, stream=None):
                      mu_circle=cfg.mu_circle,
                      stripes=(cfg.stripe_arc, cfg.mu_stripe_b) if cfg.stripes else None,
                      mu_bottom=cfg.mu_bottom, mu_top=cfg.mu_top,
-                     drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W), rho0=rho0)
+                     drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W), rho0=rho0,
+                     concave=bool(cfg.concave))
     return lat

@@ -138,3 +138,70 @@ def test_equilibrium_angle_and_series_analysis():
     # advancing at 125 on the 120-degree wall: small positive
     assert R_["force"][1] == pytest.approx(
         2.0 * (math.cos(math.radians(120)) - math.cos(math.radians(125))))
+
+
+def _arc_points(q, r, circle, concave, n=400):
+    """Points of the drop circle (centre q, radius r) lying in the fluid region."""
+    t = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    p = np.column_stack([q[0] + r * np.cos(t), q[1] + r * np.sin(t)])
+    cx, cy, R = circle
+    rad = np.hypot(p[:, 0] - cx, p[:, 1] - cy)
+    d = (R + 0.5) - rad if concave else rad - (R + 0.5)
+    keep = d > 0
+    return p[keep], d[keep]
+
+
+@pytest.mark.parametrize("concave", [False, True])
+def test_cap_angle_closed_form(concave):
+    """Sec. 4.1 on exact circles: the fitted radius is the drop's, R0 from (4H^2 + L^2)/8H equals
+    it, and theta is the circle-circle angle of the law of cosines (convex and cavity)."""
+    from helpers import cap_angle_on_circle
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        R = float(rng.integers(60, 300))
+        r = float(rng.uniform(15, 0.5 * R))
+        th = float(rng.uniform(40, 140))
+        Rs = R + 0.5
+        sgn = 1.0 if concave else -1.0
+        D = math.sqrt(Rs * Rs + r * r + sgn * 2 * Rs * r * math.cos(math.radians(th)))
+        circle = (0.0, 0.0, R)
+        q = (0.3, -D) if concave else (0.3, D)
+        D = math.hypot(*q)
+        p, d = _arc_points(q, r, circle, concave)
+        cap = CM.cap_angle(p, d, circle, concave=concave)
+        assert cap["r"] == pytest.approx(r, rel=1e-9)
+        assert cap["R0"] == pytest.approx(r, rel=1e-7)
+        assert cap["theta"] == pytest.approx(cap_angle_on_circle(Rs, r, D, concave), abs=1e-6)
+
+
+def test_cap_angle_flat_wall():
+    r, th = 20.0, 70.0
+    q = (5.0, -0.5 - r * math.cos(math.radians(th)))
+    t = np.linspace(0, 2 * np.pi, 300, endpoint=False)
+    p = np.column_stack([q[0] + r * np.cos(t), q[1] + r * np.sin(t)])
+    d = p[:, 1] + 0.5
+    cap = CM.cap_angle(p[d > 0], d[d > 0], None)
+    assert cap["theta"] == pytest.approx(th, abs=1e-6) and cap["alpha"] == 0
+
+
+def test_cap_angle_matches_oracle_on_fields(oracle_mod):
+    """Host and oracle implementations of Sec. 4.1 on the same synthetic density fields (the
+    oracle's Eq. 15 link points as input): same fitted circle and angle."""
+    from helpers import tanh_drop
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    rm = 0.5 * (rg + rl)
+    cases = [(dict(has_circle=1, cx=100.0, cy=0.0, R=50.0), (100.3, 62.0, 30.0), (0.0, 0.0, 50.0),
+              False),
+             (dict(has_circle=1, cx=85.0, cy=66.0, R=60.0, concave=1), (85.4, 12.0, 24.0),
+              (85.0, 66.0, 60.0), True)]
+    for kw, (x0, y0, r), circle, concave in cases:
+        cfg = O.Config(nx=200, ny=110, Tr=0.7, **kw)
+        rho = tanh_drop(200, 110, x0, y0, r, rg, rl, 6.0)
+        ids, pd = O.candidates(cfg, rho, rm)
+        circ = (kw["cx"], kw["cy"], kw["R"])
+        host = CM.cap_angle(pd[:, :2], pd[:, 2], circ, concave=concave)
+        ref = O.cap_angle(cfg, rho, rm)
+        assert host["theta"] == pytest.approx(ref["theta"], abs=1e-7)
+        assert host["r"] == pytest.approx(ref["r"], rel=1e-9)

@@ -34,6 +34,8 @@ def _cfgs(O):
         w = W.Workload("t", nx, ny, circ, W.tangent_drop(circ[0], circ[1], circ[2], r),
                        mu_rel_circle=mu_rel)
         out.append(oracle_config(O, w)[0])
+    # a drop at the bottom of a circular cavity (concave substrate)
+    out.append(oracle_config(O, W.sweep_instance(40.0, 14.0, 100.0, True))[0])
     return out
 
 
@@ -44,7 +46,8 @@ def _batch(lbm, cfgs):
                   rho_l=c0.rho_l)
     for i, c in enumerate(cfgs):
         b.set_geometry(i, circle=(c.cx, c.cy, c.R), mu_circle=c.mu_circle, mu_bottom=c.mu_bottom,
-                       mu_top=c.mu_top, drop=(c.drop_x, c.drop_y, c.drop_r, c.drop_W))
+                       mu_top=c.mu_top, drop=(c.drop_x, c.drop_y, c.drop_r, c.drop_W),
+                       concave=bool(c.concave))
     return b
 
 

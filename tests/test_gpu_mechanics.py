@@ -83,3 +83,26 @@ def test_intrinsic_angle_matches_oracle(lbm, oracle_mod):
         ol, orr, _ = ref.measure()
         assert abs(got["left"] - ol.theta) <= 0.5 and abs(got["right"] - orr.theta) <= 0.5
         assert (got["theta"] > 95.0) if target > 90 else (got["theta"] < 85.0), got
+
+
+def test_intrinsic_angle_concave_matches_oracle(lbm, oracle_mod):
+    """The same experiment in a circular cavity (Fig. 2b): library vs oracle within 0.5 degrees
+    on both sides after 6k steps."""
+    from paper_2202_06516_gb300 import contact_mechanics as CM
+    O = oracle_mod
+    m = W.MODEL
+    mx = O.maxwell(m["eos"], m["Tr"])
+    neutral = m["k2"] * mx["mu_sat"]
+    mu_rel = W.mu_rel_for_angle(100.0)
+    got = CM.intrinsic_angle(m, mu_rel, R=60.0, r=24.0, steps=6000, samples=1, concave=True)
+    nx, ny = got["nx"], got["ny"]
+    cfg = O.Config(nx=nx, ny=ny, eos=m["eos"], Tr=m["Tr"], k2=m["k2"], kappa=m["kappa"],
+                   tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"],
+                   rho_g=mx["rho_g"], rho_l=mx["rho_l"], has_circle=1, concave=1,
+                   cx=nx / 2.0, cy=66.0, R=60.0, mu_circle=neutral + mu_rel, mu_bottom=neutral,
+                   mu_top=neutral, drop_x=nx / 2.0, drop_y=5.5, drop_r=24.0, drop_W=5.6)
+    ref = O.Sim(cfg)
+    ref.step(6000)
+    ol, orr, _ = ref.measure()
+    assert ol.status == orr.status == 0
+    assert abs(got["left"] - ol.theta) <= 0.5 and abs(got["right"] - orr.theta) <= 0.5

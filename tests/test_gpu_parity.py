@@ -29,7 +29,8 @@ def _cfg(O, w=None, **over):
 
 
 # --------------------------------------------------------------------------------- geometry
-@pytest.mark.parametrize("case", ["cyl", "stripes", "flat", "halfint", "wrap"])
+@pytest.mark.parametrize("case", ["cyl", "stripes", "flat", "halfint", "wrap", "concave",
+                                  "concave_wrap"])
 def test_geometry_bit_exact(lbm, oracle_mod, case):
     O = oracle_mod
     over = {}
@@ -41,6 +42,12 @@ def test_geometry_bit_exact(lbm, oracle_mod, case):
         over = dict(nx=77, ny=53, cx=38.5, cy=-0.5, R=20.5, drop_x=38.5, drop_y=40, drop_r=8)
     if case == "wrap":
         over = dict(nx=40, ny=30, cx=2.0, cy=3.0, R=9.0, drop_x=20, drop_y=22, drop_r=5)
+    if case == "concave":
+        over = dict(nx=96, ny=70, cx=48.0, cy=40.5, R=38.0, concave=1, stripes=1, stripe_arc=7.0,
+                    mu_stripe_b=0.5, drop_x=48, drop_y=12, drop_r=10)
+    if case == "concave_wrap":
+        over = dict(nx=60, ny=50, cx=1.5, cy=26.0, R=32.5, concave=1, drop_x=1.5, drop_y=10,
+                    drop_r=6)
     cfg = _cfg(O, **over)
     ref = O.Sim(cfg)
     lat = gpu_lattice(lbm, cfg)
@@ -150,6 +157,60 @@ def test_graph_chunks_equal_single_launches(lbm, oracle_mod):
     for _ in range(131):
         b.step(1)
     assert np.array_equal(a.rho(), b.rho())
+
+
+def _concave_cfg(O):
+    """Drop started as a near-hemispherical cap at the bottom of a circular cavity (Fig. 2b) of
+    radius 60 in a 160 x 100 domain (cut by the top wall), on a hydrophilic wall."""
+    cfg, mx, neutral = oracle_config(O, W.plain_small(), nx=160, ny=100, cx=80.0, cy=66.0,
+                                     R=60.0, concave=1, drop_x=80.0, drop_y=8.0, drop_r=24.0)
+    cfg.mu_circle = neutral + W.mu_rel_for_angle(70.0)
+    return cfg
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 3e-5), (1, 1e-9)])
+def test_concave_cavity_matches_oracle(lbm, oracle_mod, precision, tol):
+    """Concave substrate: density after 800 steps against the oracle, then the angles measured
+    on the independently evolved fields within 0.5 degrees (left line at smaller x)."""
+    O = oracle_mod
+    cfg = _concave_cfg(O)
+    ref = O.Sim(cfg)
+    ref.step(800)
+    lat = gpu_lattice(lbm, cfg, precision=precision)
+    lat.step(800)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < tol, err
+    gl, gr = lat.measure()
+    ol, orr, _ = ref.measure()
+    assert gl.status == gr.status == ol.status == orr.status == 0
+    assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
+    assert gl.contact[0] < gr.contact[0]
+    assert gl.beta == pytest.approx(gl.theta - gl.alpha)
+
+
+def test_concave_measure_identical_field_bit_exact(lbm, oracle_mod):
+    """On the same FP32-rounded field in a cavity: candidate links, points and distances bit for
+    bit, the same contact-line links and the same angles."""
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    for (R, cy, r, yc, dx) in [(60.0, 66.0, 22.0, 8.3, 0.4), (70.5, 75.0, 30.0, 10.0, -1.3)]:
+        nx, ny = 170, 100
+        rho = tanh_drop(nx, ny, 85.0 + dx, yc, r, rg, rl, 5.0).astype(np.float32).astype(np.float64)
+        cfg = _cfg(O, nx=nx, ny=ny, cx=85.0, cy=cy, R=R, concave=1)
+        lat = gpu_lattice(lbm, cfg, rho0=rho)
+        ids, pd = lat.candidates()
+        oids, opd = O.candidates(cfg, rho, 0.5 * (rg + rl))
+        assert np.array_equal(ids, oids)
+        assert np.array_equal(pd, opd)
+        gl, gr = lat.measure()
+        ol, orr, _ = O.measure(cfg, rho, 0.5 * (rg + rl))
+        for g, o in ((gl, ol), (gr, orr)):
+            assert g.status == o.status == 0
+            assert (g.link1, g.link2) == (o.link1, o.link2)
+            assert g.d1 == o.d1 and g.d2 == o.d2
+            assert g.theta == pytest.approx(o.theta, abs=1e-6)
+            assert g.beta == pytest.approx(o.beta, abs=1e-6)
 
 
 # ------------------------------------------------------------------------------ measurement

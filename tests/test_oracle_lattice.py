@@ -21,8 +21,9 @@ def _model():
 
 
 # ------------------------------------------------------------------ geometry (Sec. 3.1, Fig. 1)
-def _brute_flags(nx, ny, circle):
-    """Independent classification on the extended rows -2..ny+1."""
+def _brute_flags(nx, ny, circle, concave=False):
+    """Independent classification on the extended rows -2..ny+1 (concave: the circle is a cavity,
+    solid outside it)."""
     rows = ny + 4
     solid = np.zeros((rows, nx), bool)
     for r in range(rows):
@@ -31,7 +32,8 @@ def _brute_flags(nx, ny, circle):
             s = j < 0 or j >= ny
             if circle is not None:
                 cx, cy, R = circle
-                s = s or (i - cx) ** 2 + (j - cy) ** 2 <= R * R
+                inside = (i - cx) ** 2 + (j - cy) ** 2 <= R * R
+                s = s or (inside != concave)
             solid[r, i] = s
     nb = [(1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
     flags = np.where(solid, 3, 0)
@@ -48,16 +50,18 @@ def _brute_flags(nx, ny, circle):
     return flags.astype(np.uint8)
 
 
-@pytest.mark.parametrize("circle", [None, (20.0, 0.0, 9.0), (17.5, 3.0, 6.5), (0.0, 10.0, 7.0)])
-def test_geometry_bruteforce(oracle_mod, circle):
+@pytest.mark.parametrize("circle,concave", [(None, 0), ((20.0, 0.0, 9.0), 0), ((17.5, 3.0, 6.5), 0),
+                                            ((0.0, 10.0, 7.0), 0), ((20.0, 12.0, 10.5), 1),
+                                            ((19.5, 20.0, 17.0), 1), ((0.0, 11.5, 14.0), 1)])
+def test_geometry_bruteforce(oracle_mod, circle, concave):
     O = oracle_mod
     nx, ny = 40, 24
     kw = dict(nx=nx, ny=ny, Tr=0.7)
     if circle:
-        kw.update(has_circle=1, cx=circle[0], cy=circle[1], R=circle[2])
+        kw.update(has_circle=1, cx=circle[0], cy=circle[1], R=circle[2], concave=concave)
     s = O.Sim(O.Config(**kw, drop_x=20, drop_y=30, drop_r=2))
     _, _, flag, _ = s.ext()
-    assert np.array_equal(flag, _brute_flags(nx, ny, circle))
+    assert np.array_equal(flag, _brute_flags(nx, ny, circle, bool(concave)))
     # boundary links: (fluid node, q) with x + e_q solid, in (node, q) order
     ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
     ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
@@ -93,6 +97,33 @@ def test_wall_mu_assignment(oracle_mod):
                 assert muw[r, i] == (0.5 if k % 2 == 0 else 0.25)
             else:
                 assert muw[r, i] == (-1.0 if j < 0 else 2.0)
+
+
+def test_wall_mu_assignment_concave(oracle_mod):
+    """In a cavity the circle's potential (and its stripes) belongs to the layer nodes outside the
+    circle; layer nodes of the wall rows inside the circle keep the flat walls' values."""
+    O = oracle_mod
+    cfg = O.Config(nx=64, ny=40, Tr=0.7, has_circle=1, cx=32, cy=22, R=24, concave=1,
+                   mu_circle=0.5, mu_bottom=-1.0, mu_top=2.0, stripes=1, stripe_arc=5.0,
+                   mu_stripe_b=0.25, drop_x=32, drop_y=10, drop_r=3)
+    s = O.Sim(cfg)
+    _, _, flag, muw = s.ext()
+    seen = set()
+    for r in range(flag.shape[0]):
+        j = r - 2
+        for i in range(64):
+            if flag[r, i] not in (1, 2):
+                assert muw[r, i] == 0
+                continue
+            if (i - 32) ** 2 + (j - 22) ** 2 > 24 * 24:
+                phi = np.arctan2(j - 22, i - 32)
+                k = int(np.floor(24 * (phi - np.pi / 2) / 5.0))
+                assert muw[r, i] == (0.5 if k % 2 == 0 else 0.25)
+                seen.add("circle")
+            else:
+                assert muw[r, i] == (-1.0 if j < 0 else 2.0)
+                seen.add("wall")
+    assert seen == {"circle", "wall"}
 
 
 # ------------------------------------------------------- stencils (Eq. 12, fourth-order FD)
@@ -290,6 +321,73 @@ def _synthetic_cases(n, seed, flat=False):
         out.append(((cx, 0.0, R), nx, int(y0 + r + 20), x0, y0, r,
                     cap_angle_on_circle(R + 0.5, r, D)))
     return out
+
+
+def _synthetic_concave_cases(n, seed):
+    """Circular drops resting in a circular cavity (radius Rs = R + 1/2, centre (cx, cy)) at a
+    prescribed angle: D^2 = Rs^2 + r^2 + 2 Rs r cos(theta), drop centre straight below the cavity
+    centre (plus a sub-node offset), contact points within 60 degrees of the cavity's bottom."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        R = float(rng.integers(60, 160))
+        r = float(rng.uniform(20, 0.6 * R))
+        th = float(rng.uniform(40, 140))
+        Rs = R + 0.5
+        D = np.sqrt(Rs * Rs + r * r + 2 * Rs * r * np.cos(np.radians(th)))
+        cosg = (D * D + Rs * Rs - r * r) / (2 * D * Rs)   # half-angle of the wetted arc
+        if np.degrees(np.arccos(np.clip(cosg, -1, 1))) > 60:
+            continue
+        nx = int(2 * R + 20)
+        cx, cy = float(nx // 2), R + 6.0
+        x0 = cx + rng.uniform(-0.5, 0.5)
+        y0 = cy - D + rng.uniform(-0.5, 0.5)
+        D = np.hypot(x0 - cx, y0 - cy)
+        out.append(((cx, cy, R), nx, int(cy + 10), x0, y0, r,
+                    cap_angle_on_circle(Rs, r, D, concave=True)))
+    return out
+
+
+def test_measure_synthetic_caps_concave(oracle_mod):
+    """The Fig. 1 construction in a cavity (Fig. 2b): on exact circular drops the angle equals the
+    closed-form secant through the chosen points, is within the curvature offset of the true
+    angle, the contact point lies on the wall surface R + 1/2, and beta = theta - alpha."""
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    rm = 0.5 * (rg + rl)
+    for circ, nx, ny, x0, y0, r, th in _synthetic_concave_cases(20, 5):
+        cfg = O.Config(nx=nx, ny=ny, Tr=0.7, has_circle=1, cx=circ[0], cy=circ[1], R=circ[2],
+                       concave=1)
+        sub = ("concave", circ[0], circ[1], circ[2] + 0.5)
+        rho = tanh_drop(nx, ny, x0, y0, r, rg, rl, 10.0)
+        L, R_, _ = O.measure(cfg, rho, rm)
+        for side, a in enumerate((L, R_)):
+            assert a.status == 0
+            assert abs(a.d1 - 1) <= 0.75 and abs(a.d2 - 2) <= 0.75
+            sec = exact_secant_angle(sub, (x0, y0), r, a.d1, a.d2, side)
+            assert a.theta == pytest.approx(sec, abs=0.75)
+            assert abs(a.theta - th) <= np.degrees(1.6 * 1.5 / r) + 0.75
+            assert np.hypot(a.contact[0] - circ[0], a.contact[1] - circ[1]) == \
+                pytest.approx(circ[2] + 0.5, abs=1e-9)
+            assert a.beta == pytest.approx(a.theta - a.alpha)
+        # left is the smaller-x contact line for a drop at the bottom of the cavity
+        assert L.contact[0] < R_.contact[0]
+
+
+def test_cap_method_closed_form_concave(oracle_mod):
+    """Spherical-cap method in a cavity: theta = beta + alpha equals the circle-circle angle."""
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    for circ, nx, ny, x0, y0, r, th in _synthetic_concave_cases(8, 9):
+        cfg = O.Config(nx=nx, ny=ny, Tr=0.7, has_circle=1, cx=circ[0], cy=circ[1], R=circ[2],
+                       concave=1)
+        rho = tanh_drop(nx, ny, x0, y0, r, rg, rl, 6.0)
+        cap = O.cap_angle(cfg, rho, 0.5 * (rg + rl))
+        assert cap["r"] == pytest.approx(r, abs=0.1)
+        assert cap["theta"] == pytest.approx(th, abs=0.5)
+        assert cap["theta"] == pytest.approx(cap["beta"] + cap["alpha"], abs=1e-9)
 
 
 @pytest.mark.parametrize("flat", [False, True])
