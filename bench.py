@@ -482,6 +482,41 @@ def run_sweep(args):
             "sweep": per}
 
 
+def run_boundary(args):
+    """Staircase sensitivity of the equilibrium angle under the two curved-wall schemes: the same
+    drop (r = 40) on cylinders whose radius (R, R + 1/2) and centre (offsets of 0 or 1/2 in x and
+    y) change only how the circle falls on the lattice; the spread of the measured angle over
+    these discretisations, with half-way and with interpolated bounce-back."""
+    import torch
+    from paper_2202_06516_gb300 import lbm, workloads as W, contact_mechanics as CM
+    m = W.MODEL
+    out, t0 = {}, time.perf_counter()
+    for name, bnd in (("halfway", lbm.LBM_BB_HALFWAY), ("interpolated", lbm.LBM_BB_INTERP)):
+        for target in (70.0, 110.0):
+            th, failed = [], []
+            for R in (100.0, 100.5):
+                for off in ((0.0, 0.0), (0.5, 0.0), (0.0, 0.5), (0.5, 0.5)):
+                    try:
+                        res = CM.intrinsic_angle(m, W.mu_rel_for_angle(target), R=R, r=40.0,
+                                                 steps=args.boundary_steps, samples=5,
+                                                 every=1000, boundary=bnd, offset=off)
+                        th.append(res["theta"])
+                    except RuntimeError:
+                        failed.append([R, *off])
+            th = np.array(th)
+            out[f"{name}-{target:g}"] = {"n": len(th), "mean": float(th.mean()),
+                                         "std": float(th.std()),
+                                         "range": float(th.max() - th.min()),
+                                         "values": [round(float(v), 3) for v in th],
+                                         "no_contact": failed}
+    torch.cuda.synchronize()
+    return {"metric": "angle spread over discretisations", "value": None, "unit": "deg",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "staircase-sensitivity-R100-r40",
+                       "steps": args.boundary_steps, "seconds": time.perf_counter() - t0},
+            "boundary": out}
+
+
 def unet_flops(H, Wd, base):
     """Multiply-add FLOPs of one forward pass (2 per MAC) of the U-Net."""
     from paper_2202_06516_gb300 import workloads as W
@@ -704,7 +739,7 @@ def main():
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "warmstart", "surrogate",
-                                                    "hysteresis", "sweep"])
+                                                    "hysteresis", "sweep", "boundary"])
     ap.add_argument("--train-cases", type=int, default=1024)
     ap.add_argument("--eval-cases", type=int, default=64)
     ap.add_argument("--gen-steps", type=int, default=20000)
@@ -715,6 +750,7 @@ def main():
     ap.add_argument("--converge", action="store_true")
     ap.add_argument("--hyst-steps", type=int, default=200000)
     ap.add_argument("--sweep-steps", type=int, default=60000)
+    ap.add_argument("--boundary-steps", type=int, default=30000)
     ap.add_argument("--sweep-tr", default="0.7",
                     help="sweep workload: comma-separated reduced temperatures")
     ap.add_argument("--sweep-detail", action="store_true",
@@ -764,6 +800,10 @@ def main():
     if args.workload == "sweep":
         if rank == 0:
             print(json.dumps(run_sweep(args)), flush=True)
+        return
+    if args.workload == "boundary":
+        if rank == 0:
+            print(json.dumps(run_boundary(args)), flush=True)
         return
     if dist:
         dist.barrier()

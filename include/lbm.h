@@ -42,6 +42,7 @@ enum { LBM_EOS_PR = 0, LBM_EOS_CS = 1 };      /* Peng-Robinson (Eq. 10) or Carna
 enum { LBM_MRT = 0, LBM_BGK = 1 };            /* collision of Eq. 1 or Eq. 3 */
 enum { LBM_FLUID = 0, LBM_LAYER1 = 1, LBM_LAYER2 = 2, LBM_SOLID = 3 }; /* node classes */
 enum { LBM_TILE_AUTO = -1 };                  /* lbm_params.tile_x: choose by autotuning */
+enum { LBM_BB_HALFWAY = 0, LBM_BB_INTERP = 1 }; /* lbm_geometry.boundary: curved-wall scheme */
 
 /* Model parameters (lattice units).
  *  k2, kappa: k^2 and kappa-hat of the mesh-space chemical potential, Eq. 12.
@@ -84,6 +85,17 @@ typedef struct lbm_params {
  *  Wall chemical potential of a wetting-layer node: mu_circle in the circle's solid (or, with stripes,
  *    alternating mu_circle / mu_stripe_b by arc length R*(phi - pi/2) in units of stripe_arc,
  *    phi = atan2(j - cy, i - cx)); mu_bottom below the domain; mu_top above it.
+ *  Boundary scheme for populations whose source node is solid: LBM_BB_HALFWAY returns the
+ *    population that left toward the wall (wall half a link out, exactly mass-conserving);
+ *    LBM_BB_INTERP places the wall on the analytic surfaces (the circle of radius R, the planes
+ *    y = -1/2 and y = ny - 1/2) at the link fraction Delta (at least 1/10), interpolates linearly (between the
+ *    node and its fluid neighbour behind it for Delta < 1/2, between the node's two opposite
+ *    populations for Delta >= 1/2; the half-way value where no fluid neighbour lies behind) and
+ *    adds the difference between the population that left and the one that returns to the
+ *    node's rest population, so mass stays conserved. With LBM_BB_INTERP the measurement takes
+ *    the circular wall surface at radius R. The first step after lbm_set_geometry pulls without
+ *    interpolation (the initial populations are the rest-state equilibrium w_q rho0). Not
+ *    available in batches (lbm_batch_set_geometry returns LBM_ERR_ARG).
  *  Initial density: rho0 (host, (ny, nx), read at fluid nodes) if non-NULL, else the Eq. 16 drop
  *    (drop_x, drop_y, drop_r, width drop_W); populations start at f = f_eq(rho, 0). */
 typedef struct lbm_geometry {
@@ -95,6 +107,7 @@ typedef struct lbm_geometry {
     double drop_x, drop_y, drop_r, drop_W;
     const double *rho0;
     int32_t concave;   /* appended: 0 = solid disc (convex), 1 = solid outside the circle */
+    int32_t boundary;  /* appended: LBM_BB_HALFWAY (default) or LBM_BB_INTERP */
 } lbm_geometry;
 
 /* One side of the contact-angle measurement (Sec. 3.2, Eq. 15, Fig. 1, Fig. 2). Angles in

@@ -54,6 +54,7 @@ class _Cfg(C.Structure):
         ("mu_stripe_b", C.c_double), ("mu_bottom", C.c_double), ("mu_top", C.c_double),
         ("drop_x", C.c_double), ("drop_y", C.c_double), ("drop_r", C.c_double),
         ("drop_W", C.c_double), ("nthreads", C.c_int32), ("concave", C.c_int32),
+        ("interp_bb", C.c_int32),
     ]
 
 
@@ -101,6 +102,7 @@ class Config:
     drop_W: float = 2.0
     nthreads: int = 0
     concave: int = 0
+    interp_bb: int = 0
 
     def _c(self) -> _Cfg:
         c = _Cfg()
@@ -140,6 +142,8 @@ def _load():
     lib.orc_cap_angle.argtypes = [C.POINTER(_Cfg), dp, C.c_double, C.c_double, dp]
     lib.orc_cap_angle.restype = C.c_int
     lib.orc_threads.restype = C.c_int
+    lib.orc_link_fraction.argtypes = [C.POINTER(_Cfg), C.c_int, C.c_int, C.c_int]
+    lib.orc_link_fraction.restype = C.c_double
     _lib = lib
     return lib
 
@@ -214,6 +218,13 @@ def candidates(cfg: Config, rho: np.ndarray, rho_m: float):
     n = _load().orc_candidates(C.byref(c), _dp(rho), rho_m,
                                ids.ctypes.data_as(C.POINTER(C.c_int64)), _dp(pd), cap)
     return ids[:n].copy(), pd[:n].copy()
+
+
+def link_fraction(cfg: Config, i: int, j: int, d: int) -> float:
+    """Fraction of the link from fluid node (i, j) along direction d at which it enters the
+    analytic solid (interpolated bounce-back)."""
+    c = cfg._c()
+    return float(_load().orc_link_fraction(C.byref(c), i, j, d))
 
 
 def cap_angle(cfg: Config, rho: np.ndarray, rho_m: float, dmin: float = 3.0) -> dict:

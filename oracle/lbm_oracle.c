@@ -78,6 +78,7 @@ typedef struct {
     double drop_x, drop_y, drop_r, drop_W; /* Eq. 16 initial drop */
     int32_t nthreads;  /* OpenMP threads (<= 0: runtime default) */
     int32_t concave;   /* 1: the circle is a cavity, solid outside it (Fig. 2b) */
+    int32_t interp_bb; /* 1: interpolated bounce-back on the analytic walls, mass-corrected */
 } orc_cfg;
 
 typedef struct {
@@ -298,6 +299,47 @@ static double wall_mu(const orc_cfg *c, int i, int j) {
     }
     return (j < 0) ? c->mu_bottom : c->mu_top;
 }
+
+/* Fraction Delta in [0, 1] of the link from fluid node (i, j) along direction e_d (whose end
+ * node is solid) at which the segment first enters the analytic solid: the closed disc of
+ * radius R (or, for a cavity, the outside of that circle) and the half-planes y <= -1/2 and
+ * y >= ny - 1/2 of the flat walls. Node classification uses the same closed disc, so the
+ * circle is crossed within the link; the flat walls give Delta = 1/2. Delta is at least 1/10. */
+static double link_fraction(const orc_cfg *c, int i, int j, int d) {
+    double vx = CX[d], vy = CY[d];
+    double best = 2.0;
+    if (vy < 0) {
+        double s = (j + 0.5) / (-vy);
+        if (s >= 0 && s <= 1 && s < best) best = s;
+    } else if (vy > 0) {
+        double s = ((c->ny - 0.5) - j) / vy;
+        if (s >= 0 && s <= 1 && s < best) best = s;
+    }
+    if (c->has_circle) {
+        double px = i - c->cx, py = j - c->cy;
+        double a = vx * vx + vy * vy, b = px * vx + py * vy;
+        double cc = px * px + py * py - c->R * c->R;
+        double disc = b * b - a * cc;
+        if (disc >= 0) {
+            double sq = sqrt(disc);
+            /* entering the disc: first root; leaving the cavity: second root */
+            double s = c->concave ? (-b + sq) / a : (-b - sq) / a;
+            /* a crossing behind the node (moving away from the disc) does not count; a node
+             * on the circle itself starts in the wall */
+            if (s > -1e-12 && s <= 1) {
+                if (s < 0) s = 0;
+                if (s < best) best = s;
+            }
+        }
+    }
+    best = best <= 1.0 ? best : 0.5;
+    /* a wall closer than a tenth of the link is taken at a tenth: as Delta -> 0 the returned
+     * population is copied from the node behind alone, which drove the gas next to a cavity
+     * wall through zero density */
+    return best < 0.1 ? 0.1 : best;
+}
+
+double orc_link_fraction(const orc_cfg *c, int i, int j, int d) { return link_fraction(c, i, j, d); }
 
 static void build_geometry(orc_sim *s) {
     const orc_cfg *c = &s->c;
@@ -567,7 +609,12 @@ void orc_step(orc_sim *s, int nsteps) {
                 s->ux[n] = ux + 0.5 * Fx / rho;
                 s->uy[n] = uy + 0.5 * Fy / rho;
             }
-        /* (6) streaming (Eq. 4) with half-way bounce-back on links into the solid */
+        /* (6) streaming (Eq. 4); a population whose source is solid comes back from the wall:
+         * half-way bounce-back returns the population that left toward it; the interpolated
+         * scheme places the wall at the link fraction Delta (linear interpolation between the
+         * node and its fluid neighbour behind it for Delta < 1/2, between the two opposite
+         * populations of the node for Delta >= 1/2) and adds the difference between what left
+         * and what returns to the rest population, so that no mass is gained or lost. */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -577,10 +624,27 @@ void orc_step(orc_sim *s, int nsteps) {
                     /* pull: population q arriving at (i, j) left (i - cx, j - cy) */
                     int si = wrapx(i - CX[q], nx), sj = j - CY[q];
                     size_t es = (size_t)(sj + 2) * nx + si;
-                    if (s->flag[es] == ORC_FLUID)
+                    if (s->flag[es] == ORC_FLUID) {
                         s->f[n * 9 + q] = s->fpost[((size_t)sj * nx + si) * 9 + q];
-                    else
-                        s->f[n * 9 + q] = s->fpost[n * 9 + OPPOSITE[q]];
+                        continue;
+                    }
+                    int qb = OPPOSITE[q];
+                    double out = s->fpost[n * 9 + qb]; /* left (i, j) toward the wall */
+                    double back = out;
+                    if (c->interp_bb) {
+                        double D = link_fraction(c, i, j, qb);
+                        if (D < 0.5) {
+                            int bi = wrapx(i + CX[q], nx), bj = j + CY[q];
+                            size_t eb = (size_t)(bj + 2) * nx + bi;
+                            if (s->flag[eb] == ORC_FLUID)
+                                back = 2.0 * D * out +
+                                       (1.0 - 2.0 * D) * s->fpost[((size_t)bj * nx + bi) * 9 + qb];
+                        } else {
+                            back = out / (2.0 * D) + (1.0 - 1.0 / (2.0 * D)) * s->fpost[n * 9 + q];
+                        }
+                        s->f[n * 9 + 0] += out - back;
+                    }
+                    s->f[n * 9 + q] = back;
                 }
             }
         s->steps++;
@@ -687,8 +751,12 @@ typedef struct {
     int side;
 } cand_t;
 
+/* Radius of the circular wall surface: half a link beyond the solid nodes with half-way
+ * bounce-back, the analytic circle R itself with interpolated bounce-back. */
+static double wall_radius(const orc_cfg *c) { return c->interp_bb ? c->R : c->R + 0.5; }
+
 /* Substrate distance of point (px, py), measured from the wall into the fluid: to the circle of
- * radius R + 1/2 (the wall lies half a link between the last fluid and the first solid node;
+ * radius R + 1/2 (R with interpolated bounce-back) (the wall lies half a link between the last fluid and the first solid node;
  * outward for a convex disc, inward for a concave cavity) or to the bottom wall plane y = -1/2.
  * Evaluated with separate rounded operations (the library is built without contraction) so that
  * both implementations reach the same bits. */
@@ -696,7 +764,7 @@ static double substrate_dist(const orc_cfg *c, double px, double py) {
     if (c->has_circle) {
         double dx = px - c->cx, dy = py - c->cy;
         double r2 = dx * dx + dy * dy;
-        return c->concave ? (c->R + 0.5) - sqrt(r2) : sqrt(r2) - (c->R + 0.5);
+        return c->concave ? wall_radius(c) - sqrt(r2) : sqrt(r2) - wall_radius(c);
     }
     return py - (-0.5);
 }
@@ -823,7 +891,7 @@ void orc_measure(const orc_cfg *c, const double *rho, double rho_m, orc_angle ou
         vy /= vl;
         double Cx, Cy, tx, ty;
         if (c->has_circle) {
-            double Rs = c->R + 0.5;
+            double Rs = wall_radius(c);
             double wx = o->p1x - c->cx, wy = o->p1y - c->cy;
             double wv = wx * vx + wy * vy;
             double disc = wv * wv - (wx * wx + wy * wy - Rs * Rs);
@@ -963,7 +1031,7 @@ int orc_cap_angle(const orc_cfg *c, const double *rho, double rho_m, double dmin
     /* base chord: intersections of the fitted drop circle with the substrate */
     double c1x, c1y, c2x, c2y, alpha;
     if (c->has_circle) {
-        double Rs = c->R + 0.5;
+        double Rs = wall_radius(c);
         double dx = qx - c->cx, dy = qy - c->cy, D = sqrt(dx * dx + dy * dy);
         if (D >= Rs + rr || D <= fabs(Rs - rr)) return -1;
         double aa = (Rs * Rs - rr * rr + D * D) / (2.0 * D);
@@ -996,7 +1064,7 @@ int orc_cap_angle(const orc_cfg *c, const double *rho, double rho_m, double dmin
             nx_ = -nx_;
             ny_ = -ny_;
         }
-        alpha = asin(L / (2.0 * (c->R + 0.5)));
+        alpha = asin(L / (2.0 * wall_radius(c)));
     } else {
         nx_ = 0;
         ny_ = 1;

@@ -205,25 +205,28 @@ def cap_angle(points, d, circle, concave=False, dmin=3.0) -> dict:
 # ------------------------------------------------------------------ intrinsic contact angle
 def intrinsic_angle(model: dict, mu_rel: float, R: float = 800.0, r: float = 120.0,
                     steps: int = 40000, samples: int = 10, every: int = 2000,
-                    precision: int = L.LBM_FP32, concave: bool = False) -> dict:
+                    precision: int = L.LBM_FP32, concave: bool = False,
+                    boundary: int = L.LBM_BB_HALFWAY, offset=(0.0, 0.0)) -> dict:
     """Equilibrium contact angle a uniform wall of chemical potential neutral + mu_rel produces
     (theta_s of Eq. 18): a drop of radius r started as a 90-degree cap on a cylinder of radius R
     centred on the bottom boundary (convex), or at the bottom of a circular cavity of radius R
     whose lowest wall point sits 5.5 lu above the bottom boundary (concave, Fig. 2b); no body
     force. After `steps` steps the device measures both angles `samples` times, `every` steps
     apart (the contact lines creep across the staircase wall, so single readings scatter by a
-    few degrees); returns the means and the scatter."""
+    few degrees); returns the means and the scatter. offset shifts the circle centre by
+    multiples of 1/2 (a different staircase of the same circle); boundary selects the curved-wall
+    scheme (LBM_BB_HALFWAY or LBM_BB_INTERP)."""
     co = L.lbm_coexistence(model["eos"], model["Tr"])
     neutral = model["k2"] * co["mu_sat"]
     if concave:
         nx, ny = int(2 * R + 20), int(3 * r + 40)
         nx += nx % 2
-        cx, cy = nx / 2.0, R + 6.0
+        cx, cy = nx / 2.0 + offset[0], R + 6.0 + offset[1]
         drop_c = (cx, cy - R - 0.5)
     else:
         nx, ny = int(2 * R + 4 * r + 40), int(R + 3 * r + 40)
         nx += nx % 2
-        cx, cy = nx / 2.0, 0.0
+        cx, cy = nx / 2.0 + offset[0], 0.0 + offset[1]
         drop_c = (cx, cy + R + 0.5)
     lat = L.Lattice(nx, ny, eos=model["eos"], Tr=model["Tr"], k2=model["k2"],
                     kappa=model["kappa"], tau=model["tau"], s_e=model["s_e"],
@@ -234,7 +237,7 @@ def intrinsic_angle(model: dict, mu_rel: float, R: float = 800.0, r: float = 120
         # (concave) the circle centre
         lat.set_geometry(circle=(cx, cy, R), mu_circle=neutral + mu_rel, mu_bottom=neutral,
                          mu_top=neutral, drop=(drop_c[0], drop_c[1], float(r), 5.6),
-                         concave=concave)
+                         concave=concave, boundary=boundary)
         lat.step(steps)
         for k in range(samples):
             if k:

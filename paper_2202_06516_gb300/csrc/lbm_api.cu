@@ -172,6 +172,8 @@ void free_all(lbm_ctx* c) {
     cudaFree(c->muw);
     cudaFree(c->flags);
     cudaFree(c->linkmask);
+    cudaFree(c->dlt);
+    c->dlt = nullptr;
     cudaFree(c->red_partials);
     cudaFree(c->red_out);
     cudaFree(c->meas_partials);
@@ -373,6 +375,9 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
         return fail(c, LBM_ERR_ARG, "lbm_set_geometry: stripe_arc must be positive");
     if (!g->rho0 && !(g->drop_W > 0))
         return fail(c, LBM_ERR_ARG, "lbm_set_geometry: drop_W must be positive");
+    if (g->boundary != LBM_BB_HALFWAY && g->boundary != LBM_BB_INTERP)
+        return fail(c, LBM_ERR_ARG, "lbm_set_geometry: boundary must be LBM_BB_HALFWAY or "
+                                    "LBM_BB_INTERP");
     DeviceGuard dg(c->device);
     lbm::GeomArgs a{};
     a.nx = c->nx;
@@ -397,6 +402,23 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     LBM_CUDA(c, cudaMemsetAsync(c->muw, 0, c->plane * c->esz, c->stream));
     LBM_CUDA(c, cudaMemsetAsync(c->linkmask, 0, c->plane, c->stream));
     LBM_CUDA(c, lbm::launch_geometry(c, a));
+    // captured step graphs hold the previous boundary scheme
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+    }
+    c->ibb = g->boundary == LBM_BB_INTERP;
+    if (c->ibb) {
+        if (!c->dlt) LBM_CUDA(c, cudaMalloc(&c->dlt, 8 * c->plane * c->esz));
+        LBM_CUDA(c, lbm::launch_link_fractions(c, a));
+        // the interpolated scheme is compiled for the default tile variant only
+        if (!lbm::step_has_ibb(c->esz, c->tile_x, c->tile_y, c->min_blocks)) {
+            c->tile_x = 32;
+            c->tile_y = 16;
+            c->min_blocks = c->esz == 4 ? 5 : 0;
+            LBM_CUDA(c, lbm::step_configure(c));
+        }
+    }
     double* d_rho0 = nullptr;
     if (g->rho0) {
         const size_t nb = sizeof(double) * (size_t)c->nx * c->ny;
@@ -417,7 +439,9 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     c->sub.concave = g->has_circle && g->concave ? 1 : 0;
     c->sub.cx = g->cx;
     c->sub.cy = g->cy;
-    c->sub.Rs = g->R + 0.5;
+    // the wall surface: half a link beyond the solid nodes (half-way bounce-back) or the
+    // analytic circle itself (interpolated bounce-back)
+    c->sub.Rs = c->ibb ? g->R : g->R + 0.5;
     c->cur = 0;
     c->steps = 0;
     c->has_geometry = true;
@@ -435,6 +459,17 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
         if (st != LBM_OK) return st;
     }
     int64_t left = nsteps;
+    if (c->ibb && c->steps == 0 && left > 0) {
+        // the initial populations are f = w rho0 themselves (the stored state encodes them for
+        // half-way pulls): nothing has come back from a wall yet, so the first step pulls
+        // without interpolation
+        c->ibb = false;
+        const cudaError_t e = lbm::launch_step(c, c->cur, false);
+        c->ibb = true;
+        LBM_CUDA(c, e);
+        c->cur ^= 1;
+        --left;
+    }
     if (left >= lbm::kGraphChunk && !c->graph[c->cur] && !c->graph_failed) capture_graph(c, c->cur);
     while (left >= lbm::kGraphChunk && c->graph[c->cur]) {
         LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
@@ -456,6 +491,12 @@ lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, lbm_tune_entry* entries
     DeviceGuard dg(c->device);
     std::vector<lbm::StepVariant> vs;
     lbm::step_variants(c->esz, &vs);
+    if (c->ibb) {  // interpolated bounce-back: only the variants compiled with it
+        std::vector<lbm::StepVariant> keep_ibb;
+        for (const auto& v : vs)
+            if (lbm::step_has_ibb(c->esz, v.tile_x, v.tile_y, v.min_blocks)) keep_ibb.push_back(v);
+        vs.swap(keep_ibb);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     LBM_CUDA(c, cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);

@@ -399,6 +399,8 @@ lbm_status lbm_batch_create(const lbm_params* model, int32_t n, const int32_t* n
 lbm_status lbm_batch_set_geometry(lbm_batch* b, int32_t i, const lbm_geometry* g) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_set_geometry: batch is NULL");
     if (i < 0 || i >= b->n) return bfail(b, LBM_ERR_ARG, "lbm_batch_set_geometry: bad index");
+    if (g && g->boundary != LBM_BB_HALFWAY)
+        return bfail(b, LBM_ERR_ARG, "lbm_batch_set_geometry: batches use half-way bounce-back");
     lbm_status st = lbm_set_geometry(b->inst[i], g);
     if (st != LBM_OK) return bfail(b, st, lbm_last_error(b->inst[i]));
     b->cur[i] = 0;

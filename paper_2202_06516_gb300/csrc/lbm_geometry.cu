@@ -109,6 +109,61 @@ __global__ void k_linkmask(const uint8_t* flags, uint8_t* mask, unsigned long lo
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(n_fluid, local);
 }
 
+// Fraction of the link from fluid node (i, j) along e_d at which it first enters the analytic
+// solid: the closed disc of radius R (its outside for a cavity) or the half-planes y <= -1/2 and
+// y >= ny - 1/2, at least 1/10. Every operation is a separately rounded IEEE double operation.
+__device__ double link_fraction(const GeomArgs& g, int i, int j, int d) {
+    const double vx = qx(d), vy = qy(d);
+    double best = 2.0;
+    if (vy < 0) {
+        const double s = __ddiv_rn(__dadd_rn((double)j, 0.5), -vy);
+        if (s >= 0 && s <= 1 && s < best) best = s;
+    } else if (vy > 0) {
+        const double s = __ddiv_rn(__dsub_rn(__dsub_rn((double)g.ny, 0.5), (double)j), vy);
+        if (s >= 0 && s <= 1 && s < best) best = s;
+    }
+    if (g.has_circle) {
+        const double px = __dsub_rn((double)i, g.cx), py = __dsub_rn((double)j, g.cy);
+        const double a = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
+        const double b = __dadd_rn(__dmul_rn(px, vx), __dmul_rn(py, vy));
+        const double cc = __dsub_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)),
+                                    __dmul_rn(g.R, g.R));
+        const double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(a, cc));
+        if (disc >= 0) {
+            const double sq = __dsqrt_rn(disc);
+            double s = g.concave ? __ddiv_rn(__dadd_rn(-b, sq), a) : __ddiv_rn(__dsub_rn(-b, sq), a);
+            // a crossing behind the node (moving away from the disc) does not count; a node on
+            // the circle itself starts in the wall
+            if (s > -1e-12 && s <= 1) {
+                if (s < 0) s = 0;
+                if (s < best) best = s;
+            }
+        }
+    }
+    best = best <= 1.0 ? best : 0.5;
+    // a wall closer than a tenth of the link is taken at a tenth (Delta -> 0 copies the returned
+    // population from the node behind alone, which is unstable next to a cavity wall)
+    return best < 0.1 ? 0.1 : best;
+}
+
+// dlt[(q - 1) * plane + x] = link fraction toward the solid source x - e_q of population q
+template <typename T>
+__global__ void k_link_fractions(const uint8_t* flags, T* dlt, GeomArgs g) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < (long long)g.ny * g.nx;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(n / g.nx), i = (int)(n % g.nx);
+        const int o = lidx(g.P, i, j);
+        const bool fluid = flags[o] == kFluid;
+#pragma unroll 1
+        for (int q = 1; q < 9; ++q) {
+            double v = 0.5;
+            if (fluid && flags[lidx(g.P, wrap(i - qx(q), g.nx), j - qy(q))] != kFluid)
+                v = link_fraction(g, i, j, qopp(q));
+            dlt[(size_t)(q - 1) * g.plane + o] = (T)v;
+        }
+    }
+}
+
 // Eq. 16 drop (or a given density) at fluid nodes; zero elsewhere
 template <typename T>
 __global__ void k_init_rho(const uint8_t* flags, T* rho, T* rho_other, const double* rho0,
@@ -208,6 +263,19 @@ cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g) {
     c->n_fluid = (int64_t)nfl;
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t launch_link_fractions(lbm_ctx* c, const GeomArgs& g) {
+    const long long nf = (long long)c->ny * c->nx;
+    if (c->esz == 4)
+        k_link_fractions<float><<<grid_for(nf), kThreads, 0, c->stream>>>(c->flags, (float*)c->dlt, g);
+    else
+        k_link_fractions<double><<<grid_for(nf), kThreads, 0, c->stream>>>(c->flags, (double*)c->dlt,
+                                                                           g);
+    cudaError_t e = cudaGetLastError();
+    for (int q = 0; q < 8 && e == cudaSuccess; ++q)
+        e = launch_fill_pads(c, (char*)c->dlt + (size_t)q * c->plane * c->esz, c->esz);
+    return e;
 }
 
 cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& geo, const double* d_rho0) {

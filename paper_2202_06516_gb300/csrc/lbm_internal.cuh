@@ -59,6 +59,7 @@ struct StepArgs {
     T* rho_out;        // rho(t+1)
     const uint8_t* flags;
     const T* muw;      // wall chemical potential on the wetting layers
+    const T* dlt;      // interpolated bounce-back: link fraction of direction q at plane q - 1
     T* vx;             // optional velocity output (macroscopic mode)
     T* vy;
     int nx, ny, P;
@@ -105,6 +106,8 @@ struct lbm_ctx {
     void* muw = nullptr;
     uint8_t* flags = nullptr;
     uint8_t* linkmask = nullptr;   // per node, bit q-1 set when fluid x has a solid x + e_q
+    void* dlt = nullptr;           // 8 planes of link fractions (interpolated bounce-back)
+    bool ibb = false;
     int cur = 0;
     bool has_geometry = false;
     int64_t steps = 0;
@@ -137,6 +140,7 @@ constexpr int kAutotuneTrial = 20;  // timed launches per variant when LBM_TILE_
 
 // launchers (return the CUDA error of the launch)
 cudaError_t launch_geometry(lbm_ctx* c, const GeomArgs& g);
+cudaError_t launch_link_fractions(lbm_ctx* c, const GeomArgs& g);
 cudaError_t launch_init_state(lbm_ctx* c, const lbm_geometry& g, const double* d_rho0);
 cudaError_t launch_step(lbm_ctx* c, int src, bool macro);
 size_t step_smem_bytes(int tile_x, int tile_y, size_t esz, int min_blocks);
@@ -145,6 +149,7 @@ struct StepVariant {
 };
 // the compiled step-kernel variants for element size esz (4: FP32, 8: FP64)
 void step_variants(size_t esz, std::vector<StepVariant>* out);
+bool step_has_ibb(size_t esz, int tile_x, int tile_y, int min_blocks);
 cudaError_t step_configure(lbm_ctx* c);
 cudaError_t launch_reduce(lbm_ctx* c);
 cudaError_t launch_measure(lbm_ctx* c);

@@ -27,14 +27,30 @@ namespace {
 
 using namespace stepdev;
 
+// the interpolated bounce-back kernels exist for the default variants only (32 x 16 tiles,
+// 5 CTAs per SM in FP32, unconstrained in FP64)
+template <typename T, int TX, int TY, int MINB>
+constexpr bool has_ibb() {
+    return TX == 32 && TY == 16 && MINB == (sizeof(T) == 4 ? 5 : 1);
+}
+
 template <typename T, int TX, int TY, int MINB>
 cudaError_t configure_one() {
     using L = Layout<T, TX, TY>;
     cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, 256, false, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step<T, TX, TY, 256, true, MINB>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step<T, TX, TY, 256, true, MINB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if constexpr (has_ibb<T, TX, TY, MINB>()) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_step<T, TX, TY, 256, false, MINB, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_step<T, TX, TY, 256, true, MINB, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    }
+    return e;
 }
 
 template <typename T, int TX, int TY, int MINB>
@@ -42,6 +58,17 @@ cudaError_t launch_one(lbm_ctx* c, const StepArgs<T>& a, bool macro) {
     using L = Layout<T, TX, TY>;
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY);
     const T rho_mid = (T)(0.5 * (c->rho_g + c->rho_l));
+    if (c->ibb) {
+        if constexpr (has_ibb<T, TX, TY, MINB>()) {
+            if (macro)
+                k_step<T, TX, TY, 256, true, MINB, true><<<grid, 256, L::bytes, c->stream>>>(a, rho_mid);
+            else
+                k_step<T, TX, TY, 256, false, MINB, true><<<grid, 256, L::bytes, c->stream>>>(a,
+                                                                                         rho_mid);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     if (macro)
         k_step<T, TX, TY, 256, true, MINB><<<grid, 256, L::bytes, c->stream>>>(a, rho_mid);
     else
@@ -62,6 +89,7 @@ StepArgs<T> make_args(lbm_ctx* c, int src) {
     a.rho_out = (T*)c->rho[src ^ 1];
     a.flags = c->flags;
     a.muw = (const T*)c->muw;
+    a.dlt = (const T*)c->dlt;
     a.vx = (T*)c->vel;
     a.vy = c->vel ? (T*)c->vel + c->plane : nullptr;
     a.nx = c->nx;
@@ -105,6 +133,10 @@ size_t step_smem_bytes(int tx, int ty, size_t esz, int min_blocks) {
     LBM_STEP_VARIANTS(X)
 #undef X
     return 0;
+}
+
+bool step_has_ibb(size_t esz, int tx, int ty, int min_blocks) {
+    return tx == 32 && ty == 16 && min_blocks == (esz == 4 ? 5 : 0);
 }
 
 void step_variants(size_t esz, std::vector<StepVariant>* out) {

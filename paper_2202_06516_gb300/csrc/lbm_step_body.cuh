@@ -189,6 +189,32 @@ __device__ __forceinline__ T mu_fluid(const T* s_rho, int o, const StepArgs<T>& 
     return fma_rn(a.k2, psi_prime<T>(c0, a), mul_rn(mul_rn(a.kappa, (T)-1 / (T)12), lap12));
 }
 
+// Interpolated bounce-back of population q at fluid node x whose source x - e_q is solid, as a
+// deviation from w_q rho(x). out = h_qbar(x) is the deviation of the population that left x
+// toward the wall (what half-way bounce-back returns). With the wall at the link fraction D:
+//   D < 1/2: 2D f*_qbar(x) + (1 - 2D) f*_qbar(x + e_q)   (the half-way value if x + e_q is not
+//            fluid), i.e. 2D out + (1 - 2D) (h_qbar(x + e_q) + w_q (rho(x + e_q) - rho(x)));
+//   D >= 1/2: f*_qbar(x) / 2D + (1 - 1/2D) f*_q(x), i.e. out / 2D + (1 - 1/2D) h_q(x).
+// The caller adds out minus the returned value to the rest population (mass correction).
+template <typename T, int RW, bool PP>
+__device__ __forceinline__ T ibb_return(const StepArgs<T>& a, int q, unsigned us, int o, T rho,
+                                        T out, const T* s_rho, const uint8_t* s_flag) {
+    const T D = a.dlt[(unsigned)(q - 1) * (unsigned)a.plane + us];
+    const T D2 = add_rn(D, D);
+    if (D < (T)0.5) {
+        const int ob = o + qy(q) * RW + qx(q);
+        if (s_flag[ob] != kFluid) return out;
+        const unsigned ub = us + (unsigned)(qy(q) * a.P + qx(q));
+        const T hbh = PP ? __ldg(a.hq_in[qopp(q)] + ub)
+                         : __ldg(a.h_in + (unsigned)qopp(q) * (unsigned)a.plane + ub);
+        const T behind = fma_rn(qw<T>(q), sub_rn(s_rho[ob], rho), hbh);
+        return fma_rn(D2, out, mul_rn(sub_rn((T)1, D2), behind));
+    }
+    const T hq = PP ? __ldg(a.hq_in[q] + us) : __ldg(a.h_in + (unsigned)q * (unsigned)a.plane + us);
+    const T c = recip(D2);
+    return fma_rn(c, out, mul_rn(sub_rn((T)1, c), hq));  // exactly out at D = 1/2
+}
+
 // (6) of the step: new density rho(t+1) = sum_q f*_q(x - e_q) (half-way bounce-back where the
 // source is not fluid) and the stored deviations f*_q(x) - w_q rho(t+1)(x). EDGE: the tile lies
 // within kPadX of an x edge and also writes the periodic images into the pads. PP: the planes
@@ -250,8 +276,9 @@ __device__ __forceinline__ void stream_out(const StepArgs<T>& a, const T* s_rho,
 
 // MIXED: the tile and its halo contain non-fluid nodes (walls, the disc, the domain edge), so
 // wetting layers are rebuilt and every neighbour access checks the node class. Interior tiles
-// take the branch-free path (the choice is uniform per CTA).
-template <typename T, int TX, int TY, int NT, bool MACRO, bool MIXED, bool PP>
+// take the branch-free path (the choice is uniform per CTA). IBB: interpolated, mass-corrected
+// bounce-back on cut links (a separate kernel, so the default one carries none of its code).
+template <typename T, int TX, int TY, int NT, bool MACRO, bool MIXED, bool PP, bool IBB = false>
 __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid, T* s_rho,
                                           T* s_mu, T* s_g, const uint8_t* s_flag, int x0,
                                           int y0) {
@@ -352,6 +379,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
         T g[9];
         g[0] = PP ? __ldg(a.hq_in[0] + r0) : __ldg(hb);
         T A = mul_rn(qw<T>(0), rho);  // sum_q w_q rho(x - e_q); bounce-back sources take rho(x)
+        T dm = (T)0;                  // interpolated bounce-back: mass returned to the rest population
 #pragma unroll
         for (int q = 1; q < 9; ++q) {
             const int os = o - qy(q) * RW - qx(q);
@@ -363,10 +391,16 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
                 g[q] = fma_rn(qw<T>(q), sub_rn(rs, rho), h);
                 A = fma_rn(qw<T>(q), rs, A);
             } else {
-                g[q] = PP ? __ldg(a.hq_in[qopp(q)] + r0) : __ldg(hb + (int)QPL(qopp(q)));
+                const T out = PP ? __ldg(a.hq_in[qopp(q)] + r0) : __ldg(hb + (int)QPL(qopp(q)));
+                g[q] = out;
+                if (MIXED && IBB) {
+                    g[q] = ibb_return<T, RW, PP>(a, q, us, o, rho, out, s_rho, s_flag);
+                    dm = add_rn(dm, sub_rn(out, g[q]));
+                }
                 A = fma_rn(qw<T>(q), rho, A);
             }
         }
+        if (MIXED && IBB) g[0] = add_rn(g[0], dm);
         T ux, uy;
         collide<T>(g, rho, Fx, Fy, a, ux, uy);
         if (MACRO) {
@@ -425,7 +459,7 @@ __device__ __forceinline__ int stage_load(const StepArgs<T>& a, T* s_rho, uint8_
 }
 
 // One time step of one TX x TY tile with origin (x0, y0); smem holds Layout<T, TX, TY>::bytes.
-template <typename T, int TX, int TY, int NT, bool MACRO, bool PP>
+template <typename T, int TX, int TY, int NT, bool MACRO, bool PP, bool IBB = false>
 __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
                                           unsigned char* smem, int x0, int y0) {
     using L = Layout<T, TX, TY>;
@@ -439,15 +473,17 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
     // a tile without fluid nodes (inside the disc or the wall rows) has nothing to write
     if (!__syncthreads_or(any & 2)) return;
     if (mixed)
-        step_body<T, TX, TY, NT, MACRO, true, PP>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
+        step_body<T, TX, TY, NT, MACRO, true, PP, IBB>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0,
+                                                       y0);
     else
         step_body<T, TX, TY, NT, MACRO, false, PP>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0, y0);
 }
 
-template <typename T, int TX, int TY, int NT, bool MACRO, int MINB>
+template <typename T, int TX, int TY, int NT, bool MACRO, int MINB, bool IBB = false>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs<T> a, const T rho_mid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_tile<T, TX, TY, NT, MACRO, true>(a, rho_mid, smem_raw, blockIdx.x * TX, blockIdx.y * TY);
+    step_tile<T, TX, TY, NT, MACRO, true, IBB>(a, rho_mid, smem_raw, blockIdx.x * TX,
+                                               blockIdx.y * TY);
 }
 
 }  // namespace stepdev

@@ -20,6 +20,7 @@ LBM_EOS_PR, LBM_EOS_CS = 0, 1
 LBM_MRT, LBM_BGK = 0, 1
 LBM_FIELD_RHO, LBM_FIELD_VEL, LBM_FIELD_DEVICE_DST = 1, 2, 4
 LBM_TILE_AUTO = -1
+LBM_BB_HALFWAY, LBM_BB_INTERP = 0, 1
 
 
 class LbmError(RuntimeError):
@@ -46,7 +47,7 @@ class lbm_geometry(C.Structure):
                 ("mu_stripe_b", C.c_double), ("mu_bottom", C.c_double), ("mu_top", C.c_double),
                 ("drop_x", C.c_double), ("drop_y", C.c_double), ("drop_r", C.c_double),
                 ("drop_W", C.c_double), ("rho0", C.POINTER(C.c_double)),
-                ("concave", C.c_int32)]
+                ("concave", C.c_int32), ("boundary", C.c_int32)]
 
 
 class lbm_angle(C.Structure):
@@ -299,8 +300,10 @@ class Lattice:
             pass
 
     def set_geometry(self, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
-                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False):
+                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False,
+                     boundary=LBM_BB_HALFWAY):
         g = lbm_geometry()
+        g.boundary = boundary
         if circle is not None:
             g.has_circle = 1
             g.cx, g.cy, g.R = circle
@@ -430,8 +433,10 @@ class Batch:
             pass
 
     def set_geometry(self, i, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
-                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False):
+                     mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False,
+                     boundary=LBM_BB_HALFWAY):
         g = lbm_geometry()
+        g.boundary = boundary
         if circle is not None:
             g.has_circle = 1
             g.cx, g.cy, g.R = circle

@@ -114,5 +114,5 @@ def gpu_lattice(lbm, cfg, precision=0, tile=(0, 0), rho0=None, stream=None):
                      stripes=(cfg.stripe_arc, cfg.mu_stripe_b) if cfg.stripes else None,
                      mu_bottom=cfg.mu_bottom, mu_top=cfg.mu_top,
                      drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W), rho0=rho0,
-                     concave=bool(cfg.concave))
+                     concave=bool(cfg.concave), boundary=int(cfg.interp_bb))
     return lat

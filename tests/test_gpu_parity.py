@@ -213,6 +213,84 @@ def test_concave_measure_identical_field_bit_exact(lbm, oracle_mod):
             assert g.beta == pytest.approx(o.beta, abs=1e-6)
 
 
+def _ibb_cfg(O, **over):
+    """Drop on a cylinder (or in a cavity) with the interpolated, mass-corrected bounce-back."""
+    cfg, mx, neutral = oracle_config(O, W.plain_small(), nx=96, ny=64, cx=48.0, R=20.5,
+                                     drop_x=48.3, drop_y=20.5 + 13.0, drop_r=14.0, interp_bb=1,
+                                     stripes=1, stripe_arc=6.0)
+    cfg.mu_stripe_b = neutral + 0.02
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+@pytest.mark.parametrize("concave,precision,tol", [(0, 1, 1e-9), (0, 0, 3e-5), (1, 1, 1e-9),
+                                                   (1, 0, 3e-5)])
+def test_interp_bb_matches_oracle(lbm, oracle_mod, concave, precision, tol):
+    """Interpolated bounce-back (link fractions from the analytic wall, mass correction) on a
+    striped cylinder and in a cavity: density against the oracle after 600 steps, the mass
+    conserved, and the angles on the independently evolved fields within 0.5 degrees."""
+    O = oracle_mod
+    over = dict(concave=concave)
+    if concave:
+        over.update(cx=48.0, cy=40.0, R=37.0, drop_x=48.3, drop_y=9.0, drop_r=14.0)
+    cfg = _ibb_cfg(O, **over)
+    ref = O.Sim(cfg)
+    ref.step(600)
+    lat = gpu_lattice(lbm, cfg, precision=precision)
+    m0 = lat.mass()["mass"]
+    lat.step(600)
+    err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
+    assert err < tol, err
+    assert abs(lat.mass()["mass"] - m0) / m0 < (1e-12 if precision else 1e-6)
+    gl, gr = lat.measure()
+    ol, orr, _ = ref.measure()
+    assert gl.status == gr.status == ol.status == orr.status == 0
+    assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
+
+
+def test_interp_bb_flat_walls_equal_halfway(lbm, oracle_mod):
+    """Flat walls only: every link fraction is 1/2 and the interpolated run equals the half-way
+    run bit for bit on the GPU too."""
+    O = oracle_mod
+    cfg = _ibb_cfg(O, has_circle=0, stripes=0, drop_y=10.0)
+    a = gpu_lattice(lbm, cfg)
+    cfg.interp_bb = 0
+    b = gpu_lattice(lbm, cfg)
+    a.step(500)
+    b.step(500)
+    assert np.array_equal(a.rho(), b.rho())
+
+
+def test_interp_bb_measure_identical_field(lbm, oracle_mod):
+    """With interpolated bounce-back the wall surface is the circle R itself: candidate points,
+    distances and chosen links bit for bit on an identical field."""
+    O = oracle_mod
+    mx = O.maxwell(0, 0.7)
+    rg, rl = mx["rho_g"], mx["rho_l"]
+    nx, ny = 200, 120
+    rho = tanh_drop(nx, ny, 100.4, 58.0, 25.0, rg, rl, 5.0).astype(np.float32).astype(np.float64)
+    cfg = _cfg(O, nx=nx, ny=ny, cx=100.0, R=40.0, interp_bb=1)
+    lat = gpu_lattice(lbm, cfg, rho0=rho)
+    ids, pd = lat.candidates()
+    oids, opd = O.candidates(cfg, rho, 0.5 * (rg + rl))
+    assert np.array_equal(ids, oids) and np.array_equal(pd, opd)
+    gl, gr = lat.measure()
+    ol, orr, _ = O.measure(cfg, rho, 0.5 * (rg + rl))
+    for g, o in ((gl, ol), (gr, orr)):
+        assert (g.link1, g.link2) == (o.link1, o.link2)
+        assert g.theta == pytest.approx(o.theta, abs=1e-6)
+        assert np.hypot(g.contact[0] - 100.0, g.contact[1]) == pytest.approx(40.0, abs=1e-9)
+
+
+def test_interp_bb_rejected_in_batches(lbm, oracle_mod):
+    b = lbm.Batch([(64, 48)], Tr=0.7)
+    with pytest.raises(lbm.LbmError):
+        b.set_geometry(0, circle=(32.0, 0.0, 10.0), drop=(32.0, 20.0, 6.0, 5.6),
+                       boundary=lbm.LBM_BB_INTERP)
+    b.close()
+
+
 # ------------------------------------------------------------------------------ measurement
 def test_measure_identical_field_bit_exact(lbm, oracle_mod):
     """On the same (FP32-rounded) density field the GPU finds the same liquid/gas links, points

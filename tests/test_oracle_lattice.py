@@ -473,3 +473,122 @@ def test_equilibrium_present_vs_cap(oracle_mod):
     assert L.theta == pytest.approx(R_.theta, abs=0.2)
     assert L.theta == pytest.approx(cap["theta"], abs=2.0)
     assert L.theta == pytest.approx(L1.theta, abs=0.2)
+
+
+# ------------------------------------------- interpolated bounce-back (curved-wall variant)
+def _in_analytic_solid(x, y, ny, circle, concave):
+    if y <= -0.5 or y >= ny - 0.5:
+        return True
+    if circle is None:
+        return False
+    cx, cy, R = circle
+    inside = (x - cx) ** 2 + (y - cy) ** 2 <= R * R
+    return inside != concave
+
+
+def _brute_fraction(i, j, d, ny, circle, concave, n=4001):
+    """First s in [0, 1] at which the point (i, j) + s e_d lies in the analytic solid: a scan,
+    then bisection on the first bracket."""
+    ex = [0, 1, 0, -1, 0, 1, -1, -1, 1][d]
+    ey = [0, 0, 1, 0, -1, 1, 1, -1, -1][d]
+    s = np.linspace(0.0, 1.0, n)
+    hit = [k for k in range(n) if _in_analytic_solid(i + s[k] * ex, j + s[k] * ey, ny, circle,
+                                                     concave)]
+    k = hit[0]
+    if k == 0:
+        return 0.0
+    lo, hi = s[k - 1], s[k]
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if _in_analytic_solid(i + mid * ex, j + mid * ey, ny, circle, concave):
+            hi = mid
+        else:
+            lo = mid
+    return hi
+
+
+@pytest.mark.parametrize("circle,concave", [((20.0, 0.0, 9.0), 0), ((17.5, 3.0, 6.5), 0),
+                                            ((20.0, 12.0, 10.5), 1), (None, 0)])
+def test_link_fraction_bruteforce(oracle_mod, circle, concave):
+    """Link fractions of every cut link against a scan-and-bisect of the analytic wall; flat
+    walls sit half way."""
+    O = oracle_mod
+    nx, ny = 40, 24
+    kw = dict(nx=nx, ny=ny, Tr=0.7)
+    if circle:
+        kw.update(has_circle=1, cx=circle[0], cy=circle[1], R=circle[2], concave=concave)
+    cfg = O.Config(**kw, drop_x=20, drop_y=30, drop_r=2)
+    _, _, flag, _ = O.Sim(cfg).ext()
+    ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    checked = 0
+    for j in range(ny):
+        for i in range(nx):
+            if flag[j + 2, i] != 0:
+                continue
+            for d in range(1, 9):
+                if flag[j + 2 + ey[d], (i + ex[d]) % nx] == 0:
+                    continue
+                got = O.link_fraction(cfg, i, j, d)
+                assert 0.0 <= got <= 1.0
+                if not 0 <= i + ex[d] < nx:
+                    continue   # across the periodic edge (the circle has no periodic image)
+                # the scheme takes walls closer than a tenth of the link at a tenth
+                want = max(_brute_fraction(i, j, d, ny, circle, bool(concave)), 0.1)
+                assert got == pytest.approx(want, abs=1e-6), (i, j, d)
+                checked += 1
+    assert checked > 20
+
+
+def _ibb_cfg(O, **over):
+    cfg, mx, neutral = oracle_config(O, W.plain_small(), nx=96, ny=64, cx=48.0, R=20.0,
+                                     drop_x=48.0, drop_y=20.0 + 14.0, drop_r=14.0, interp_bb=1)
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def test_interp_bb_reduces_to_halfway_on_flat_walls(oracle_mod):
+    """With only flat walls every link fraction is 1/2, where the interpolation returns the
+    outgoing population exactly: the interpolated run equals the half-way run bit for bit."""
+    O = oracle_mod
+    a = O.Sim(_ibb_cfg(O, has_circle=0, drop_y=10.0))
+    b = O.Sim(_ibb_cfg(O, has_circle=0, drop_y=10.0, interp_bb=0))
+    a.step(300)
+    b.step(300)
+    assert np.array_equal(a.f(), b.f())
+
+
+@pytest.mark.parametrize("concave", [0, 1])
+def test_interp_bb_conserves_mass_and_differs(oracle_mod, concave):
+    """The mass correction keeps the total mass to round-off on a circle (convex and cavity),
+    and the scheme is live: the fields differ from the half-way run (by a shift of the contact
+    line, a small fraction of the density jump)."""
+    O = oracle_mod
+    over = dict(concave=concave)
+    if concave:
+        over.update(cx=48.0, cy=40.0, R=37.0, drop_y=10.0)
+    a = O.Sim(_ibb_cfg(O, **over))
+    b = O.Sim(_ibb_cfg(O, interp_bb=0, **over))
+    m0 = a.mass()
+    a.step(400)
+    b.step(400)
+    assert abs(a.mass() - m0) / m0 < 1e-12
+    d = np.abs(a.rho() - b.rho()) / a.cfg.rho_l
+    assert d.max() > 1e-6
+    assert d.max() < 0.2
+
+
+def test_interp_bb_keeps_uniform_coexistence_at_rest(oracle_mod):
+    """A uniform liquid at the coexistence density around a cylinder is an exact fixed point of
+    the interpolated scheme as well (equal populations interpolate to themselves)."""
+    O = oracle_mod
+    cfg = _ibb_cfg(O)
+    mx = O.maxwell(0, cfg.Tr)
+    s = O.Sim(cfg, np.full((cfg.ny, cfg.nx), mx["rho_l"]))
+    s.step(300)
+    _, _, flag, _ = s.ext()
+    r = s.rho()[flag[2:-2] == 0]
+    assert np.abs(r - mx["rho_l"]).max() / mx["rho_l"] < 1e-12
+    ux, uy, _, _ = s.velocity_force()
+    assert np.abs(ux[flag[2:-2] == 0]).max() < 1e-12
