@@ -87,13 +87,13 @@ typedef struct lbm_params {
  *    phi = atan2(j - cy, i - cx)); mu_bottom below the domain; mu_top above it.
  *  Boundary scheme for populations whose source node is solid: LBM_BB_HALFWAY returns the
  *    population that left toward the wall (wall half a link out, exactly mass-conserving);
- *    LBM_BB_INTERP places the wall on the analytic surfaces (the circle of radius R, the planes
- *    y = -1/2 and y = ny - 1/2) at the link fraction Delta (at least 1/10), interpolates linearly (between the
+ *    LBM_BB_INTERP places the wall on the analytic surfaces (the circle of radius R + 1/2, the
+ *    planes y = -1/2 and y = ny - 1/2) at the link fraction Delta (at least 1/10; 1/2 for a link
+ *    that does not cross the circle within its length), interpolates linearly (between the
  *    node and its fluid neighbour behind it for Delta < 1/2, between the node's two opposite
  *    populations for Delta >= 1/2; the half-way value where no fluid neighbour lies behind) and
  *    adds the difference between the population that left and the one that returns to the
- *    node's rest population, so mass stays conserved. With LBM_BB_INTERP the measurement takes
- *    the circular wall surface at radius R. The first step after lbm_set_geometry pulls without
+ *    node's rest population, so mass stays conserved. The first step after lbm_set_geometry pulls without
  *    interpolation (the initial populations are the rest-state equilibrium w_q rho0). Not
  *    available in batches (lbm_batch_set_geometry returns LBM_ERR_ARG).
  *  Initial density: rho0 (host, (ny, nx), read at fluid nodes) if non-NULL, else the Eq. 16 drop

@@ -301,10 +301,12 @@ static double wall_mu(const orc_cfg *c, int i, int j) {
 }
 
 /* Fraction Delta in [0, 1] of the link from fluid node (i, j) along direction e_d (whose end
- * node is solid) at which the segment first enters the analytic solid: the closed disc of
- * radius R (or, for a cavity, the outside of that circle) and the half-planes y <= -1/2 and
- * y >= ny - 1/2 of the flat walls. Node classification uses the same closed disc, so the
- * circle is crossed within the link; the flat walls give Delta = 1/2. Delta is at least 1/10. */
+ * node is solid) at which the segment first enters the analytic solid: the disc of radius
+ * R + 1/2 (or, for a cavity, the outside of that circle), the wall surface the half-way scheme
+ * approximates and the measurement uses, and the half-planes y <= -1/2 and y >= ny - 1/2 of
+ * the flat walls (Delta = 1/2). A link that does not cross the wall surface within its length
+ * (a fluid node already inside the R + 1/2 circle, or a solid end node not yet beyond it) keeps
+ * the half-way value 1/2. Delta is at least 1/10. */
 static double link_fraction(const orc_cfg *c, int i, int j, int d) {
     double vx = CX[d], vy = CY[d];
     double best = 2.0;
@@ -318,14 +320,15 @@ static double link_fraction(const orc_cfg *c, int i, int j, int d) {
     if (c->has_circle) {
         double px = i - c->cx, py = j - c->cy;
         double a = vx * vx + vy * vy, b = px * vx + py * vy;
-        double cc = px * px + py * py - c->R * c->R;
+        double Rw = c->R + 0.5;
+        double cc = px * px + py * py - Rw * Rw;
         double disc = b * b - a * cc;
         if (disc >= 0) {
             double sq = sqrt(disc);
             /* entering the disc: first root; leaving the cavity: second root */
             double s = c->concave ? (-b + sq) / a : (-b - sq) / a;
-            /* a crossing behind the node (moving away from the disc) does not count; a node
-             * on the circle itself starts in the wall */
+            /* a crossing behind the node does not count; a node on the circle itself starts
+             * in the wall */
             if (s > -1e-12 && s <= 1) {
                 if (s < 0) s = 0;
                 if (s < best) best = s;
@@ -751,9 +754,9 @@ typedef struct {
     int side;
 } cand_t;
 
-/* Radius of the circular wall surface: half a link beyond the solid nodes with half-way
- * bounce-back, the analytic circle R itself with interpolated bounce-back. */
-static double wall_radius(const orc_cfg *c) { return c->interp_bb ? c->R : c->R + 0.5; }
+/* Radius of the circular wall surface: half a link beyond the solid nodes (both boundary
+ * schemes place the wall there). */
+static double wall_radius(const orc_cfg *c) { return c->R + 0.5; }
 
 /* Substrate distance of point (px, py), measured from the wall into the fluid: to the circle of
  * radius R + 1/2 (R with interpolated bounce-back) (the wall lies half a link between the last fluid and the first solid node;

@@ -439,9 +439,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     c->sub.concave = g->has_circle && g->concave ? 1 : 0;
     c->sub.cx = g->cx;
     c->sub.cy = g->cy;
-    // the wall surface: half a link beyond the solid nodes (half-way bounce-back) or the
-    // analytic circle itself (interpolated bounce-back)
-    c->sub.Rs = c->ibb ? g->R : g->R + 0.5;
+    // the wall surface: half a link beyond the solid nodes (both boundary schemes)
+    c->sub.Rs = g->R + 0.5;
     c->cur = 0;
     c->steps = 0;
     c->has_geometry = true;

@@ -110,8 +110,10 @@ __global__ void k_linkmask(const uint8_t* flags, uint8_t* mask, unsigned long lo
 }
 
 // Fraction of the link from fluid node (i, j) along e_d at which it first enters the analytic
-// solid: the closed disc of radius R (its outside for a cavity) or the half-planes y <= -1/2 and
-// y >= ny - 1/2, at least 1/10. Every operation is a separately rounded IEEE double operation.
+// solid: the disc of radius R + 1/2 (its outside for a cavity; the wall surface the half-way
+// scheme approximates) or the half-planes y <= -1/2 and y >= ny - 1/2; 1/2 where the link does
+// not cross the wall surface within its length; at least 1/10. Every operation is a separately
+// rounded IEEE double operation.
 __device__ double link_fraction(const GeomArgs& g, int i, int j, int d) {
     const double vx = qx(d), vy = qy(d);
     double best = 2.0;
@@ -126,8 +128,9 @@ __device__ double link_fraction(const GeomArgs& g, int i, int j, int d) {
         const double px = __dsub_rn((double)i, g.cx), py = __dsub_rn((double)j, g.cy);
         const double a = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
         const double b = __dadd_rn(__dmul_rn(px, vx), __dmul_rn(py, vy));
+        const double Rw = __dadd_rn(g.R, 0.5);
         const double cc = __dsub_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)),
-                                    __dmul_rn(g.R, g.R));
+                                    __dmul_rn(Rw, Rw));
         const double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(a, cc));
         if (disc >= 0) {
             const double sq = __dsqrt_rn(disc);

@@ -477,26 +477,29 @@ def test_equilibrium_present_vs_cap(oracle_mod):
 
 # ------------------------------------------- interpolated bounce-back (curved-wall variant)
 def _in_analytic_solid(x, y, ny, circle, concave):
+    """The analytic solid of the interpolated scheme: beyond the flat wall planes, inside the
+    disc of radius R + 1/2 (outside it for a cavity)."""
     if y <= -0.5 or y >= ny - 0.5:
         return True
     if circle is None:
         return False
     cx, cy, R = circle
-    inside = (x - cx) ** 2 + (y - cy) ** 2 <= R * R
-    return inside != concave
+    d2, w2 = (x - cx) ** 2 + (y - cy) ** 2, (R + 0.5) ** 2
+    return d2 >= w2 if concave else d2 <= w2      # the wall circle itself counts as solid
 
 
 def _brute_fraction(i, j, d, ny, circle, concave, n=4001):
-    """First s in [0, 1] at which the point (i, j) + s e_d lies in the analytic solid: a scan,
-    then bisection on the first bracket."""
+    """First s in [0, 1] at which the point (i, j) + s e_d crosses into the analytic solid: a
+    scan, then bisection on the first bracket; 1/2 when the segment starts inside it or never
+    enters it (no crossing within the link)."""
     ex = [0, 1, 0, -1, 0, 1, -1, -1, 1][d]
     ey = [0, 0, 1, 0, -1, 1, 1, -1, -1][d]
     s = np.linspace(0.0, 1.0, n)
     hit = [k for k in range(n) if _in_analytic_solid(i + s[k] * ex, j + s[k] * ey, ny, circle,
                                                      concave)]
+    if not hit or hit[0] == 0:
+        return 0.5
     k = hit[0]
-    if k == 0:
-        return 0.0
     lo, hi = s[k - 1], s[k]
     for _ in range(60):
         mid = 0.5 * (lo + hi)
