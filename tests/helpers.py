@@ -101,14 +101,14 @@ def exact_secant_angle(substrate, drop_c, r, d1, d2, side):
 MODEL_KEYS = ("eos", "Tr", "k2", "kappa", "tau", "s_e", "s_eps", "s_q")
 
 
-def gpu_lattice(lbm, cfg, precision=0, tile=(0, 0), rho0=None, stream=None):
+def gpu_lattice(lbm, cfg, precision=0, tile=(0, 0), rho0=None, stream=None, min_blocks=0):
     """CUDA-library lattice with exactly the numbers of an oracle Config (same coexistence
     densities, wall chemical potentials and initial drop)."""
     lat = lbm.Lattice(cfg.nx, cfg.ny, eos=cfg.eos, Tr=cfg.Tr, k2=cfg.k2, kappa=cfg.kappa,
                       tau=cfg.tau, s_e=cfg.s_e, s_eps=cfg.s_eps, s_q=cfg.s_q, gx=cfg.gx,
                       gy=cfg.gy, rho_g=cfg.rho_g, rho_l=cfg.rho_l, precision=precision,
                       collision=cfg.collision, tile=tile, stream=stream,
-                      g_rho_ref=cfg.g_rho_ref)
+                      g_rho_ref=cfg.g_rho_ref, min_blocks=min_blocks)
     lat.set_geometry(circle=(cfg.cx, cfg.cy, cfg.R) if cfg.has_circle else None,
                      mu_circle=cfg.mu_circle,
                      stripes=(cfg.stripe_arc, cfg.mu_stripe_b) if cfg.stripes else None,

@@ -83,14 +83,15 @@ def test_fp64_matches_oracle(lbm, oracle_mod, tile):
     assert np.abs(uy - ouy).max() < 1e-9
 
 
-@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 16), (32, 32)])
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 16), (32, 32), (32, 16, 5), (32, 8, 6),
+                                  (32, 16, 6)])
 def test_fp32_matches_oracle_ragged(lbm, oracle_mod, tile):
     """FP32 path on a domain that is not a multiple of any tile (ragged tails in x and y)."""
     O = oracle_mod
     cfg = _cfg(O, nx=77, ny=53, cx=38.5, R=20.0, drop_x=38.5, drop_y=20.5 + 14, drop_r=14)
     ref = O.Sim(cfg)
     ref.step(500)
-    lat = gpu_lattice(lbm, cfg, tile=tile)
+    lat = gpu_lattice(lbm, cfg, tile=tile[:2], min_blocks=tile[2] if len(tile) > 2 else 0)
     lat.step(500)
     err = np.abs(lat.rho() - ref.rho()).max() / cfg.rho_l
     assert err < 2e-5, err
