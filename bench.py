@@ -482,6 +482,74 @@ def run_sweep(args):
             "sweep": per}
 
 
+def run_gravity(args):
+    """Gravity independence of the microscopic angle (Sec. 4.3): the same drops (radius 20-120 on
+    a cylinder of radius 150, three wall potentials) without body force, sessile and pendent, each
+    setting one persistent batched run until the angles settle; per instance the device
+    measurement and the spherical-cap estimate of the same field."""
+    import torch
+    from paper_2202_06516_gb300 import lbm, workloads as W, contact_mechanics as CM
+    sw = W.gravity_sweep()
+    ws = sw["instances"]
+    m = ws[0].model
+    co = lbm.lbm_coexistence(m["eos"], m["Tr"])
+    neutral = m["k2"] * co["mu_sat"]
+    per, t_all, upd = {}, 0.0, 0
+    for gname, g in sw["g"].items():
+        b = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
+                      kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"],
+                      s_q=m["s_q"], gx=g[0], gy=g[1], tile_auto=True)
+        for i, w in enumerate(ws):
+            b.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+                           mu_bottom=neutral, mu_top=neutral, drop=w.drop)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        steps, conv, res = b.run(args.gravity_steps, check_every=1000, tol=0.0, angle_tol=0.05)
+        torch.cuda.synchronize()
+        t_all += time.perf_counter() - t
+        upd += sum(w.nx * w.ny * int(s) for w, s in zip(ws, steps))
+        ang = b.measure()
+        rows = []
+        for i, w in enumerate(ws):
+            l, r = ang[i]
+            row = {"target": float(w.name.rsplit("theta", 1)[1]), "r": w.drop[2],
+                   "steps": int(steps[i]), "converged": bool(conv[i]),
+                   "contact": l.status == 0 and r.status == 0}
+            if row["contact"]:
+                row["theta"] = 0.5 * (l.theta + r.theta)
+                _, pd = lbm.lbm_read_candidates(lbm.lbm_batch_instance(b.b, i), w.nx, w.ny)
+                try:
+                    row["cap"] = CM.cap_angle(pd[:, :2], pd[:, 2], w.circle)["theta"]
+                except ValueError:
+                    row["cap"] = None
+            rows.append(row)
+        b.close()
+        per[gname] = rows
+    summary = {}
+    for gname, rows in per.items():
+        for t in sorted({x["target"] for x in rows}):
+            sel = [x for x in rows if x["target"] == t and x["contact"]]
+            th = np.array([x["theta"] for x in sel])
+            cp = np.array([x["cap"] for x in sel if x.get("cap") is not None])
+            summary[f"{gname}-{t:g}"] = {
+                "drops_with_contact": len(sel),
+                "present_mean": float(th.mean()) if th.size else None,
+                "present_range": float(th.max() - th.min()) if th.size else None,
+                "cap_mean": float(cp.mean()) if cp.size else None,
+                "cap_range": float(cp.max() - cp.min()) if cp.size else None,
+                "by_radius": {f"{x['r']:g}": [round(x["theta"], 2),
+                                              None if x.get("cap") is None else round(x["cap"], 2)]
+                              for x in sel}}
+    return {"metric": "MLUPS", "value": upd / t_all / 1e6, "unit": "MLUPS", "n_gpus": 1,
+            "steps": args.gravity_steps, "warmup": 0, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"gravity-sweep-{len(ws)}-drops-x3",
+                       "g": {k: list(v) for k, v in sw["g"].items()},
+                       "timing": "host wall clock around the three synchronous batch runs"},
+            "gravity": summary}
+
+
 def run_boundary(args):
     """Staircase sensitivity of the equilibrium angle under the two curved-wall schemes: the same
     drop (r = 40) on cylinders whose radius (R, R + 1/2) and centre (offsets of 0 or 1/2 in x and
@@ -739,7 +807,8 @@ def main():
     ap.add_argument("--tile", type=lambda v: tuple(int(t) for t in v.split("x")), default=(0, 0),
                     help="step-kernel tile, e.g. 32x16 (default: the library's)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "warmstart", "surrogate",
-                                                    "hysteresis", "sweep", "boundary"])
+                                                    "hysteresis", "sweep", "boundary",
+                                                    "gravity"])
     ap.add_argument("--train-cases", type=int, default=1024)
     ap.add_argument("--eval-cases", type=int, default=64)
     ap.add_argument("--gen-steps", type=int, default=20000)
@@ -751,6 +820,7 @@ def main():
     ap.add_argument("--hyst-steps", type=int, default=200000)
     ap.add_argument("--sweep-steps", type=int, default=60000)
     ap.add_argument("--boundary-steps", type=int, default=30000)
+    ap.add_argument("--gravity-steps", type=int, default=60000)
     ap.add_argument("--sweep-tr", default="0.7",
                     help="sweep workload: comma-separated reduced temperatures")
     ap.add_argument("--sweep-detail", action="store_true",
@@ -804,6 +874,10 @@ def main():
     if args.workload == "boundary":
         if rank == 0:
             print(json.dumps(run_boundary(args)), flush=True)
+        return
+    if args.workload == "gravity":
+        if rank == 0:
+            print(json.dumps(run_gravity(args)), flush=True)
         return
     if dist:
         dist.barrier()

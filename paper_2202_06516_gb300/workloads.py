@@ -164,6 +164,25 @@ def curvature_sweep(targets=(70.0, 90.0, 110.0, 130.0, 150.0), radii=(150.0, 250
     return out
 
 
+def gravity_sweep(targets=(70.0, 100.0, 140.0), drops=(20.0, 40.0, 60.0, 80.0, 100.0, 120.0),
+                  R=150.0, G=1e-6) -> dict:
+    """Sessile and pendent drops of growing size on a cylinder (Sec. 4.3): for each wall potential
+    and drop radius, a drop started as a 90-degree cap on top of a cylinder of radius R centred on
+    the bottom boundary. Three body-force settings share the instances: none, toward the
+    cylinder (sessile) and away from it (pendent: the paper's drop beneath the substrate with
+    gravity reversed, turned upside down). Returns {"instances": [...], "g": {...}}."""
+    out = []
+    for t in targets:
+        for r in drops:
+            nx, ny = int(2 * R + 4 * r + 40), int(R + 4 * r + 40)
+            nx += nx % 2
+            cx = nx / 2.0
+            out.append(Workload(f"cyl{R:g}-r{r:g}-theta{t:g}", nx, ny, (cx, 0.0, R),
+                                cap_drop(cx, 0.0, R, r), mu_rel_circle=mu_rel_for_angle(t),
+                                steps=60000, measure_every=1000))
+    return {"instances": out, "g": {"none": (0.0, 0.0), "sessile": (0.0, -G), "pendent": (0.0, G)}}
+
+
 def flat_drop(nx=160, ny=80, r=20.0, theta_rel=0.0) -> Workload:
     """Drop on a flat bottom wall (no cylinder)."""
     return Workload(f"flat-{nx}x{ny}-drop{r:g}", nx, ny, None, (nx / 2.0, -0.5 + r, r, W_INIT),
