@@ -23,6 +23,19 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+@pytest.mark.parametrize("lang,std", [("c", "-std=c11"), ("c++", "-std=c++17")])
+def test_header_compiles_standalone(lang, std):
+    """include/lbm.h is a plain C header: it compiles on its own as C11 and as C++17."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    r = subprocess.run([cc, "-fsyntax-only", "-x", lang, std, "-Wall", "-Wextra", "-Werror",
+                        os.path.join(ROOT, "include", "lbm.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol():
     from paper_2202_06516_gb300 import _native
     lib = _native.load()
