@@ -326,8 +326,9 @@ def run_reference(args):
 
 def run_batched(args):
     """256-instance sweep (domains 128..768 x 128..512, R 20..200, r 15..90, target angle 30..150
-    degrees): all instances advance together in the persistent batched kernel; value = all
-    instances' node updates per second over args.steps steps (no early exit in the timed run),
+    degrees): all instances advance together in the batched kernel (grid mode and tile from the
+    autotuner); value = all instances' node updates per second over args.steps steps (no early
+    exit in the timed run),
     then a convergence run (residual < 1e-6 per 500 steps or 40k steps) reports steps and
     angles per instance."""
     import torch
@@ -357,8 +358,10 @@ def run_batched(args):
             "config": {"workload": f"batched-{args.instances}-instances", "total_nodes": nodes,
                        "fluid_nodes": fluid,
                        "timing": "host wall clock around the synchronous batch run",
-                       "autotune_us_per_step": {f"{r['tile'][0]}x{r['tile'][1]}/{r['min_blocks']}":
-                                                round(r["us_per_step"], 2) for r in tune}}}
+                       "autotune_us_per_step": {
+                           f"{r['tile'][0]}x{r['tile'][1]}/{r['min_blocks']}"
+                           f"{' persistent' if r['persistent'] else ' per-tile'}":
+                           round(r["us_per_step"], 2) for r in tune}}}
     peak, kind = _peaks()
     ach = BYTES_PER_FLUID_NODE * fluid * args.steps / dt / 1e9
     line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",

@@ -205,11 +205,13 @@ lbm_status lbm_read_candidates(lbm_ctx *ctx, int64_t *ids, double *pxyd, int64_t
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 
-/* One timed step-kernel variant: tile shape, register budget (CTAs per SM, 0 = none) and the
- * mean device time of one step over the trial, in microseconds. */
+/* One timed step-kernel variant: tile shape, register budget (CTAs per SM, 0 = none), the mean
+ * device time of one step over the trial in microseconds, and (batched kernel only) the grid
+ * mode: 0 = one CTA per tile, 1 = persistent CTAs looping over the tile table. */
 typedef struct lbm_tune_entry {
     int32_t tile_x, tile_y, min_blocks;
     double us_per_step;
+    int32_t persistent;
 } lbm_tune_entry;
 
 /* Step-kernel autotuner (no counterpart in the paper; it only picks among launch shapes that
@@ -250,15 +252,17 @@ lbm_status lbm_mass_noalloc(const float *rho, const uint8_t *flags, int32_t nx, 
 
 /* ---------------------------------------------------------------------------------------------
  * Batched sweeps: independent lattices of uneven size (drop radius, cylinder curvature and
- * wettability sweeps, Sec. 4.1-4.2) advanced together by one persistent kernel over a device
- * table of (instance, tile) pairs, replayed from a CUDA graph, with per-instance convergence.
+ * wettability sweeps, Sec. 4.1-4.2) advanced together by one kernel launch per step over a
+ * device table of (instance, tile) pairs (one CTA per tile, or persistent CTAs looping over the
+ * table), replayed from a CUDA graph, with per-instance convergence.
  * ------------------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch; /* opaque; owns n lattices, their stream and tile tables */
 
 /* Create n lattices of sizes nx[i] x ny[i] sharing the model parameters (model->nx, ny, tile_y,
  * min_blocks and stream are ignored; precision must be LBM_FP32; model->tile_x = LBM_TILE_AUTO
  * autotunes the batch kernel at the first lbm_batch_run, any other value starts with the
- * default 32x16 tiles). Every instance is an lbm_ctx on the batch's private stream. On failure
+ * default 32x16 tiles, one CTA per tile). Every instance is an lbm_ctx on the batch's private
+ * stream. On failure
  * *out is NULL and nothing is leaked. */
 lbm_status lbm_batch_create(const lbm_params *model, int32_t n, const int32_t *nx,
                             const int32_t *ny, lbm_batch **out);
@@ -277,8 +281,9 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int32_t check_every, d
                          double angle_tol, int64_t *steps_out, int32_t *converged_out,
                          double *residual_out);
 
-/* Autotuner of the batched kernel: times each compiled tile variant of the persistent kernel
- * (FP32 32x8, 32x16, 64x16, 32x32, each with its register budget) over trial_steps launches on
+/* Autotuner of the batched kernel: times each compiled tile variant (FP32 32x8, 32x16, 64x16,
+ * 32x32, each with its register budget) in both grid modes (one CTA per tile, then persistent;
+ * entries in that order, 2 per variant) over trial_steps launches on
  * the tile table of the instances that have geometry (those sharing the parity of the first), and
  * keeps the fastest for later lbm_batch_run calls. As in lbm_autotune the trial launches do not
  * advance any instance. entries / n_out as in lbm_autotune. LBM_ERR_STATE if no instance has

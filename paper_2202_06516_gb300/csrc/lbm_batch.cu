@@ -3,8 +3,12 @@
 //
 // Every instance is an ordinary lbm_ctx (its own planes, geometry and measurement scratch, all
 // on the batch's stream). A device tile table lists (instance, tile) pairs of the instances still
-// running; one persistent kernel, one CTA per resident slot, walks the table and advances each
-// tile one time step with the same device code as the single-lattice kernel. A CUDA graph holds
+// running; one kernel launch per time step walks the table and advances each tile one step with
+// the same device code as the single-lattice kernel. Its grid is either one CTA per tile of all
+// instances (CTAs past the current table length exit at once) or persistent (one CTA per
+// resident slot, looping over the table); the autotuner times both, and one CTA per tile is the
+// default (measured faster: the hardware scheduler interleaves CTAs in different stages of
+// their tiles, while a persistent CTA serialises its tiles' four barriers). A CUDA graph holds
 // `check_every` such launches. After each graph the FP64 residual sum |rho(t) - rho(t - check)| /
 // sum rho of every running instance is computed (one block per instance, fixed order), converged
 // instances leave the table, and the graph is replayed on the shorter table without recapture
@@ -38,7 +42,8 @@ struct lbm_batch {
     float* snap = nullptr;        // one density snapshot plane per instance
     std::vector<size_t> snap_off;
     int max_tiles = 0;
-    int grid = 0;
+    int grid = 0;                 // resident slots (persistent grid)
+    bool persistent = false;      // grid mode: resident slots, or one CTA per tile
     int variant = 0;              // index into the compiled tile variants
     int tx = 32, ty = 16;         // its tile shape
     bool autotune_pending = false;
@@ -253,9 +258,15 @@ lbm_status upload_tiles(lbm_batch* b, int p, int* ntiles, std::vector<int>* act)
 
 cudaError_t launch_batch_step(lbm_batch* b, int parity) {
     int i = 0;
+    int grid = b->grid;
+    if (!b->persistent) {  // one CTA per tile of every instance; CTAs past the table exit at once
+        long long all = 0;
+        for (const lbm_ctx* c : b->inst) all += tiles_of(b, c);
+        grid = (int)std::max<long long>(1, all);
+    }
 #define X(A, B, M)                                                                           \
     if (b->variant == i++) {                                                                 \
-        k_batch_step<A, B, M><<<b->grid, NTB, Layout<float, A, B>::bytes, b->stream>>>(      \
+        k_batch_step<A, B, M><<<grid, NTB, Layout<float, A, B>::bytes, b->stream>>>(         \
             b->model, (const BatchInst*)b->d_desc, b->d_tiles, b->d_ntiles, parity);         \
         return cudaGetLastError();                                                           \
     }
@@ -546,11 +557,15 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, lbm_tune_entry*
     cudaError_t err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     const int keep = b->variant;
+    const bool keep_persistent = b->persistent;
     int best = -1;
     double best_us = 0;
     lbm_status st = LBM_OK;
     std::vector<int> act;
-    for (int v = 0; v < num_variants() && err == cudaSuccess && st == LBM_OK; ++v) {
+    // trial k: tile variant k / 2, grid one CTA per tile (k even) or persistent (k odd)
+    for (int k2 = 0; k2 < 2 * num_variants() && err == cudaSuccess && st == LBM_OK; ++k2) {
+        const int v = k2 / 2;
+        b->persistent = (k2 & 1) != 0;
         err = configure_variant(b, v);
         if (err != cudaSuccess) break;
         int ntiles = 0;
@@ -569,17 +584,19 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, lbm_tune_entry*
         const double us = 1e3 * (double)ms / trial_steps;
         int vx = 0, vy = 0, vm = 0;
         variant_shape(v, &vx, &vy, &vm);
-        if (entries && v < max_entries) entries[v] = lbm_tune_entry{vx, vy, vm, us};
+        if (entries && k2 < max_entries)
+            entries[k2] = lbm_tune_entry{vx, vy, vm, us, b->persistent ? 1 : 0};
         if (best < 0 || us < best_us) {
-            best = v;
+            best = k2;
             best_us = us;
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     b->running = keep_running;
-    const cudaError_t ce = configure_variant(b, (err == cudaSuccess && st == LBM_OK && best >= 0)
-                                                    ? best : keep);
+    const bool ok = err == cudaSuccess && st == LBM_OK && best >= 0;
+    b->persistent = ok ? (best & 1) != 0 : keep_persistent;
+    const cudaError_t ce = configure_variant(b, ok ? best / 2 : keep);
     if (st != LBM_OK) return st;
     BCUDA(b, err);
     BCUDA(b, ce);
@@ -588,7 +605,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, lbm_tune_entry*
     b->graph = nullptr;
     b->graph_chunk = 0;
     b->graph_parity = -1;
-    if (n_out) *n_out = num_variants();
+    if (n_out) *n_out = 2 * num_variants();
     return LBM_OK;
 }
 

@@ -67,7 +67,7 @@ class lbm_info(C.Structure):
 
 class lbm_tune_entry(C.Structure):
     _fields_ = [("tile_x", C.c_int32), ("tile_y", C.c_int32), ("min_blocks", C.c_int32),
-                ("us_per_step", C.c_double)]
+                ("us_per_step", C.c_double), ("persistent", C.c_int32)]
 
 
 _sig = None
@@ -231,7 +231,8 @@ def _tune(fn, handle, trial_steps, check):
     n = C.c_int32()
     check(fn(handle, int(trial_steps), out, cap, C.byref(n)), handle)
     return [dict(tile=(out[i].tile_x, out[i].tile_y), min_blocks=out[i].min_blocks,
-                 us_per_step=out[i].us_per_step) for i in range(min(n.value, cap))]
+                 us_per_step=out[i].us_per_step, persistent=bool(out[i].persistent))
+            for i in range(min(n.value, cap))]
 
 
 def lbm_autotune(ctx, trial_steps: int = 20):

@@ -79,7 +79,9 @@ def test_batch_autotune_keeps_state(lbm, oracle_mod):
     b.run(200, check_every=100, tol=0.0)
     before = [b.rho(i) for i in range(len(cfgs))]
     res = b.autotune(5)
-    assert [r["tile"] for r in res] == [(32, 8), (32, 16), (64, 16), (32, 32)]
+    tiles = [(32, 8), (32, 16), (64, 16), (32, 32)]
+    assert [r["tile"] for r in res] == [t for t in tiles for _ in range(2)]
+    assert [r["persistent"] for r in res] == [False, True] * 4
     assert all(r["us_per_step"] > 0 for r in res)
     for i in range(len(cfgs)):
         assert np.array_equal(b.rho(i), before[i])
