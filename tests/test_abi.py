@@ -36,6 +36,43 @@ def test_header_compiles_standalone(lang, std):
     assert r.returncode == 0, r.stderr
 
 
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every public struct of include/lbm.h has, in the ctypes binding, the same size and the
+    same field offsets as the C compiler gives it (fields are appended over time; a mismatch
+    would silently shift every later field)."""
+    import shutil
+    import subprocess
+    from paper_2202_06516_gb300 import lbm
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    structs = [lbm.lbm_params, lbm.lbm_geometry, lbm.lbm_angle, lbm.lbm_info, lbm.lbm_tune_entry]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            n, f, v = line.split()
+            got[(n, f)] = int(v)
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "size")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
+
+
 def test_library_exports_every_declared_symbol():
     from paper_2202_06516_gb300 import _native
     lib = _native.load()
