@@ -191,6 +191,43 @@ def test_body_force_momentum(oracle_mod, g_rho_ref):
     assert np.allclose((f @ ey)[mid] / rho[mid], -2e-4 * scale, rtol=1e-10, atol=1e-14)
 
 
+@pytest.mark.parametrize("collision,tau", [(0, 1.0), (0, 0.8), (1, 0.9)])
+def test_channel_shear_mode_decays_at_the_lattice_viscosity(oracle_mod, collision, tau):
+    """The lowest shear mode of the channel, u_x = U sin(pi (y + 1/2) / ny) between the walls at
+    y = -1/2 and ny - 1/2, in a uniform liquid (no interface, so no force) decays as
+    exp(-nu (pi / ny)^2 t) with the lattice viscosity nu = (tau - 1/2) / 3 of the shear rate
+    s_v = 1/tau (Sec. 2.1). This pins the stress rows of the MRT moment basis (equal rates
+    reduce MRT to BGK for any invertible basis) and the half-way wall position."""
+    O = oracle_mod
+    m = _model()
+    m.update(tau=tau)
+    mx = O.maxwell(m["eos"], m["Tr"])
+    neutral = m["k2"] * mx["mu_sat"]
+    nx, ny, U = 8, 48, 1e-3
+    cfg = O.Config(nx=nx, ny=ny, **m, collision=collision, rho_g=mx["rho_g"], rho_l=mx["rho_l"],
+                   mu_bottom=neutral, mu_top=neutral, drop_x=0, drop_y=0, drop_r=1)
+    rho0 = np.full((ny, nx), mx["rho_l"])
+    s = O.Sim(cfg, rho0)
+    # equilibrium populations (Eq. 2) of the mode, as the initial state
+    mode = np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
+    ux = (U * mode)[:, None].repeat(nx, 1)
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    eu = ex[None, None, :] * ux[:, :, None]
+    f = w * rho0[:, :, None] * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (ux ** 2)[:, :, None])
+    s.set_f(f)
+    steps = 3000
+    s.step(steps)
+    s.step(1)   # the reported velocity is that of the state before the last step
+    vx, _, _, _ = s.velocity_force()
+    amp = (vx.mean(1) * mode).sum() / (mode * mode).sum()
+    nu = (tau - 0.5) / 3.0
+    want = np.exp(-nu * (np.pi / ny) ** 2 * steps)
+    assert amp / U == pytest.approx(want, rel=5e-3)
+    # and not the decay of another viscosity (a 10 % error in nu moves it by > 1 %)
+    assert abs(amp / U - np.exp(-1.1 * nu * (np.pi / ny) ** 2 * steps)) > 0.01 * want
+
+
 @pytest.mark.parametrize("tau", [1.0, 0.8])
 def test_mrt_reduces_to_bgk(oracle_mod, tau):
     """With every relaxation rate equal to 1/tau, MRT (Eq. 1) equals BGK (Eq. 3): pins the moment
