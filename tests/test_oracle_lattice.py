@@ -126,6 +126,44 @@ def test_wall_mu_assignment_concave(oracle_mod):
     assert seen == {"circle", "wall"}
 
 
+def test_wetting_layer_densities_eq14(oracle_mod):
+    """Eq. 14 on a random density field, by brute force: a first-layer node takes the D2Q9-weighted
+    mean of its fluid neighbours, a second-layer node the weighted mean of its first-layer
+    neighbours (the layers of a step are built from the density the step starts from)."""
+    O = oracle_mod
+    nx, ny = 40, 30
+    cfg = O.Config(nx=nx, ny=ny, Tr=0.7, has_circle=1, cx=20.5, cy=4.0, R=9.0, mu_circle=0.1,
+                   mu_bottom=0.0, mu_top=0.0, drop_x=20, drop_y=24, drop_r=3)
+    rng = np.random.default_rng(5)
+    rho0 = 1.0 + rng.random((ny, nx))
+    s = O.Sim(cfg, rho0)
+    _, _, flag, _ = s.ext()
+    s.step(1)
+    r_ext, _, _, _ = s.ext()
+    ext0 = np.zeros((ny + 4, nx))
+    ext0[2:-2] = rho0
+    ex = [1, 0, -1, 0, 1, -1, -1, 1]
+    ey = [0, 1, 0, -1, 1, 1, -1, -1]
+    wq = [1 / 9] * 4 + [1 / 36] * 4
+    want = ext0.copy()
+    for layer, src in ((1, 0), (2, 1)):
+        for r in range(ny + 4):
+            for i in range(nx):
+                if flag[r, i] != layer:
+                    continue
+                num = den = 0.0
+                for dx, dy, w in zip(ex, ey, wq):
+                    rr = r + dy
+                    if 0 <= rr < ny + 4 and flag[rr, (i + dx) % nx] == src:
+                        num += w * want[rr, (i + dx) % nx]
+                        den += w
+                assert den > 0
+                want[r, i] = num / den
+        sel = flag == layer
+        assert sel.sum() > 10
+        assert np.allclose(r_ext[sel], want[sel], rtol=1e-14, atol=0)
+
+
 # ------------------------------------------------------- stencils (Eq. 12, fourth-order FD)
 def test_chemical_potential_exact_on_quartics(oracle_mod):
     """mu = k^2 psi'(rho) - kappa lap(rho); the fourth-order Laplacian is exact on quartics, so
