@@ -303,6 +303,11 @@ class Lattice:
     def set_geometry(self, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
                      mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False,
                      boundary=LBM_BB_HALFWAY):
+        """lbm_set_geometry: circle = (cx, cy, R) in multiples of 1/2 or None (flat walls only);
+        mu_circle / mu_bottom / mu_top = wall chemical potentials; stripes = (arc length,
+        mu of the odd stripes) or None; drop = (x, y, r, W) of the Eq. 16 start, or rho0 =
+        (ny, nx) host densities; concave = the circle is a cavity; boundary = LBM_BB_HALFWAY or
+        LBM_BB_INTERP."""
         g = lbm_geometry()
         g.boundary = boundary
         if circle is not None:
@@ -436,6 +441,8 @@ class Batch:
     def set_geometry(self, i, *, circle=None, mu_circle=0.0, stripes=None, mu_bottom=0.0,
                      mu_top=0.0, drop=(0.0, 0.0, 1.0, 4.0), rho0=None, concave=False,
                      boundary=LBM_BB_HALFWAY):
+        """lbm_batch_set_geometry for instance i (arguments as Lattice.set_geometry; batches
+        accept LBM_BB_HALFWAY only)."""
         g = lbm_geometry()
         g.boundary = boundary
         if circle is not None:
