@@ -241,7 +241,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trial_steps, lbm_tune_entry *entri
  * array inside the library image of LBM_NOALLOC_MAX_ROWS x 8 doubles (256 KiB), which every GPU
  * that loads the library holds until the process exits; ny > LBM_NOALLOC_MAX_ROWS is rejected
  * with LBM_ERR_ARG. The first call on a device looks up the array's device address (a one-time
- * set-up per device); make that first call before any stream capture. Calls overwrite every
+ * set-up per device); make that first call before any stream capture. The address is kept for
+ * the life of the process: after a cudaDeviceReset of that device it is stale, so do not call
+ * this entry point on a device that was reset after its first call. Calls overwrite every
  * scratch entry they read, so no clearing is needed, but calls that overlap on the GPU share the
  * array and race. Errors: LBM_ERR_ARG (NULL pointer, nx or ny <= 0, pitch < nx, ny too large),
  * LBM_ERR_CUDA (no current device, set-up or launch failure); the message is available from
@@ -343,6 +345,14 @@ void lbm_surrogate_destroy(lbm_surrogate *s);
 lbm_status lbm_sg_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t K,
                        int32_t a_kmajor, int32_t b_kmajor, int32_t lda, int32_t ldb, float *C,
                        int32_t ldc, void *stream);
+
+/* Failure-path test hook (no counterpart in the paper): latch, from the host, the flag that a
+ * tensor-core GEMM sets when one of its bounded device waits runs out. The next
+ * lbm_surrogate_forward, lbm_surrogate_train_step or lbm_sg_gemm call then returns
+ * LBM_ERR_TIMEOUT (its message says a wait timed out) and clears the flag, exactly as after a
+ * real expiry. Nothing is launched and no GPU state changes. LBM_ERR_CUDA if the mapped host
+ * flag could not be allocated. */
+lbm_status lbm_sg_inject_timeout(void);
 
 /* Wait for the context's stream. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);

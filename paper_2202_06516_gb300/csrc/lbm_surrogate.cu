@@ -908,6 +908,17 @@ lbm_status lbm_sg_gemm(const void* A, const void* B, int32_t M, int32_t N, int32
     return LBM_OK;
 }
 
+// Host-side fault injection: latch the timeout flag exactly as a device wait that ran out
+// would, so that callers can exercise their LBM_ERR_TIMEOUT path without stalling a GPU.
+lbm_status lbm_sg_inject_timeout(void) {
+    TcFlag& f = tc_flag();
+    if (!f.host)
+        return sfail(nullptr, LBM_ERR_CUDA,
+                     "lbm_sg_inject_timeout: the mapped timeout flag could not be allocated");
+    *f.host = 1;
+    return LBM_OK;
+}
+
 void lbm_surrogate_destroy(lbm_surrogate* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);

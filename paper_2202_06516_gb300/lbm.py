@@ -497,9 +497,10 @@ def _sg_sig():
     L.lbm_surrogate_last_error.restype = C.c_char_p
     L.lbm_sg_gemm.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                               C.c_int32, C.c_int32, vp, C.c_int32, vp]
+    L.lbm_sg_inject_timeout.argtypes = []
     for n in ("lbm_surrogate_create", "lbm_surrogate_set_weights", "lbm_surrogate_get_weights",
               "lbm_surrogate_forward", "lbm_surrogate_train_step", "lbm_surrogate_phi",
-              "lbm_sg_gemm"):
+              "lbm_sg_gemm", "lbm_sg_inject_timeout"):
         getattr(L, n).restype = C.c_int
     L._sg_ready = True
     return L
@@ -514,6 +515,12 @@ def lbm_sg_gemm(A_ptr, B_ptr, M, N, K, a_kmajor, b_kmajor, lda, ldb, C_ptr, ldc,
     """C (FP32, device) = A * B with BF16 device operands; see include/lbm.h."""
     _scheck(_sg_sig().lbm_sg_gemm(A_ptr, B_ptr, M, N, K, int(a_kmajor), int(b_kmajor), lda, ldb,
                                   C_ptr, ldc, stream))
+
+
+def lbm_sg_inject_timeout():
+    """Latch the tensor-core timeout flag from the host (failure-path test hook; see
+    include/lbm.h): the next surrogate or GEMM call returns LBM_ERR_TIMEOUT."""
+    _scheck(_sg_sig().lbm_sg_inject_timeout())
 
 
 class Surrogate:

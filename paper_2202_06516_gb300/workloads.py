@@ -73,6 +73,21 @@ def plain_small() -> Workload:
                     tangent_drop(100, 0, 40, 25), steps=3000)
 
 
+# Carnahan-Starling variant of the 200 x 120 workload (a = 1, b = 4, Tr = 0.7, density ratio 38.5).
+# k^2 = 0.05 and kappa-hat = 0.05 give a 10-90 % interface width close to the PR model's; the
+# Eq. 16 start needs W = 4 here (W = 2 diverges within the 3000 steps, as with PR).
+MODEL_CS = dict(eos=1, Tr=0.7, k2=0.05, kappa=0.05, tau=1.0, s_e=1.64, s_eps=1.54, s_q=1.9)
+W_INIT_CS = 4.0
+
+
+def plain_small_cs() -> Workload:
+    """The 200 x 120 cylinder workload with the Carnahan-Starling EOS and the MRT collision:
+    R = 40 centred on the bottom boundary, drop r = 25 tangent to it, neutral walls, 3000 steps
+    then one measurement."""
+    return Workload("plain-200x120-cyl40-drop25-cs", 200, 120, (100.0, 0.0, 40.0),
+                    tangent_drop(100, 0, 40, 25, W=W_INIT_CS), steps=3000, model=dict(MODEL_CS))
+
+
 def mu_rel_for_angle(theta_deg: float, slope_per_deg: float = 1.5e-3) -> float:
     """Wall chemical potential offset for a target angle from a linear theta(mu_w) calibration
     (Sec. 4.1 reports theta linear in mu_w): mu_rel = slope * (theta - 90). The slope, 1.5e-3

@@ -422,6 +422,33 @@ def test_carnahan_starling_bgk_matches_oracle(lbm, oracle_mod):
         assert err < tol, (prec, err)
 
 
+def test_carnahan_starling_mrt_200x120_3000_steps(lbm, oracle_mod):
+    """The 200 x 120 cylinder workload with the Carnahan-Starling EOS (Tr = 0.7) and the MRT
+    collision of Eq. 1, 3000 steps: FP32 within 1e-4 of rho_l and FP64 within 1e-9 of rho_l of
+    the oracle, mass conserved, both contact angles within 0.5 degrees of the oracle's."""
+    O = oracle_mod
+    cfg = oracle_config(O, W.plain_small_cs())[0]
+    assert cfg.eos == 1 and cfg.collision == 0
+    ref = O.Sim(cfg)
+    ref.step(3000)
+    oref = ref.rho()
+    assert np.isfinite(oref).all()
+    ol, orr, _ = ref.measure()
+    assert ol.status == 0 and orr.status == 0
+    for prec, tol in ((0, 1e-4), (1, 1e-9)):
+        lat = gpu_lattice(lbm, cfg, precision=prec)
+        m0 = lat.mass()["mass"]
+        lat.step(3000)
+        err = np.abs(lat.rho() - oref).max() / cfg.rho_l
+        print(f"precision {prec}: max |drho|/rho_l = {err:.3e}")
+        assert err <= tol, (prec, err)
+        assert abs(lat.mass()["mass"] - m0) / m0 < (1e-5 if prec == 0 else 1e-12)
+        gl, gr = lat.measure()
+        assert gl.status == 0 and gr.status == 0
+        assert abs(gl.theta - ol.theta) <= 0.5 and abs(gr.theta - orr.theta) <= 0.5
+        lat.close()
+
+
 def test_striped_wetting_and_pendent_gravity(lbm, oracle_mod):
     """Heterogeneous (striped) circle wetting with a body force pulling the drop away from the
     cylinder (pendent arrangement), FP32 vs oracle, 1500 steps."""

@@ -331,6 +331,31 @@ def test_mass_conservation(oracle_mod):
     assert np.isfinite(s.rho()).all()
 
 
+def test_carnahan_starling_workload(oracle_mod):
+    """The Carnahan-Starling 200 x 120 workload (MRT, Tr = 0.7): mass conserved to round-off over
+    its 3000 steps, the mirror-symmetric set-up gives mirror-equal left and right angles, and the
+    bulk densities relax toward the CS Maxwell pair (liquid within 3 %, gas within a factor 2:
+    the forcing's discrete pressure term shifts the gas, as for PR)."""
+    O = oracle_mod
+    cfg, mx, _ = oracle_config(O, W.plain_small_cs())
+    assert cfg.eos == O.EOS_CS
+    s = O.Sim(cfg)
+    m0 = s.mass()
+    s.step(3000)
+    rho = s.rho()
+    assert np.isfinite(rho).all()
+    assert abs(s.mass() - m0) / m0 < 1e-11
+    left, right, cen = s.measure()
+    assert left.status == 0 and right.status == 0
+    assert abs(left.theta - right.theta) < 1e-9
+    assert cen[0] == pytest.approx(cfg.cx, abs=1e-9)
+    assert 60.0 < left.theta < 120.0
+    liquid = rho[int(cfg.drop_y), int(cfg.drop_x)]
+    gas = rho[cfg.ny - 10, 5]
+    assert liquid == pytest.approx(mx["rho_l"], rel=0.03)
+    assert mx["rho_g"] / 2 < gas < 2 * mx["rho_g"]
+
+
 @pytest.mark.parametrize("phase", ["liquid", "gas"])
 def test_uniform_coexistence_state_is_fixed_point(oracle_mod, phase):
     """A uniform fluid at a coexistence density next to neutral walls (mu_w = k^2 psi'(rho_sat))
