@@ -15,7 +15,8 @@ forward order its weight laid out [c_out][ky][kx][c_in] followed by its bias [c_
 head weight [base] and bias [1].
 
 Parity unpinned by the paper (the paper has no network); pinned instead by finite differences
-(tests/test_oracle_surrogate.py).
+(tests/test_oracle_surrogate.py), in the exact FP64 mode and, to BF16 precision, in the mode that
+rounds the pre-activation gradients.
 """
 from __future__ import annotations
 
@@ -61,15 +62,42 @@ def _bf16_store(t: torch.Tensor) -> torch.Tensor:
     return t + (t.to(torch.bfloat16).to(t.dtype) - t).detach()
 
 
+class _BF16GradStore(torch.autograd.Function):
+    """Identity in the forward pass; in the backward pass the gradient that arrives is rounded to
+    BF16 (round to nearest even), as when a BF16-storage network writes the gradient with respect
+    to a convolution's pre-activation once and every consumer (the weight gradient, the bias
+    gradient and the data gradient of that convolution) reads the rounded copy."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(g.dtype)
+
+
 def forward(params: torch.Tensor, x_nhwc: torch.Tensor, base: int,
-            bf16_activations: bool = False) -> torch.Tensor:
+            bf16_activations: bool = False, bf16_gradients: bool = False,
+            record: list | None = None) -> torch.Tensor:
     """phi (B, H, W) for inputs (B, H, W, 8). bf16_activations: round every stored activation
     (convolution outputs and pooled maps) to BF16, the storage precision of the method's
-    BF16-in / FP32-accumulate network; arithmetic stays FP64."""
+    BF16-in / FP32-accumulate network. bf16_gradients: round the gradient with respect to every
+    convolution's pre-activation (the output gradient times the leaky-ReLU slope) to BF16 before
+    it reaches that convolution's weights, bias and input, the other tensor such a network
+    stores in BF16. Arithmetic stays FP64 in both modes. record: if a list, every convolution's
+    pre-activation (before the leaky ReLU) is appended to it, in forward order."""
     layers, hw, hb = unpack(params, base)
     x = x_nhwc.permute(0, 3, 1, 2)
     st = _bf16_store if bf16_activations else (lambda t: t)
-    conv = lambda t, k: st(F.leaky_relu(F.conv2d(t, layers[k][0], layers[k][1], padding=1), 0.1))
+    gst = _BF16GradStore.apply if bf16_gradients else (lambda t: t)
+
+    def conv(t, k):
+        z = F.conv2d(t, layers[k][0], layers[k][1], padding=1)
+        if record is not None:
+            record.append(z.detach())
+        return st(F.leaky_relu(gst(z), 0.1))
+
     pool = lambda t: st(F.avg_pool2d(t, 2))
     s1 = conv(conv(x, 0), 1)
     s2 = conv(conv(pool(s1), 2), 3)
@@ -86,20 +114,20 @@ def forward(params: torch.Tensor, x_nhwc: torch.Tensor, base: int,
     return torch.sigmoid(z)
 
 
-def loss_fn(params, x, target, mask, base, bf16_activations=False):
-    phi = forward(params, x, base, bf16_activations)
+def loss_fn(params, x, target, mask, base, bf16_activations=False, bf16_gradients=False):
+    phi = forward(params, x, base, bf16_activations, bf16_gradients)
     m = mask.to(phi.dtype)
     return ((phi - target) ** 2 * m).sum() / m.sum(), phi
 
 
 def loss_and_grad(params: np.ndarray, x: np.ndarray, target: np.ndarray, mask: np.ndarray,
-                  base: int, bf16_activations: bool = False):
+                  base: int, bf16_activations: bool = False, bf16_gradients: bool = False):
     """Masked mean squared error on phi and its gradient (FP64, numpy in and out)."""
     p = torch.tensor(params, dtype=torch.float64, requires_grad=True)
     xt = torch.tensor(x, dtype=torch.float64)
     tt = torch.tensor(target, dtype=torch.float64)
     mt = torch.tensor(mask)
-    loss, phi = loss_fn(p, xt, tt, mt, base, bf16_activations)
+    loss, phi = loss_fn(p, xt, tt, mt, base, bf16_activations, bf16_gradients)
     loss.backward()
     return float(loss.item()), p.grad.numpy().copy(), phi.detach().numpy()
 

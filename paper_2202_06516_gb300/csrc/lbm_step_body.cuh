@@ -471,7 +471,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, const T rho_mid,
     const int any = stage_load<T, TX, TY, NT>(a, s_rho, s_flag, x0, y0);
     const int mixed = __syncthreads_or(any & 1);
     // a tile without fluid nodes (inside the disc or the wall rows) has nothing to write
-    if (!__syncthreads_or(any & 2)) return;
+    // (an all-fluid staged region certainly holds fluid nodes: one barrier less for those)
+    if (mixed && !__syncthreads_or(any & 2)) return;
     if (mixed)
         step_body<T, TX, TY, NT, MACRO, true, PP, IBB>(a, rho_mid, s_rho, s_mu, s_g, s_flag, x0,
                                                        y0);

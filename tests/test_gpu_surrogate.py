@@ -96,11 +96,14 @@ def _bf16(a):
     return torch.tensor(a).to(torch.bfloat16).double().numpy()
 
 
-@pytest.mark.parametrize("base,H", [(8, 32), (8, 48), (16, 64), (32, 64)])
-def test_forward_loss_gradients_match_oracle(env, base, H):
+def _gpu_and_oracle(env, x, t, m, p, base, H):
+    """One GPU training step without update (gradients only) and the oracle on the same BF16
+    inputs and weights the GPU used (convolution weights rounded to BF16; biases and the head
+    stay FP32, as in the GPU epilogue and head), in three modes: FP64 throughout, BF16
+    activations, and BF16 activations plus BF16 pre-activation gradients (the two tensors the
+    GPU stores in BF16)."""
     torch, lbm = env
     from oracle import surrogate as S
-    x, t, m, p = _case(base=base, H=H, Wd=H)
     s = lbm.Surrogate(H, H, base=base, max_batch=2)
     assert s.n == p.size
     s.set_weights(p)
@@ -108,45 +111,109 @@ def test_forward_loss_gradients_match_oracle(env, base, H):
     td = torch.tensor(t).cuda()
     md = torch.tensor(m).cuda()
     loss = s.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 2, 0.0)
-    g = s.weights(grads=True).astype(np.float64)
-    phi = s.phi(2)
-    # oracle on the BF16-rounded inputs and weights the GPU used
+    gpu = dict(loss=loss, g=s.weights(grads=True).astype(np.float64), phi=s.phi(2))
+    s.close()
     pw = _bf16(p)
     convs, n = S.layer_specs(base)
     o = 0
-    for ci, co, _ in convs:          # biases stay FP32 in the GPU epilogue
+    for ci, co, _ in convs:
         o += co * 9 * ci
         pw[o:o + co] = p[o:o + co]
         o += co
-    pw[o:] = p[o:]                   # head is FP32 on the GPU
+    pw[o:] = p[o:]
     xb, tt, mb = _bf16(x), t.astype(np.float64), m.astype(bool)
-    lref, gref, phiref = S.loss_and_grad(pw, xb, tt, mb, base)
-    lbf, gbf, phibf = S.loss_and_grad(pw, xb, tt, mb, base, bf16_activations=True)
-    cosine = lambda a, b_: a @ b_ / (np.linalg.norm(a) * np.linalg.norm(b_) + 1e-30)
-    # against the FP64 network: within what BF16 storage of activations and gradients allows
-    assert np.abs(phi - phiref).max() < 2e-2
-    assert loss == pytest.approx(lref, rel=3e-2)
-    # BF16 storage of activations and gradients: the relative gradient error grows with the
-    # channel count (measured 0.12 at base 32 with either tensor-core GEMM)
-    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < (0.1 if base < 32 else 0.2)
-    assert cosine(g, gref) > 0.98
-    # against the oracle that stores activations in BF16 as the method does: every layer's
-    # weight gradient points the same way (the rest is BF16 storage of the gradients)
-    assert np.abs(phi - phibf).max() < 5e-3
-    # the remaining difference is BF16 storage of the activation gradients (the oracle keeps them
-    # in FP64); it grows with the channel count (base 32: cosine 0.991 with either GEMM kernel)
-    wide = base >= 32
-    assert cosine(g, gbf) > (0.985 if wide else 0.995)
-    o = 0
-    for k, (ci, co, _) in enumerate(convs):
-        sl = slice(o, o + co * 9 * ci)
-        assert cosine(g[sl], gbf[sl]) > (0.95 if wide else 0.975), k
-        bias = slice(o + co * 9 * ci, o + co * 9 * ci + co)
-        assert cosine(g[bias], gbf[bias]) > (0.9 if wide else 0.95), k
+    ref = {}
+    for mode, flags in (("fp64", (False, False)), ("act", (True, False)), ("full", (True, True))):
+        l, g, phi = S.loss_and_grad(pw, xb, tt, mb, base, *flags)
+        ref[mode] = dict(loss=l, g=g, phi=phi)
+    return gpu, ref, pw, xb
+
+
+def _layers(base):
+    """(weight slice, bias slice) of every convolution and the head slice."""
+    from oracle import surrogate as S
+    convs, _ = S.layer_specs(base)
+    out, o = [], 0
+    for ci, co, _ in convs:
+        out.append((slice(o, o + co * 9 * ci), slice(o + co * 9 * ci, o + co * 9 * ci + co)))
         o += co * 9 * ci + co
-    head = slice(o, o + base + 1)
-    assert cosine(g[head], gbf[head]) > 0.999
-    s.close()
+    return out, slice(o, o + base + 1)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _cos(a, b):
+    return (a @ b) / (np.linalg.norm(a) * np.linalg.norm(b))
+
+
+CASES = [(8, 32), (8, 48), (16, 64), (32, 64)]  # base, resolution (48: not a power of two)
+
+
+@pytest.mark.parametrize("regime", ["positive", "negative"])
+@pytest.mark.parametrize("base,H", CASES)
+def test_gradients_match_bf16_oracle_per_layer(env, base, H, regime):
+    """Every layer's weight and bias gradient within 1.5e-2 (relative, per layer) of the oracle
+    that stores activations and pre-activation gradients in BF16 as the GPU does, with weights
+    chosen so that every pre-activation keeps one sign with a wide margin (positive: weights
+    x 0.1, biases +1; negative: weights x 0.25, biases -1; margin checked in the oracle). Away
+    from the leaky-ReLU kink the only differences left are FP32 against FP64 accumulation and
+    the BF16 rounding decisions they move (measured worst layer: 1.2e-2); the forward pass then
+    agrees to ~1e-7 and the head gradient to 1e-4. The oracle without the gradient rounding is
+    farther from the GPU, so that mode is what the GPU computes."""
+    torch, _ = env
+    from oracle import surrogate as S
+    x, t, m, p = _case(base=base, H=H, Wd=H)
+    scale, bias = (0.1, 1.0) if regime == "positive" else (0.25, -1.0)
+    p = p.copy()
+    layers, head = _layers(base)
+    for sw, sb in layers:
+        p[sw] *= scale
+        p[sb] = bias
+    gpu, ref, pw, xb = _gpu_and_oracle(env, x, t, m, p, base, H)
+    rec = []
+    S.forward(torch.tensor(pw), torch.tensor(xb), base, bf16_activations=True, record=rec)
+    margin = min(float(z.abs().min()) for z in rec)
+    assert margin > 0.3 and all(((z > 0).all() if bias > 0 else (z < 0).all()) for z in rec)
+    full = ref["full"]
+    assert np.abs(gpu["phi"] - full["phi"]).max() < 5e-4
+    assert gpu["loss"] == pytest.approx(full["loss"], rel=1e-5)
+    assert _rel(gpu["g"][head], full["g"][head]) < 1e-3
+    errs = []
+    for k, (sw, sb) in enumerate(layers):
+        ew, eb = _rel(gpu["g"][sw], full["g"][sw]), _rel(gpu["g"][sb], full["g"][sb])
+        errs.append(max(ew, eb))
+        assert ew < 1.5e-2 and eb < 1.5e-2, (k, ew, eb)
+    act_only = [max(_rel(gpu["g"][sw], ref["act"]["g"][sw]), _rel(gpu["g"][sb], ref["act"]["g"][sb]))
+                for sw, sb in layers]
+    assert sum(errs) < sum(act_only)
+    print(f"{regime} base {base} H {H}: worst layer {max(errs):.2e} (activation-only oracle "
+          f"{max(act_only):.2e})")
+
+
+@pytest.mark.parametrize("base,H", CASES)
+def test_forward_loss_gradients_match_oracle_random_init(env, base, H):
+    """Seeded initial weights (pre-activations of both signs). Forward and loss within BF16
+    storage of the oracle; gradients: the leaky-ReLU slope switches between 1 and 0.1 at zero,
+    and pre-activations within a BF16 rounding step of zero flip with any FP32-level change of
+    the inputs (the oracle's own per-layer gradients move by 3-12 % when its weights move by a
+    relative 6e-8, see the oracle tests), so here the per-layer check is on direction: cosine > 0.99
+    (0.96 at base 32) against the BF16 oracle, > 0.999 (0.99) for the whole gradient."""
+    x, t, m, p = _case(base=base, H=H, Wd=H)
+    gpu, ref, _, _ = _gpu_and_oracle(env, x, t, m, p, base, H)
+    wide = base >= 32
+    assert np.abs(gpu["phi"] - ref["fp64"]["phi"]).max() < 2e-2
+    assert gpu["loss"] == pytest.approx(ref["fp64"]["loss"], rel=3e-2)
+    full = ref["full"]
+    assert np.abs(gpu["phi"] - full["phi"]).max() < 1e-3
+    assert gpu["loss"] == pytest.approx(full["loss"], rel=1e-4)
+    assert _cos(gpu["g"], full["g"]) > (0.99 if wide else 0.999)
+    layers, head = _layers(base)
+    for k, (sw, sb) in enumerate(layers):
+        assert _cos(gpu["g"][sw], full["g"][sw]) > (0.96 if wide else 0.99), k
+        assert _cos(gpu["g"][sb], full["g"][sb]) > (0.96 if wide else 0.99), k
+    assert _rel(gpu["g"][head], full["g"][head]) < 2e-2
 
 
 def test_training_reduces_loss(env):
