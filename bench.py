@@ -12,7 +12,10 @@ flush is inserted between steps. ``e2e`` repeats the run through the C ABI from 
 geometry and a host initial density in, angles and the final density out.
 
 N > 1 (torchrun): every rank runs an independent instance (seed = rank) with no data-path
-collective; value = all ranks' node updates / the slowest rank's time (weak scaling).
+collective; value = all ranks' node updates / the slowest rank's time (weak scaling). The
+batched, sweep and warm-start workloads instead split their independent instances over the
+ranks in contiguous ranges (paper_2202_06516_gb300/shard.py) and gather the per-instance results
+on rank 0 (strong scaling of a fixed instance set).
 
 --impl reference: the FP64 CPU oracle on the host cores on the same workload, for a bounded
 number of steps.
@@ -324,109 +327,149 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
-def run_batched(args):
+def run_batched(args, rank=0, world=1, dist=None):
     """256-instance sweep (domains 128..768 x 128..512, R 20..200, r 15..90, target angle 30..150
     degrees): all instances advance together in the batched kernel (grid mode and tile from the
     autotuner); value = all instances' node updates per second over args.steps steps (no early
-    exit in the timed run),
-    then a convergence run (residual < 1e-6 per 500 steps or 40k steps) reports steps and
-    angles per instance."""
+    exit in the timed run), then (--converge) a convergence run (residual < 1e-6 per 500 steps
+    or the angle rule, at most 40k steps) reports steps and angles per instance.
+    Under torchrun the instances are split over the ranks in contiguous ranges balanced by
+    lattice nodes, each rank runs its own batch, and the per-instance results are gathered on
+    rank 0; the timed region is the slowest rank's."""
     import torch
-    from paper_2202_06516_gb300 import lbm, workloads as W
-    ws = W.batched(args.instances, seed=0)
-    m = ws[0].model
+    from paper_2202_06516_gb300 import lbm, shard, workloads as W
+    ws_all = W.batched(args.instances, seed=0)
+    lo, hi = shard.partition([w.nx * w.ny for w in ws_all], world, rank)
+    ws = ws_all[lo:hi]
+    m = ws_all[0].model
     co = lbm.lbm_coexistence(m["eos"], m["Tr"])
     neutral = m["k2"] * co["mu_sat"]
-    b = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
-                  kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"])
-    for i, w in enumerate(ws):
-        b.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
-                       mu_bottom=neutral, mu_top=neutral, drop=w.drop)
-    nodes = sum(w.nx * w.ny for w in ws)
-    fluid = sum(lbm.lbm_get_info(lbm.lbm_batch_instance(b.b, i)).n_fluid for i in range(len(ws)))
-    tune = b.autotune(20)
-    b.run(max(4, args.warmup // 2 * 2), check_every=max(2, args.warmup // 2 * 2), tol=0.0)
+
+    def make():
+        bb = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
+                       kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"],
+                       s_q=m["s_q"])
+        for i, w in enumerate(ws):
+            bb.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+                            mu_bottom=neutral, mu_top=neutral, drop=w.drop)
+        return bb
+
+    b = make() if ws else None
+    fluid_local = sum(lbm.lbm_get_info(lbm.lbm_batch_instance(b.b, i)).n_fluid
+                      for i in range(len(ws))) if ws else 0
+    tune = b.autotune(20) if ws else []
+    if ws:
+        b.run(max(4, args.warmup // 2 * 2), check_every=max(2, args.warmup // 2 * 2), tol=0.0)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t = time.perf_counter()
-    steps, conv, res = b.run(args.steps, check_every=500, tol=0.0)
+    if ws:
+        b.run(args.steps, check_every=500, tol=0.0)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t
+    dt_local = time.perf_counter() - t
+    dt = shard.max_over_ranks(dt_local, dist)
+    fluid = sum(shard.gather([fluid_local], dist) or [fluid_local]) if dist else fluid_local
+    nodes = sum(w.nx * w.ny for w in ws_all)
     line = {"metric": "MLUPS", "value": nodes * args.steps / dt / 1e6, "unit": "MLUPS",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched-{args.instances}-instances", "total_nodes": nodes,
                        "fluid_nodes": fluid,
-                       "timing": "host wall clock around the synchronous batch run",
+                       "parallelism": f"instances split over {world} rank(s), contiguous ranges "
+                                      "balanced by nodes, results gathered on rank 0",
+                       "timing": "host wall clock around the synchronous batch run, slowest rank",
                        "autotune_us_per_step": {
                            f"{r['tile'][0]}x{r['tile'][1]}/{r['min_blocks']}"
                            f"{' persistent' if r['persistent'] else ' per-tile'}":
                            round(r["us_per_step"], 2) for r in tune}}}
     peak, kind = _peaks()
     ach = BYTES_PER_FLUID_NODE * fluid * args.steps / dt / 1e9
-    line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                        "frac": ach / peak, "traffic": None, "peak_kind": kind,
+    line["roofline"] = {"bound": "hbm", "achieved": ach / world, "peak": peak, "unit": "GB/s",
+                        "frac": ach / world / peak, "traffic": None, "peak_kind": kind,
                         "kernel": "k_batch_step (autotuned tile)",
-                        "note": "80 B per fluid node over host wall time, residual checks "
-                                "every 500 steps included"}
+                        "note": "80 B per fluid node over host wall time per GPU, residual "
+                                "checks every 500 steps included"}
+    if b is not None:
+        b.close()
     if args.converge:
-        b2 = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
-                       kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"],
-                       s_q=m["s_q"])
-        for i, w in enumerate(ws):
-            b2.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
-                            mu_bottom=neutral, mu_top=neutral, drop=w.drop)
+        rows = []
         t = time.perf_counter()
-        steps, conv, res = b2.run(40000, check_every=500, tol=1e-6, angle_tol=0.05)
-        dt2 = time.perf_counter() - t
-        ang = b2.measure()
-        line["converge"] = {"seconds": dt2, "converged": int(conv.sum()),
-                            "steps_mean": float(steps.mean()), "steps_max": int(steps.max()),
-                            "angles_ok": int(sum(a[0].status == 0 and a[1].status == 0
-                                                 for a in ang))}
-        b2.close()
-    b.close()
+        if ws:
+            b2 = make()
+            steps, conv, res = b2.run(40000, check_every=500, tol=1e-6, angle_tol=0.05)
+            ang = b2.measure()
+            rows = [(lo + i, int(steps[i]), bool(conv[i]),
+                     ang[i][0].status == 0 and ang[i][1].status == 0,
+                     [ang[i][0].theta, ang[i][1].theta]) for i in range(len(ws))]
+            b2.close()
+        dt2 = shard.max_over_ranks(time.perf_counter() - t, dist)
+        rows = shard.gather(rows, dist)
+        if rows is not None:
+            assert [r[0] for r in rows] == list(range(len(ws_all)))
+            line["converge"] = {"seconds": dt2, "converged": sum(r[2] for r in rows),
+                                "steps_mean": float(np.mean([r[1] for r in rows])),
+                                "steps_max": max(r[1] for r in rows),
+                                "angles_ok": sum(r[3] for r in rows)}
     return line
 
 
-def _sweep_one(args, Tr):
-    """One temperature of the curvature sweep: returns (node updates, seconds, summary)."""
+def _sweep_one(args, Tr, rank=0, world=1, dist=None):
+    """One temperature of the curvature sweep: returns (node updates, seconds, summary); None
+    on ranks other than 0 under torchrun (instances split over the ranks, rows gathered)."""
     import torch
-    from paper_2202_06516_gb300 import lbm, workloads as W, contact_mechanics as CM
-    ws = W.curvature_sweep()
-    m = dict(ws[0].model, Tr=Tr)
+    from paper_2202_06516_gb300 import lbm, shard, workloads as W, contact_mechanics as CM
+    ws_all = W.curvature_sweep()
+    lo, hi = shard.partition([w.nx * w.ny for w in ws_all], world, rank)
+    ws = ws_all[lo:hi]
+    m = dict(ws_all[0].model, Tr=Tr)
     co = lbm.lbm_coexistence(m["eos"], m["Tr"])
     neutral = m["k2"] * co["mu_sat"]
-    b = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
-                  kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"], s_q=m["s_q"],
-                  tile_auto=True)
-    for i, w in enumerate(ws):
-        b.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
-                       mu_bottom=neutral, mu_top=neutral, drop=w.drop, concave=w.concave)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    steps, conv, res = b.run(args.sweep_steps, check_every=1000, tol=0.0, angle_tol=0.05)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t
-    ang = b.measure()
     rows = []
-    for i, w in enumerate(ws):
-        l, r = ang[i]
-        row = {"name": w.name, "concave": w.concave, "R": w.circle[2], "r": w.drop[2],
-               "target": float(w.name.rsplit("theta", 1)[1]), "steps": int(steps[i]),
-               "converged": bool(conv[i]), "ok": l.status == 0 and r.status == 0}
-        if row["ok"]:
-            row.update(left=l.theta, right=r.theta, theta=0.5 * (l.theta + r.theta),
-                       alpha=0.5 * (l.alpha + r.alpha), beta=0.5 * (l.beta + r.beta))
-            ctx = lbm.lbm_batch_instance(b.b, i)
-            _, pd = lbm.lbm_read_candidates(ctx, w.nx, w.ny)
-            try:
-                row["cap"] = CM.cap_angle(pd[:, :2], pd[:, 2], w.circle, concave=w.concave)["theta"]
-            except ValueError:
-                row["cap"] = None
-        rows.append(row)
-    b.close()
-    updates = sum(w.nx * w.ny * int(s) for w, s in zip(ws, steps))
+    if dist:
+        dist.barrier()
+    t = time.perf_counter()
+    if ws:
+        b = lbm.Batch([(w.nx, w.ny) for w in ws], eos=m["eos"], Tr=m["Tr"], k2=m["k2"],
+                      kappa=m["kappa"], tau=m["tau"], s_e=m["s_e"], s_eps=m["s_eps"],
+                      s_q=m["s_q"], tile_auto=True)
+        for i, w in enumerate(ws):
+            b.set_geometry(i, circle=w.circle, mu_circle=neutral + w.mu_rel_circle,
+                           mu_bottom=neutral, mu_top=neutral, drop=w.drop, concave=w.concave)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        steps, conv, res = b.run(args.sweep_steps, check_every=1000, tol=0.0, angle_tol=0.05)
+        torch.cuda.synchronize()
+    dt = shard.max_over_ranks(time.perf_counter() - t, dist)
+    if ws:
+        ang = b.measure()
+        for i, w in enumerate(ws):
+            l, r = ang[i]
+            row = {"name": w.name, "concave": w.concave, "R": w.circle[2], "r": w.drop[2],
+                   "target": float(w.name.rsplit("theta", 1)[1]), "steps": int(steps[i]),
+                   "converged": bool(conv[i]), "ok": l.status == 0 and r.status == 0,
+                   "updates": w.nx * w.ny * int(steps[i])}
+            if row["ok"]:
+                row.update(left=l.theta, right=r.theta, theta=0.5 * (l.theta + r.theta),
+                           alpha=0.5 * (l.alpha + r.alpha), beta=0.5 * (l.beta + r.beta))
+                ctx = lbm.lbm_batch_instance(b.b, i)
+                _, pd = lbm.lbm_read_candidates(ctx, w.nx, w.ny)
+                try:
+                    row["cap"] = CM.cap_angle(pd[:, :2], pd[:, 2], w.circle,
+                                              concave=w.concave)["theta"]
+                except ValueError:
+                    row["cap"] = None
+            rows.append(row)
+        b.close()
+    rows = shard.gather(rows, dist)
+    if rows is None:
+        return None
+    assert [r["name"] for r in rows] == [w.name for w in ws_all]
+    ws = ws_all
+    steps = np.array([r["steps"] for r in rows])
+    conv = np.array([r["converged"] for r in rows])
+    updates = sum(r.pop("updates") for r in rows)
     groups = {}
     for row in rows:
         if row["ok"]:
@@ -459,7 +502,7 @@ def _sweep_one(args, Tr):
     return updates, dt, summary
 
 
-def run_sweep(args):
+def run_sweep(args, rank=0, world=1, dist=None):
     """Grid-independence and curvature sweep (Sec. 4.1-4.2): drops of 30-100 lu on convex
     cylinders and in cavities of radius 150-400 lu for five wall potentials, all instances
     advanced together by the persistent batched kernel until their angles settle (two
@@ -469,17 +512,23 @@ def run_sweep(args):
     temps = [float(t) for t in args.sweep_tr.split(",")]
     total_u, total_t, per = 0, 0.0, {}
     for Tr in temps:
-        u, dt, summ = _sweep_one(args, Tr)
+        res = _sweep_one(args, Tr, rank, world, dist)
+        if res is None:
+            continue
+        u, dt, summ = res
         total_u += u
         total_t += dt
         per[f"Tr={Tr:g}"] = summ
+    if rank != 0:
+        return None
     n_inst = next(iter(per.values()))["instances"]
-    return {"metric": "MLUPS", "value": total_u / total_t / 1e6, "unit": "MLUPS", "n_gpus": 1,
+    return {"metric": "MLUPS", "value": total_u / total_t / 1e6, "unit": "MLUPS", "n_gpus": world,
             "steps": args.sweep_steps, "warmup": 0, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"curvature-sweep-{n_inst}-instances",
                        "temperatures": temps,
+                       "parallelism": f"instances split over {world} rank(s), rows gathered",
                        "timing": "host wall clock around each synchronous batch run (autotune, "
                                  "angle checks every 1,000 steps included)"},
             "sweep": per}
@@ -753,49 +802,61 @@ def run_surrogate(args):
                                  "the limit"}}
 
 
-def run_warmstart(args):
-    """Learned warm start (256 x 256 cases): generate equilibria with the batched solver, train
-    the BF16 U-Net with the library's kernels, compare steps to the +-0.5 degree equilibrated
-    angle for cold (Eq. 16 cap) and warm (prediction) starts on held-out seeds."""
-    from paper_2202_06516_gb300 import lbm, warmstart as WS, workloads as W
-    log = lambda msg: print(msg, file=sys.stderr, flush=True)
+def run_warmstart(args, rank=0, world=1, dist=None):
+    """Learned warm start (256 x 256 cases) and the time to the equilibrated angle: generate
+    equilibria with the batched solver, train the BF16 U-Net with the library's kernels, then on
+    held-out seeds measure steps and wall-clock seconds to the +-0.5 degree equilibrated angle
+    (the plain cold run's final angle) for the plain single-instance solver (one lattice per
+    case, one after another), the batched solver from the Eq. 16 start, and the batched solver
+    from the network's prediction. Under torchrun the training-case generation and the held-out
+    evaluation are split over the ranks (contiguous ranges), the data and the per-case results
+    gathered on rank 0, which trains; the trained weights are broadcast for the evaluation."""
+    from paper_2202_06516_gb300 import lbm, shard, warmstart as WS, workloads as W
+    log = (lambda msg: print(msg, file=sys.stderr, flush=True)) if rank == 0 else None
     t0 = time.perf_counter()
     tr = W.warm_cases(args.train_cases, seed=1)
     ev = W.warm_cases(args.eval_cases, seed=10000)
-    x, t, m = WS.generate(tr, steps=args.gen_steps)
-    t_gen = time.perf_counter() - t0
-    log(f"generated {len(tr)} cases in {t_gen:.1f}s")
+    lo, hi = shard.partition([1.0] * len(tr), world, rank)
+    part = WS.generate(tr[lo:hi], steps=args.gen_steps) if hi > lo else None
+    parts = shard.gather([part] if part is not None else [], dist)
+    t_gen = shard.max_over_ranks(time.perf_counter() - t0, dist)
+    weights = None
+    info = {}
+    if rank == 0:
+        x = np.concatenate([p_[0] for p_ in parts])
+        t = np.concatenate([p_[1] for p_ in parts])
+        m = np.concatenate([p_[2] for p_ in parts])
+        log(f"generated {len(tr)} cases in {t_gen:.1f}s")
+        sur = lbm.Surrogate(256, 256, base=32, max_batch=args.batch)
+        sur.set_weights(W.unet_init(32, seed=0))
+        losses, t_train = WS.train(sur, x, t, m, epochs=args.epochs, batch=args.batch,
+                                   lr=args.lr, log=log)
+        steps_per_epoch = len(tr) // args.batch
+        flops = 3 * unet_flops(256, 256, 32) * args.batch * steps_per_epoch * args.epochs
+        weights = sur.weights()
+        sur.close()
+        info = {"loss_first_last": [losses[0], losses[-1]], "train_seconds": t_train,
+                "train_tflops": flops / t_train / 1e12}
+    weights = shard.broadcast(weights, dist)
     sur = lbm.Surrogate(256, 256, base=32, max_batch=args.batch)
-    sur.set_weights(W.unet_init(32, seed=0))
-    losses, t_train = WS.train(sur, x, t, m, epochs=args.epochs, batch=args.batch, lr=args.lr,
-                               log=log)
-    steps_per_epoch = len(tr) // args.batch
-    flops = 3 * unet_flops(256, 256, 32) * args.batch * steps_per_epoch * args.epochs
-    rows, hc, hw = WS.evaluate(sur, ev, steps=args.gen_steps, every=250, log=log)
-    cold = [r[0] for r in rows if r[0] is not None and r[1] is not None]
-    warm = [r[1] for r in rows if r[0] is not None and r[1] is not None]
-    both = len(cold)
-    # each run against its own final angle (contact lines pin on the staircase wall, so a warm
-    # run may settle a little away from the cold run's final state)
-    own = [(r[2], r[3]) for r in rows if r[2] is not None and r[3] is not None]
-    gaps = [r[4] for r in rows if r[4] is not None]
-    line = {"metric": "steps to +-0.5 deg equilibrated angle (median, held-out)",
-            "impl": "cuda", "workload": "warm-start-256x256", "data": "synthetic",
-            "train_cases": len(tr), "eval_cases": len(ev), "epochs": args.epochs,
-            "loss_first_last": [losses[0], losses[-1]], "gen_seconds": t_gen,
-            "train_seconds": t_train,
-            "train_tflops": flops / t_train / 1e12,
-            "eval_pairs": both,
-            "cold_median_steps": float(np.median(cold)) if both else None,
-            "warm_median_steps": float(np.median(warm)) if both else None,
-            "warm_faster_fraction": float(np.mean(np.array(warm) < np.array(cold))) if both else None,
-            "cold_unreached": sum(1 for r in rows if r[0] is None),
-            "warm_unreached": sum(1 for r in rows if r[0] is not None and r[1] is None),
-            "self_equilibration_pairs": len(own),
-            "self_cold_median_steps": float(np.median([a for a, _ in own])) if own else None,
-            "self_warm_median_steps": float(np.median([b_ for _, b_ in own])) if own else None,
-            "final_angle_gap_deg_median": float(np.median(gaps)) if gaps else None}
+    sur.set_weights(weights)
+    lo, hi = shard.partition([1.0] * len(ev), world, rank)
+    rows, extra = (WS.evaluate(sur, ev[lo:hi], steps=args.gen_steps, every=250,
+                               plain=not args.no_plain) if hi > lo else ([], {}))
     sur.close()
+    rows = shard.gather(rows, dist)
+    extras = shard.gather([extra], dist)
+    if rank != 0:
+        return None
+    tta = WS.summarise(rows, WS.merge_extra(extras))
+    line = {"metric": "time to +-0.5 deg equilibrated angle (held-out 256x256 cases)",
+            "impl": "cuda", "workload": "warm-start-256x256", "data": "synthetic",
+            "n_gpus": world, "train_cases": len(tr), "eval_cases": len(ev),
+            "epochs": args.epochs, "gen_seconds": t_gen, **info,
+            "criterion": "first angle check (every 250 steps, both sides) after which every "
+                         "later check lies within 0.5 deg of the plain cold run's final angle "
+                         f"after {args.gen_steps} steps",
+            "time_to_angle": tta}
     return line
 
 
@@ -820,6 +881,8 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--converge", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="warmstart workload: skip the plain single-instance runs")
     ap.add_argument("--hyst-steps", type=int, default=200000)
     ap.add_argument("--sweep-steps", type=int, default=60000)
     ap.add_argument("--boundary-steps", type=int, default=30000)
@@ -854,13 +917,21 @@ def main():
     from paper_2202_06516_gb300 import _native
     if rank == 0:
         _native.build()
+    if dist:
+        dist.barrier()  # the other ranks load the library rank 0 has just built
     if args.workload == "batched":
+        line = run_batched(args, rank, world, dist)
         if rank == 0:
-            print(json.dumps(run_batched(args)), flush=True)
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
         return
     if args.workload == "warmstart":
+        line = run_warmstart(args, rank, world, dist)
         if rank == 0:
-            print(json.dumps(run_warmstart(args)), flush=True)
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
         return
     if args.workload == "surrogate":
         if rank == 0:
@@ -871,8 +942,11 @@ def main():
             print(json.dumps(run_hysteresis(args)), flush=True)
         return
     if args.workload == "sweep":
+        line = run_sweep(args, rank, world, dist)
         if rank == 0:
-            print(json.dumps(run_sweep(args)), flush=True)
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
         return
     if args.workload == "boundary":
         if rank == 0:

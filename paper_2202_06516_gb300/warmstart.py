@@ -171,28 +171,77 @@ def match_mass(phi, mask, target_mass, rho_g, rho_l):
 
 
 def angle_histories(b, n, steps, every):
-    """Angles (n, n_meas, 2) measured every `every` steps (NaN where a side had no contact)."""
-    hist = []
+    """Angles (n, n_meas, 2) measured every `every` steps (NaN where a side had no contact) and
+    the wall-clock seconds since the start at each measurement (the batch run and the
+    measurement are synchronous)."""
+    hist, times = [], []
+    t0 = time.perf_counter()
     for _ in range(steps // every):
         b.run(every, check_every=every, tol=0.0)
         ang = b.measure()
         hist.append([[a.theta if a.status == 0 else np.nan for a in pair] for pair in ang])
-    return np.transpose(np.array(hist), (1, 0, 2))
+        times.append(time.perf_counter() - t0)
+    return np.transpose(np.array(hist), (1, 0, 2)), np.array(times)
+
+
+def plain_histories(ws, steps, every, rho0=None):
+    """The plain single-instance solver: one lattice per case, run one after another, angles
+    every `every` steps. Returns the angles (n, n_meas, 2) and per case the wall-clock seconds
+    since that case's first step at each measurement (n, n_meas)."""
+    m = ws[0].model
+    co = lbm.lbm_coexistence(m["eos"], m["Tr"])
+    neutral = m["k2"] * co["mu_sat"]
+    hist = np.full((len(ws), steps // every, 2), np.nan)
+    times = np.zeros((len(ws), steps // every))
+    for i, w in enumerate(ws):
+        lat = lbm.Lattice(w.nx, w.ny, **_model_kw(m))
+        lat.set_geometry(**_geometry(w, neutral), rho0=None if rho0 is None else rho0[i])
+        lat.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps // every):
+            lat.step(every)
+            st, ang = lbm.lbm_measure_contact_angle(lat.ctx)
+            hist[i, k] = [a.theta_deg if a.status == 0 else np.nan for a in ang]
+            times[i, k] = time.perf_counter() - t0
+        lat.close()
+    return hist, times
+
+
+def reach_index(hist, theta_final, tol=0.5):
+    """Index of the first measurement after which every later measurement of both sides lies
+    within tol of theta_final (None if never): the time-to-equilibrated-angle criterion."""
+    ok = np.all(np.abs(hist - theta_final[None, :]) <= tol, axis=1)
+    for k in range(len(ok)):
+        if ok[k:].all():
+            return k
+    return None
 
 
 def time_to_angle(hist, theta_final, every, tol=0.5):
     """First measured step after which every later measurement of both sides lies within tol of
     theta_final (None if never)."""
-    ok = np.all(np.abs(hist - theta_final[None, :]) <= tol, axis=1)
-    for k in range(len(ok)):
-        if ok[k:].all():
-            return (k + 1) * every
-    return None
+    k = reach_index(hist, theta_final, tol)
+    return None if k is None else (k + 1) * every
 
 
-def evaluate(sur, ws, steps=20000, every=250, log=None):
-    """Cold start (Eq. 16 cap) vs warm start (prediction) for the held-out cases: steps to the
-    +-0.5 degree equilibrated angle of the cold run's final angle."""
+def evaluate(sur, ws, steps=20000, every=250, log=None, plain=True):
+    """Time to the equilibrated angle for held-out cases, three ways, all judged against the final
+    angle theta_f of the plain cold run (Eq. 16 cap start) of the same case, criterion
+    `reach_index` with tol 0.5 degrees:
+      plain   one lattice per case, cases one after another (skipped with plain=False; the
+              batched cold run then stands in for the reference, which it equals bit for bit);
+      cold    all cases in one batch from the Eq. 16 start;
+      warm    the network's prediction (shifted to the cold start's liquid mass) as the initial
+              density, all cases in one batch; its clock includes the prediction.
+    Returns one dict per case: the reference angle, steps and seconds to reach it per variant
+    (None if not reached), the warm run's own final angle, and a class: 'ok', 'no_contact' (a
+    side without contact at the end of the reference run: the drop lifted off or wet past the
+    circle) or 'unsettled' (the reference run's last quarter strays more than 0.5 degrees from
+    its final angle, so theta_f is no equilibrium)."""
+    n_meas = steps // every
+    hp = tp = None
+    if plain:
+        hp, tp = plain_histories(ws, steps, every)
     bc, co, neutral = make_batch(ws)
     x = inputs_of(bc, ws, neutral, co)
     masses, fluid = [], []
@@ -200,24 +249,103 @@ def evaluate(sur, ws, steps=20000, every=250, log=None):
         ctx = lbm.lbm_batch_instance(bc.b, i)
         masses.append(lbm.lbm_mass(ctx)[1]["mass"])
         fluid.append(lbm.lbm_read_geometry(ctx, w.nx, w.ny)[0][2:-2] == 0)
-    hc = angle_histories(bc, len(ws), steps, every)
+    hc, tc = angle_histories(bc, len(ws), steps, every)
     bc.close()
+    t0 = time.perf_counter()
     phi = predict(sur, x).astype(np.float64)
     phi = np.stack([match_mass(phi[i], fluid[i], masses[i], co["rho_g"], co["rho_l"])
                     for i in range(len(ws))])
     rho0 = co["rho_g"] + phi * (co["rho_l"] - co["rho_g"])
     bw, _, _ = make_batch(ws, rho0=rho0)
-    hw = angle_histories(bw, len(ws), steps, every)
+    t_pred = time.perf_counter() - t0
+    hw, tw = angle_histories(bw, len(ws), steps, every)
     bw.close()
+    ref = hp if plain else hc
     rows = []
     for i in range(len(ws)):
-        final = hc[i, -1]
+        final = ref[i, -1]
+        row = {"theta_f": final.tolist(), "plain_identical": None if hp is None else
+               bool(np.array_equal(hp[i], hc[i], equal_nan=True))}
         if np.isnan(final).any():
-            rows.append((None, None, None, None, None))
-            continue
+            row["class"] = "no_contact"
+        elif reach_index(ref[i], final) is None or reach_index(ref[i], final) > (3 * n_meas) // 4:
+            row["class"] = "unsettled"
+        else:
+            row["class"] = "ok"
+        for name, h, tt in (("plain", hp, tp), ("cold", hc, None), ("warm", hw, None)):
+            if h is None or row["class"] == "no_contact":
+                row[name] = None
+                continue
+            k = reach_index(h[i], final)
+            if k is None:
+                row[name] = None
+            elif name == "plain":
+                row[name] = ((k + 1) * every, float(tt[i, k]))
+            elif name == "cold":
+                row[name] = ((k + 1) * every, float(tc[k]))
+            else:
+                row[name] = ((k + 1) * every, float(t_pred + tw[k]))
         own = hw[i, -1]
-        rows.append((time_to_angle(hc[i], final, every), time_to_angle(hw[i], final, every),
-                     time_to_angle(hc[i], final, every),
-                     None if np.isnan(own).any() else time_to_angle(hw[i], own, every),
-                     None if np.isnan(own).any() else float(np.abs(own - final).max())))
-    return rows, hc, hw
+        row["warm_final_gap"] = None if np.isnan(own).any() or np.isnan(final).any() else \
+            float(np.abs(own - final).max())
+        row["warm_self"] = None if np.isnan(own).any() else time_to_angle(hw[i], own, every)
+        row["cold_self"] = None if np.isnan(final).any() else time_to_angle(hc[i], hc[i, -1], every)
+        rows.append(row)
+    extra = {"prediction_seconds": t_pred, "cold_batch_seconds": float(tc[-1]),
+             "warm_batch_seconds": float(tw[-1]),
+             "plain_seconds": None if tp is None else float(tp[:, -1].sum())}
+    return rows, extra
+
+
+def merge_extra(parts):
+    """Per-rank `evaluate` timings combined: batches run side by side (the slowest rank's time),
+    the prediction likewise, the plain runs' total is a sum over all cases."""
+    parts = [p for p in parts if p]
+    if not parts:
+        return {}
+    out = {k: max(p[k] for p in parts) for k in ("prediction_seconds", "cold_batch_seconds",
+                                                 "warm_batch_seconds")}
+    plain = [p["plain_seconds"] for p in parts]
+    out["plain_seconds"] = None if any(v is None for v in plain) else float(sum(plain))
+    return out
+
+
+def summarise(rows, extra):
+    """Aggregate the per-case rows of `evaluate` (possibly gathered from several ranks):
+    per variant the cases that reach the reference angle, their median steps and seconds, and
+    the time until every reaching case has reached it (the plain variant runs the cases one after
+    another, so its total is the sum over cases)."""
+    classes = {}
+    for r in rows:
+        classes[r["class"]] = classes.get(r["class"], 0) + 1
+    ok = [r for r in rows if r["class"] == "ok"]
+    out = {"cases": len(rows), "classes": classes, "judged": len(ok)}
+    ran_plain = any(r["plain_identical"] is not None for r in rows)
+    for name in ("plain", "cold", "warm"):
+        if name == "plain" and not ran_plain:
+            out[name] = None
+            continue
+        got = [r[name] for r in ok if r[name] is not None]
+        steps = [g[0] for g in got]
+        secs = [g[1] for g in got]
+        out[name] = {"reached": len(got), "reached_fraction": len(got) / len(ok) if ok else None,
+                     "median_steps": float(np.median(steps)) if got else None,
+                     "median_seconds": float(np.median(secs)) if got else None,
+                     "all_reached_seconds": (float(np.sum(secs)) if name == "plain"
+                                             else float(np.max(secs))) if got else None}
+    both = [(r["cold"][0], r["warm"][0]) for r in ok if r["cold"] and r["warm"]]
+    out["warm_faster_fraction"] = float(np.mean([w < c for c, w in both])) if both else None
+    gaps = [r["warm_final_gap"] for r in rows if r["warm_final_gap"] is not None]
+    out["warm_final_gap_median_deg"] = float(np.median(gaps)) if gaps else None
+    out["warm_settles_elsewhere"] = sum(1 for r in ok if r["warm"] is None and
+                                        r["warm_final_gap"] is not None and
+                                        r["warm_final_gap"] > 0.5)
+    own = [(r["cold_self"], r["warm_self"]) for r in rows
+           if r["cold_self"] is not None and r["warm_self"] is not None]
+    out["own_final_angle"] = {"pairs": len(own),
+                              "cold_median_steps": float(np.median([a for a, _ in own])) if own else None,
+                              "warm_median_steps": float(np.median([b for _, b in own])) if own else None}
+    ident = [r["plain_identical"] for r in rows if r["plain_identical"] is not None]
+    out["plain_equals_batched_cold"] = all(ident) if ident else None
+    out.update(extra)
+    return out
