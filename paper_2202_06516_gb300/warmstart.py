@@ -154,20 +154,29 @@ def predict(sur, x, batch=8):
     return out
 
 
-def match_mass(phi, mask, target_mass, rho_g, rho_l):
+def match_mass(phi, mask, target_mass, rho_g, rho_l, rtol=1e-12):
     """Shift phi by one constant (then clip to [0, 1]) so that the fluid nodes hold the mass of
-    the cold start: the warm and cold runs then relax the same amount of liquid. Bisection on
-    the shift."""
-    def mass(c):
-        return (rho_g + np.clip(phi + c, 0, 1) * (rho_l - rho_g))[mask].sum()
+    the cold start: the warm and cold runs then relax the same amount of liquid. The liquid
+    content F(c) = sum clip(phi + c, 0, 1) is piecewise linear and non-decreasing in the shift c
+    with slope = the number of nodes strictly inside (0, 1); Newton steps on it, kept inside a
+    shrinking bracket (bisection where a step leaves it), find the shift in a few evaluations."""
+    p = phi[mask].astype(np.float64)
+    goal = (target_mass - rho_g * p.size) / (rho_l - rho_g)
     lo, hi = -1.0, 1.0
-    for _ in range(60):
-        mid = 0.5 * (lo + hi)
-        if mass(mid) < target_mass:
-            lo = mid
+    c = 0.0
+    for _ in range(100):
+        v = p + c
+        F = np.clip(v, 0.0, 1.0).sum()
+        if abs(F - goal) <= rtol * max(1.0, abs(goal)):
+            break
+        if F < goal:
+            lo = c
         else:
-            hi = mid
-    return np.clip(phi + 0.5 * (lo + hi), 0, 1)
+            hi = c
+        slope = np.count_nonzero((v > 0.0) & (v < 1.0))
+        nxt = c + (goal - F) / slope if slope else 0.5 * (lo + hi)
+        c = nxt if lo < nxt < hi else 0.5 * (lo + hi)
+    return np.clip(phi.astype(np.float64) + c, 0, 1)
 
 
 def angle_histories(b, n, steps, every):
