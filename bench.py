@@ -265,6 +265,9 @@ def run_cuda(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name.rsplit("-s", 1)[0], "nx": w.nx, "ny": w.ny,
                    "fluid_nodes": n_fluid, "measure_every": MEASURE_EVERY,
+                   "value_counts": "all nx*ny nodes (the disc's solid nodes included); the "
+                                   "roofline counts fluid nodes only",
+                   "fluid_mlups": n_fluid * args.steps * world / (ms * 1e-3) / 1e6,
                    "precision": "FP32 populations (deviation form), FP64 reductions/angles",
                    "l2": "working set 170 MB > L2, no flush", "parallelism": f"replicas{world}",
                    "eos": "Peng-Robinson Tr=0.7", "seed": "rank",

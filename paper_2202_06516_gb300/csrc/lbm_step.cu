@@ -160,15 +160,17 @@ cudaError_t launch_step(lbm_ctx* c, int src, bool macro) {
     if (c->esz == 4) {
         const StepArgs<float> a = make_args<float>(c, src);
 #define X(T, A, B, M)                                                                 \
-    if (sizeof(T) == 4 && c->tile_x == A && c->tile_y == B && minb_of(c) == M) \
-        return launch_one<float, A, B, M>(c, a, macro);
+    if constexpr (sizeof(T) == 4)                                                     \
+        if (c->tile_x == A && c->tile_y == B && minb_of(c) == M)                      \
+            return launch_one<float, A, B, M>(c, a, macro);
         LBM_STEP_VARIANTS(X)
 #undef X
     } else {
         const StepArgs<double> a = make_args<double>(c, src);
 #define X(T, A, B, M)                                                                 \
-    if (sizeof(T) == 8 && c->tile_x == A && c->tile_y == B && minb_of(c) == M) \
-        return launch_one<double, A, B, M>(c, a, macro);
+    if constexpr (sizeof(T) == 8)                                                     \
+        if (c->tile_x == A && c->tile_y == B && minb_of(c) == M)                      \
+            return launch_one<double, A, B, M>(c, a, macro);
         LBM_STEP_VARIANTS(X)
 #undef X
     }

@@ -274,29 +274,6 @@ __device__ __forceinline__ void stream_out(const StepArgs<T>& a, const T* s_rho,
     }
 }
 
-// Visits every (row, column) of a W x H region once with NT threads: lanes take consecutive
-// columns of one row in 32-wide segments, so a warp's shared-memory accesses stay inside a row
-// (the region rows are narrower than the staged rows they read, and a warp that wrapped from one
-// row into the next would hit the same banks twice); the W mod 32 columns left in every row are
-// handed out afterwards, starting at the first warp that got one segment fewer.
-template <int NT, int W, int H, typename F>
-__device__ __forceinline__ void for_region(F&& f) {
-    constexpr int NW = NT / 32, K = W / 32, T = W % 32, SEG = K * H;
-    static_assert(NT % 32 == 0 && K >= 1, "whole warps and regions at least 32 wide");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int sg = warp; sg < SEG; sg += NW) {
-        const int r = sg / K;
-        f(r, (sg - r * K) * 32 + lane);
-    }
-    if constexpr (T > 0) {
-        constexpr int OFF = (SEG % NW) * 32;
-        for (int i = ((int)threadIdx.x - OFF + NT) % NT; i < T * H; i += NT) {
-            const int r = i / T;
-            f(r, K * 32 + (i - r * T));
-        }
-    }
-}
-
 // MIXED: the tile and its halo contain non-fluid nodes (walls, the disc, the domain edge), so
 // wetting layers are rebuilt and every neighbour access checks the node class. Interior tiles
 // take the branch-free path (the choice is uniform per CTA). IBB: interpolated, mass-corrected
@@ -349,8 +326,8 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
     }
 
     // (4) chemical potential on tile + 3 (Eq. 12)
-    for_region<NT, MW, MH>([&](const int my, const int mx) {
-        const int idx = my * MW + mx;
+    for (int idx = tid; idx < MW * MH; idx += NT) {
+        const int my = idx / MW, mx = idx - my * MW;
         const int o = (my + 4) * RW + (mx + 5);
         T mu;
         if (!MIXED) {
@@ -365,7 +342,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
                 mu = (T)0;
         }
         s_mu[idx] = mu;
-    });
+    }
     __syncthreads();
 
     // (5) force and collision on tile + 1
@@ -374,10 +351,10 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
     const unsigned upl = (unsigned)a.plane, uP = (unsigned)a.P;
 #define QPL(q) ((unsigned)(q) * upl)
 #define QSRC(q) ((unsigned)(q) * upl - (unsigned)(qy(q) * (int)uP + qx(q)))
-    for_region<NT, CW, CH>([&](const int cy, const int cx) {
-        const int idx = cy * CW + cx;
+    for (int idx = tid; idx < CW * CH; idx += NT) {
+        const int cy = idx / CW, cx = idx - cy * CW;
         const int o = (cy + 6) * RW + (cx + 7);
-        if (MIXED && s_flag[o] != kFluid) return;
+        if (MIXED && s_flag[o] != kFluid) continue;
         const int om = (cy + 2) * MW + (cx + 2);
         const int gx = x0 - 1 + cx, gy = y0 - 1 + cy;
         const int self = lidx(a.P, gx, gy);
@@ -436,7 +413,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T>& a, const T rho_mid,
             for (int q = 0; q < 9; ++q) s_g[q * CW * CH + idx] = g[q];
             s_g[9 * CW * CH + idx] = A;
         }
-    });
+    }
     if (MACRO) return;
     __syncthreads();
 
