@@ -354,6 +354,22 @@ lbm_status lbm_sg_gemm(const void *A, const void *B, int32_t M, int32_t N, int32
  * flag could not be allocated. */
 lbm_status lbm_sg_inject_timeout(void);
 
+/* Checkpoint and restart (no counterpart in the paper): the dynamic state of a lattice, i.e. the
+ * current populations and densities exactly as stored on the device (padded planes, the
+ * context's precision) and the step counter, behind a small header (magic, version, nx, ny,
+ * element size, steps, plane size). The geometry is not part of it: restore by creating a
+ * context with the same parameters, calling lbm_set_geometry with the same geometry, then
+ * lbm_load_state; stepping on is then bit-identical to the uninterrupted run.
+ * lbm_state_bytes: the checkpoint's size for this context (0 for NULL).
+ * lbm_save_state: writes it into a caller-owned host buffer of exactly that size; synchronous.
+ *   LBM_ERR_STATE before lbm_set_geometry, LBM_ERR_ARG for a NULL buffer or another size.
+ * lbm_load_state: reads it back; LBM_ERR_STATE before lbm_set_geometry, LBM_ERR_ARG for a
+ *   buffer that is not a checkpoint of this version or belongs to another nx, ny or precision
+ *   (the context is then unchanged). Synchronous. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+lbm_status lbm_save_state(lbm_ctx *ctx, void *host, size_t bytes);
+lbm_status lbm_load_state(lbm_ctx *ctx, const void *host, size_t bytes);
+
 /* Wait for the context's stream. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
 

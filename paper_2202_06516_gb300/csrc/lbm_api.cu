@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "lbm_internal.cuh"
+#include "lbm_trace.h"
 
 namespace lbm {
 size_t meas_partial_bytes(int nblocks);
@@ -365,6 +366,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
 }
 
 lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
+    lbm::NvtxRange nvtx_("lbm_set_geometry");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_set_geometry: ctx is NULL");
     if (!g) return fail(c, LBM_ERR_ARG, "lbm_set_geometry: geometry is NULL");
     if (g->has_circle && (!half_integral(g->cx) || !half_integral(g->cy) || !half_integral(g->R) ||
@@ -448,6 +450,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
 }
 
 lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
+    lbm::NvtxRange nvtx_("lbm_step");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_step: ctx is NULL");
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "lbm_step: nsteps < 0");
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_step: call lbm_set_geometry first");
@@ -484,6 +487,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
 
 lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, lbm_tune_entry* entries,
                         int32_t max_entries, int32_t* n_out) {
+    lbm::NvtxRange nvtx_("lbm_autotune");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_autotune: ctx is NULL");
     if (trial_steps < 1) return fail(c, LBM_ERR_ARG, "lbm_autotune: trial_steps < 1");
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_autotune: call lbm_set_geometry first");
@@ -548,6 +552,7 @@ lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, lbm_tune_entry* entries
 }
 
 lbm_status lbm_measure_contact_angle(lbm_ctx* c, lbm_angle out[2]) {
+    lbm::NvtxRange nvtx_("lbm_measure_contact_angle");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_measure_contact_angle: ctx is NULL");
     if (!out) return fail(c, LBM_ERR_ARG, "lbm_measure_contact_angle: out is NULL");
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_measure_contact_angle: no geometry");
@@ -562,6 +567,7 @@ lbm_status lbm_measure_contact_angle(lbm_ctx* c, lbm_angle out[2]) {
 }
 
 lbm_status lbm_mass(lbm_ctx* c, double out[4]) {
+    lbm::NvtxRange nvtx_("lbm_mass");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_mass: ctx is NULL");
     if (!out) return fail(c, LBM_ERR_ARG, "lbm_mass: out is NULL");
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_mass: no geometry");
@@ -580,6 +586,7 @@ lbm_status lbm_mass(lbm_ctx* c, double out[4]) {
 
 lbm_status lbm_read_fields(lbm_ctx* c, uint32_t which, double* rho, double* ux, double* uy,
                            size_t n) {
+    lbm::NvtxRange nvtx_("lbm_read_fields");
     if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_read_fields: ctx is NULL");
     if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_read_fields: no geometry");
     const size_t N = (size_t)c->nx * c->ny;
@@ -704,6 +711,77 @@ lbm_status lbm_get_info(lbm_ctx* c, lbm_info* out) {
     out->tile_y = c->tile_y;
     out->precision = c->p.precision;
     out->min_blocks = c->min_blocks;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Checkpoint of the dynamic state: a fixed header, then the current population planes and the
+// current density plane exactly as stored on the device (padded layout, FP32 or FP64).
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr uint64_t kStateMagic = 0x314b43504d424c00ull;  // "\0LBMPCK1" little-endian
+constexpr int32_t kStateVersion = 1;
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, nx, ny, esz;
+    int64_t steps;
+    uint64_t plane;    // elements per padded plane
+    uint64_t payload;  // bytes after the header: 10 planes
+};
+size_t state_payload(const lbm_ctx* c) { return 10 * c->plane * c->esz; }
+}  // namespace
+
+size_t lbm_state_bytes(const lbm_ctx* c) {
+    return c ? sizeof(StateHeader) + state_payload(c) : 0;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* host, size_t bytes) {
+    lbm::NvtxRange nvtx_("lbm_save_state");
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_save_state: ctx is NULL");
+    if (!host) return fail(c, LBM_ERR_ARG, "lbm_save_state: buffer is NULL");
+    if (!c->has_geometry) return fail(c, LBM_ERR_STATE, "lbm_save_state: no geometry");
+    if (bytes != lbm_state_bytes(c))
+        return fail(c, LBM_ERR_ARG, "lbm_save_state: bytes must equal lbm_state_bytes(ctx) = " +
+                                        std::to_string(lbm_state_bytes(c)));
+    DeviceGuard dg(c->device);
+    StateHeader h{kStateMagic, kStateVersion, c->nx, c->ny, (int32_t)c->esz, c->steps,
+                  (uint64_t)c->plane, (uint64_t)state_payload(c)};
+    memcpy(host, &h, sizeof h);
+    uint8_t* dst = static_cast<uint8_t*>(host) + sizeof h;
+    const size_t hb = 9 * c->plane * c->esz;
+    LBM_CUDA(c, cudaMemcpyAsync(dst, c->h[c->cur], hb, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(dst + hb, c->rho[c->cur], c->plane * c->esz,
+                                cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* host, size_t bytes) {
+    lbm::NvtxRange nvtx_("lbm_load_state");
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "lbm_load_state: ctx is NULL");
+    if (!host) return fail(c, LBM_ERR_ARG, "lbm_load_state: buffer is NULL");
+    if (!c->has_geometry)
+        return fail(c, LBM_ERR_STATE, "lbm_load_state: call lbm_set_geometry (the checkpoint's "
+                                      "geometry) first");
+    if (bytes < sizeof(StateHeader))
+        return fail(c, LBM_ERR_ARG, "lbm_load_state: buffer shorter than the header");
+    StateHeader h;
+    memcpy(&h, host, sizeof h);
+    if (h.magic != kStateMagic || h.version != kStateVersion)
+        return fail(c, LBM_ERR_ARG, "lbm_load_state: not a checkpoint of this library version");
+    if (h.nx != c->nx || h.ny != c->ny || h.esz != (int32_t)c->esz || h.plane != c->plane ||
+        h.payload != state_payload(c) || bytes != lbm_state_bytes(c) || h.steps < 0)
+        return fail(c, LBM_ERR_ARG, "lbm_load_state: checkpoint of another lattice size or "
+                                    "precision, or wrong buffer size");
+    DeviceGuard dg(c->device);
+    const uint8_t* src = static_cast<const uint8_t*>(host) + sizeof h;
+    const size_t hb = 9 * c->plane * c->esz;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));  // nothing in flight reads the buffers
+    LBM_CUDA(c, cudaMemcpyAsync(c->h[c->cur], src, hb, cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(c->rho[c->cur], src + hb, c->plane * c->esz,
+                                cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
     return LBM_OK;
 }
 

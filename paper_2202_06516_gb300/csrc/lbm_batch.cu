@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "lbm_step_body.cuh"
+#include "lbm_trace.h"
 
 namespace lbm {
 void set_global_error(const std::string& msg);
@@ -424,6 +425,7 @@ lbm_status lbm_batch_set_geometry(lbm_batch* b, int32_t i, const lbm_geometry* g
 lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, double tol,
                          double angle_tol, int64_t* steps_out, int32_t* converged_out,
                          double* residual_out) {
+    lbm::NvtxRange nvtx_("lbm_batch_run");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_run: batch is NULL");
     if (max_steps < 0 || check_every < 2 || (check_every & 1))
         return bfail(b, LBM_ERR_ARG, "lbm_batch_run: need max_steps >= 0 and an even check_every >= 2");
@@ -543,6 +545,7 @@ lbm_status lbm_batch_run(lbm_batch* b, int64_t max_steps, int32_t check_every, d
 
 lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, lbm_tune_entry* entries,
                               int32_t max_entries, int32_t* n_out) {
+    lbm::NvtxRange nvtx_("lbm_batch_autotune");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_autotune: batch is NULL");
     if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "lbm_batch_autotune: trial_steps < 1");
     BCUDA(b, cudaSetDevice(b->inst[0]->device));
@@ -610,6 +613,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, lbm_tune_entry*
 }
 
 lbm_status lbm_batch_measure(lbm_batch* b, lbm_angle* out) {
+    lbm::NvtxRange nvtx_("lbm_batch_measure");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "lbm_batch_measure: batch is NULL");
     if (!out) return bfail(b, LBM_ERR_ARG, "lbm_batch_measure: out is NULL");
     lbm_status worst = LBM_OK;

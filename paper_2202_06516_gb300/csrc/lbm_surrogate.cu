@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "lbm_internal.cuh"
+#include "lbm_trace.h"
 #include "sg_gemm.cuh"
 #include "sg_tc.cuh"
 
@@ -695,6 +696,7 @@ lbm_status lbm_surrogate_get_weights(lbm_surrogate* s, float* host, int64_t n, i
 }
 
 lbm_status lbm_surrogate_forward(lbm_surrogate* s, const void* x, int32_t B, float* phi_out) {
+    lbm::NvtxRange nvtx_("lbm_surrogate_forward");
     if (!s || !x || !phi_out || B <= 0 || B > s->maxB)
         return sfail(s, LBM_ERR_ARG, "lbm_surrogate_forward: bad arguments");
     SCUDA(s, cudaSetDevice(s->device));
@@ -726,6 +728,7 @@ lbm_status lbm_surrogate_forward(lbm_surrogate* s, const void* x, int32_t B, flo
 // Gradients of the masked MSE into s->g; with lr > 0 also an Adam update. *loss gets the loss.
 lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const float* target,
                                     const uint8_t* mask, int32_t B, float lr, double* loss) {
+    lbm::NvtxRange nvtx_("lbm_surrogate_train_step");
     if (!s || !xin || !target || !mask || B <= 0 || B > s->maxB)
         return sfail(s, LBM_ERR_ARG, "lbm_surrogate_train_step: bad arguments");
     SCUDA(s, cudaSetDevice(s->device));

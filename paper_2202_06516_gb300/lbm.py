@@ -91,6 +91,10 @@ def lib() -> C.CDLL:
         L.lbm_read_candidates.argtypes = [vp, i64p, dp, C.c_int64, i64p]
         L.lbm_get_info.argtypes = [vp, C.POINTER(lbm_info)]
         L.lbm_synchronize.argtypes = [vp]
+        L.lbm_state_bytes.argtypes = [vp]
+        L.lbm_state_bytes.restype = C.c_size_t
+        L.lbm_save_state.argtypes = [vp, vp, C.c_size_t]
+        L.lbm_load_state.argtypes = [vp, vp, C.c_size_t]
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_last_error.argtypes = [vp]
@@ -116,7 +120,8 @@ def lib() -> C.CDLL:
             getattr(L, n).restype = C.c_int
         for n in ("lbm_coexistence", "lbm_eos_eval", "lbm_create", "lbm_set_geometry", "lbm_step",
                   "lbm_measure_contact_angle", "lbm_read_fields", "lbm_mass", "lbm_read_geometry",
-                  "lbm_read_candidates", "lbm_get_info", "lbm_synchronize"):
+                  "lbm_read_candidates", "lbm_get_info", "lbm_synchronize", "lbm_save_state",
+                  "lbm_load_state"):
             getattr(L, n).restype = C.c_int
         _sig = True
     return L
@@ -239,6 +244,20 @@ def lbm_autotune(ctx, trial_steps: int = 20):
     """Time every step-kernel variant on the lattice's state and keep the fastest; returns
     the timings (list of dicts)."""
     return _tune(lib().lbm_autotune, ctx, trial_steps, _check)
+
+
+def lbm_save_state(ctx) -> bytes:
+    """Checkpoint of the lattice's dynamic state (populations, densities, step counter)."""
+    n = int(lib().lbm_state_bytes(ctx))
+    buf = (C.c_uint8 * n)()
+    _check(lib().lbm_save_state(ctx, buf, n), ctx)
+    return bytes(buf)
+
+
+def lbm_load_state(ctx, data: bytes):
+    """Restore a checkpoint written by lbm_save_state (after lbm_set_geometry)."""
+    buf = (C.c_uint8 * len(data)).from_buffer_copy(data)
+    _check(lib().lbm_load_state(ctx, buf, len(data)), ctx)
 
 
 def lbm_synchronize(ctx):
