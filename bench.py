@@ -805,6 +805,35 @@ def run_surrogate(args):
                                  "the limit"}}
 
 
+def time_to_angle_leg(args):
+    """The second half of the metric on a bounded sample, so that every default run records it:
+    a surrogate trained on args.tta_train solver-equilibrated 256 x 256 cases, then args.tta_cases
+    held-out cases (the warm-start workload's seeds) run to args.tta_steps steps three ways: plain
+    single-instance lattices one after another, the batched solver from the Eq. 16 start, and the
+    batched solver from the network's prediction; steps and wall-clock seconds to the +-0.5 deg
+    equilibrated angle of the plain run (see the warm-start workload). Not part of the timed
+    region of the main line."""
+    from paper_2202_06516_gb300 import lbm, warmstart as WS, workloads as W
+    t0 = time.perf_counter()
+    tr = W.warm_cases(args.tta_train, seed=1)
+    ev = W.warm_cases(args.tta_cases, seed=10000)
+    x, t, m = WS.generate(tr, steps=args.tta_steps)
+    t_gen = time.perf_counter() - t0
+    sur = lbm.Surrogate(256, 256, base=32, max_batch=8)
+    sur.set_weights(W.unet_init(32, seed=0))
+    losses, t_train = WS.train(sur, x, t, m, epochs=args.tta_epochs, batch=8, lr=args.lr)
+    rows, extra = WS.evaluate(sur, ev, steps=args.tta_steps, every=250)
+    sur.close()
+    out = WS.summarise(rows, extra)
+    out["config"] = {"train_cases": len(tr), "eval_cases": len(ev), "horizon_steps": args.tta_steps,
+                     "epochs": args.tta_epochs, "lattice": "256x256", "network": "U-Net base 32",
+                     "generation_seconds": round(t_gen, 2), "training_seconds": round(t_train, 2),
+                     "loss_first_last": [losses[0], losses[-1]],
+                     "criterion": "first check (every 250 steps, both sides) after which every later "
+                                  "check stays within 0.5 deg of the plain run's final angle"}
+    return out
+
+
 def run_warmstart(args, rank=0, world=1, dist=None):
     """Learned warm start (256 x 256 cases) and the time to the equilibrated angle: generate
     equilibria with the batched solver, train the BF16 U-Net with the library's kernels, then on
@@ -884,6 +913,12 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--converge", action="store_true")
+    ap.add_argument("--no-tta", action="store_true",
+                    help="default workload: skip the bounded time-to-angle leg")
+    ap.add_argument("--tta-train", type=int, default=1024)
+    ap.add_argument("--tta-cases", type=int, default=64)
+    ap.add_argument("--tta-steps", type=int, default=30000)
+    ap.add_argument("--tta-epochs", type=int, default=20)
     ap.add_argument("--no-plain", action="store_true",
                     help="warmstart workload: skip the plain single-instance runs")
     ap.add_argument("--hyst-steps", type=int, default=200000)
@@ -965,6 +1000,8 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        if world == 1 and not args.no_tta:
+            line["time_to_angle"] = time_to_angle_leg(args)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
