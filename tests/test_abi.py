@@ -147,6 +147,9 @@ def test_null_context_is_an_error_not_a_crash():
     L = lbm.lib()
     assert L.lbm_step(None, 1) == lbm.LBM_ERR_ARG
     assert L.lbm_measure_contact_angle(None, None) == lbm.LBM_ERR_ARG
+    assert L.lbm_state_bytes(None) == 0
+    assert L.lbm_save_state(None, None, 0) == lbm.LBM_ERR_ARG
+    assert L.lbm_load_state(None, None, 0) == lbm.LBM_ERR_ARG
     L.lbm_destroy(None)
 
 
