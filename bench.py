@@ -227,8 +227,12 @@ def run_cuda(args, rank, world, dist):
         co, _ = _resolve(w, lbm)
         j, i = np.mgrid[0:w.ny, 0:w.nx].astype(np.float64)
         d = np.sqrt((i - w.drop[0]) ** 2 + (j - w.drop[1]) ** 2)
-        rho0 = 0.5 * (co["rho_g"] + co["rho_l"]) + 0.5 * (co["rho_g"] - co["rho_l"]) * \
+        # the step's input and result live in pinned host memory (the copies run at full speed
+        # and no page is first touched inside the timed region)
+        rho0 = torch.empty((w.ny, w.nx), dtype=torch.float64, pin_memory=True).numpy()
+        rho0[:] = 0.5 * (co["rho_g"] + co["rho_l"]) + 0.5 * (co["rho_g"] - co["rho_l"]) * \
             np.tanh(2.0 * (d - w.drop[2]) / w.drop[3])
+        rho_out = torch.zeros((w.ny, w.nx), dtype=torch.float64, pin_memory=True).numpy()
         lat2, geo2 = _make_lattice(lbm, w, stream=stream, tile=tile[:2], min_blocks=tile[2])
         lat2.set_geometry(**geo2)
         lat2.step(max(3, args.warmup))
@@ -245,15 +249,16 @@ def run_cuda(args, rank, world, dist):
             if done % MEASURE_EVERY == 0:
                 lat2.measure()
                 nm += 1
-        rho_out = lat2.rho()
+        lat2.rho(out=rho_out)
         te = time.perf_counter() - tt
         lat2.close()
         ang_bytes = 2 * 104
         e2e = {"value": n_nodes * ke / te / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": rho0.nbytes / ke,
                "d2h_bytes_per_step": (rho_out.nbytes + nm * ang_bytes) / ke,
-               "what": "lbm_set_geometry(host rho0) + lbm_step + lbm_measure_contact_angle every "
-                       "500 steps + lbm_read_fields(rho), host wall clock"}
+               "what": "lbm_set_geometry(pinned host rho0) + lbm_step + "
+                       "lbm_measure_contact_angle every 500 steps + lbm_read_fields(rho into "
+                       "pinned host memory), host wall clock"}
 
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_FLUID_NODE * n_fluid / (kernel_us * 1e-6) / 1e9

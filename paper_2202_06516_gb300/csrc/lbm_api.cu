@@ -162,10 +162,18 @@ bool coexistence(const HostEos& e, double out[4]) {
 
 bool half_integral(double v) { return fabs(2.0 * v - nearbyint(2.0 * v)) < 1e-9; }
 
+void destroy_graphs(lbm_ctx* c) {
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < lbm::kGraphSizes; ++k) {
+            if (c->graph[p][k]) cudaGraphExecDestroy(c->graph[p][k]);
+            c->graph[p][k] = nullptr;
+        }
+    c->graphs_ready = false;
+}
+
 void free_all(lbm_ctx* c) {
+    destroy_graphs(c);
     for (int k = 0; k < 2; ++k) {
-        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
-        c->graph[k] = nullptr;
         cudaFree(c->h[k]);
         cudaFree(c->rho[k]);
         c->h[k] = c->rho[k] = nullptr;
@@ -180,6 +188,8 @@ void free_all(lbm_ctx* c) {
     cudaFree(c->meas_partials);
     cudaFree(c->meas_out);
     cudaFree(c->vel);
+    cudaFree(c->stage);
+    c->stage = nullptr;
     c->muw = c->vel = c->meas_partials = nullptr;
     c->flags = c->linkmask = nullptr;
     c->red_partials = nullptr;
@@ -201,35 +211,46 @@ struct DeviceGuard {
     }
 };
 
-lbm_status capture_graph(lbm_ctx* c, int start) {
-    if (c->graph_failed) return LBM_OK;
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        c->graph_failed = true;
-        return LBM_OK;
-    }
-    int cur = start;
-    cudaError_t le = cudaSuccess;
-    for (int s = 0; s < lbm::kGraphChunk; ++s) {
-        cudaError_t e = lbm::launch_step(c, cur, false);
-        if (e != cudaSuccess && le == cudaSuccess) le = e;
-        cur ^= 1;
-    }
-    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
-    if (le != cudaSuccess || ee != cudaSuccess || !g) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        c->graph_failed = true;
-        return LBM_OK;
-    }
-    cudaError_t ie = cudaGraphInstantiate(&c->graph[start], g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) {
-        cudaGetLastError();
-        c->graph[start] = nullptr;
-        c->graph_failed = true;
-    }
+// Capture the step graphs of every size for both starting buffers, once per variant and
+// geometry: a later lbm_step of any length then runs as a few graph launches (largest first) and
+// at most one single launch, with no capture inside it. On any capture failure the context falls
+// back to single launches for good.
+lbm_status capture_graphs(lbm_ctx* c) {
+    if (c->graph_failed || c->graphs_ready) return LBM_OK;
+    for (int start = 0; start < 2; ++start)
+        for (int k = 0; k < lbm::kGraphSizes; ++k) {
+            const int n = lbm::kGraphChunk >> k;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                c->graph_failed = true;
+                destroy_graphs(c);
+                return LBM_OK;
+            }
+            int cur = start;
+            cudaError_t le = cudaSuccess;
+            for (int s = 0; s < n; ++s) {
+                cudaError_t e = lbm::launch_step(c, cur, false);
+                if (e != cudaSuccess && le == cudaSuccess) le = e;
+                cur ^= 1;
+            }
+            cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+            cudaError_t ie = cudaErrorUnknown;
+            if (le == cudaSuccess && ee == cudaSuccess && g)
+                ie = cudaGraphInstantiate(&c->graph[start][k], g, 0);
+            // move the one-time device upload here, out of the first lbm_step that uses it
+            if (ie == cudaSuccess) ie = cudaGraphUpload(c->graph[start][k], c->stream);
+            if (g) cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                cudaGetLastError();
+                c->graph[start][k] = nullptr;
+                c->graph_failed = true;
+                destroy_graphs(c);
+                return LBM_OK;
+            }
+        }
+    c->graphs_ready = true;
     return LBM_OK;
 }
 
@@ -404,31 +425,32 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     LBM_CUDA(c, cudaMemsetAsync(c->muw, 0, c->plane * c->esz, c->stream));
     LBM_CUDA(c, cudaMemsetAsync(c->linkmask, 0, c->plane, c->stream));
     LBM_CUDA(c, lbm::launch_geometry(c, a));
-    // captured step graphs hold the previous boundary scheme
-    for (int k = 0; k < 2; ++k) {
-        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
-        c->graph[k] = nullptr;
-    }
-    c->ibb = g->boundary == LBM_BB_INTERP;
+    // captured step graphs stay valid across geometries (the kernels read the same buffers);
+    // they hold the boundary scheme and the variant, so a change of either drops them
+    const bool ibb = g->boundary == LBM_BB_INTERP;
+    if (ibb != c->ibb) destroy_graphs(c);
+    c->ibb = ibb;
     if (c->ibb) {
-        if (!c->dlt) LBM_CUDA(c, cudaMalloc(&c->dlt, 8 * c->plane * c->esz));
+        if (!c->dlt) {
+            destroy_graphs(c);
+            LBM_CUDA(c, cudaMalloc(&c->dlt, 8 * c->plane * c->esz));
+        }
         LBM_CUDA(c, lbm::launch_link_fractions(c, a));
         // the interpolated scheme is compiled for the default tile variant only
         if (!lbm::step_has_ibb(c->esz, c->tile_x, c->tile_y, c->min_blocks)) {
+            destroy_graphs(c);
             c->tile_x = 32;
             c->tile_y = 16;
             c->min_blocks = c->esz == 4 ? 5 : 0;
             LBM_CUDA(c, lbm::step_configure(c));
         }
     }
-    double* d_rho0 = nullptr;
     if (g->rho0) {
         const size_t nb = sizeof(double) * (size_t)c->nx * c->ny;
-        LBM_CUDA(c, cudaMalloc((void**)&d_rho0, nb));
-        cudaError_t e = cudaMemcpyAsync(d_rho0, g->rho0, nb, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = lbm::launch_init_state(c, *g, d_rho0);
+        if (!c->stage) LBM_CUDA(c, cudaMalloc((void**)&c->stage, nb));
+        cudaError_t e = cudaMemcpyAsync(c->stage, g->rho0, nb, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = lbm::launch_init_state(c, *g, c->stage);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFree(d_rho0);
         if (e != cudaSuccess)
             return fail(c, LBM_ERR_CUDA, std::string("lbm_set_geometry: ") + cudaGetErrorString(e));
     } else {
@@ -472,10 +494,13 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
         c->cur ^= 1;
         --left;
     }
-    if (left >= lbm::kGraphChunk && !c->graph[c->cur] && !c->graph_failed) capture_graph(c, c->cur);
-    while (left >= lbm::kGraphChunk && c->graph[c->cur]) {
-        LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
-        left -= lbm::kGraphChunk;  // even chunk: parity of c->cur unchanged
+    if (left >= 2 && !c->graphs_ready && !c->graph_failed) capture_graphs(c);
+    for (int k = 0; c->graphs_ready && k < lbm::kGraphSizes; ++k) {
+        const int n = lbm::kGraphChunk >> k;
+        while (left >= n) {
+            LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur][k], c->stream));
+            left -= n;  // even chunk: parity of c->cur unchanged
+        }
     }
     for (; left > 0; --left) {
         LBM_CUDA(c, lbm::launch_step(c, c->cur, false));
@@ -543,10 +568,7 @@ lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, lbm_tune_entry* entries
     LBM_CUDA(c, err);
     LBM_CUDA(c, lbm::step_configure(c));
     // the captured graphs hold the previous variant
-    for (int k = 0; k < 2; ++k) {
-        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
-        c->graph[k] = nullptr;
-    }
+    destroy_graphs(c);
     if (n_out) *n_out = (int32_t)vs.size();
     return LBM_OK;
 }
@@ -595,8 +617,8 @@ lbm_status lbm_read_fields(lbm_ctx* c, uint32_t which, double* rho, double* ux, 
         return fail(c, LBM_ERR_ARG, "lbm_read_fields: NULL buffer for a requested field");
     DeviceGuard dg(c->device);
     const bool dev = (which & LBM_FIELD_DEVICE_DST) != 0;
-    double* tmp = nullptr;
-    if (!dev) LBM_CUDA(c, cudaMalloc((void**)&tmp, sizeof(double) * N));
+    if (!dev && !c->stage) LBM_CUDA(c, cudaMalloc((void**)&c->stage, sizeof(double) * N));
+    double* tmp = dev ? nullptr : c->stage;
     auto emit = [&](const void* src, double* dst) -> cudaError_t {
         double* target = dev ? dst : tmp;
         cudaError_t e = lbm::launch_to_double(c, src, target, 0);
@@ -615,7 +637,6 @@ lbm_status lbm_read_fields(lbm_ctx* c, uint32_t which, double* rho, double* ux, 
         if (e == cudaSuccess) e = emit((const char*)c->vel + c->plane * c->esz, uy);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (tmp) cudaFree(tmp);
     if (e != cudaSuccess)
         return fail(c, LBM_ERR_CUDA, std::string("lbm_read_fields: ") + cudaGetErrorString(e));
     return LBM_OK;

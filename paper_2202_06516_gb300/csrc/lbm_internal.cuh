@@ -124,8 +124,11 @@ struct lbm_ctx {
     int red_blocks = 0;
     // velocity scratch for lbm_read_fields
     void* vel = nullptr;
-    // graphs of GRAPH_CHUNK steps starting from buffer 0 / buffer 1
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // nx * ny doubles staging host transfers (initial density in, fields out), kept between calls
+    double* stage = nullptr;
+    // graphs of kGraphChunk >> k steps (k = 0 .. kGraphSizes - 1) starting from buffer 0 / 1
+    cudaGraphExec_t graph[2][6] = {};
+    bool graphs_ready = false;
     bool graph_failed = false;
     int tile_x = 32, tile_y = 16, min_blocks = 0;
     bool autotune_pending = false;  // LBM_TILE_AUTO: tune at the first lbm_step
@@ -134,7 +137,8 @@ struct lbm_ctx {
 
 namespace lbm {
 
-constexpr int kGraphChunk = 64;   // steps per captured graph (even: ping-pong parity preserved)
+constexpr int kGraphChunk = 64;   // steps in the largest captured graph
+constexpr int kGraphSizes = 6;    // graphs of 64, 32, 16, 8, 4, 2 steps (even: parity preserved)
 constexpr int kRedThreads = 256;
 constexpr int kAutotuneTrial = 20;  // timed launches per variant when LBM_TILE_AUTO tunes
 

@@ -179,17 +179,26 @@ def lbm_measure_contact_angle(ctx):
     return st, [out[0], out[1]]
 
 
-def lbm_read_fields(ctx, which: int, nx: int, ny: int, device_out=None):
+def lbm_read_fields(ctx, which: int, nx: int, ny: int, device_out=None, host_out=None):
     """Host arrays (ny, nx) of density / velocity; device_out = (rho, ux, uy) device pointers
-    (e.g. torch tensors' data_ptr()) writes on the device instead and returns None."""
+    (e.g. torch tensors' data_ptr()) writes on the device instead and returns None; host_out =
+    (rho, ux, uy) caller-owned C-contiguous float64 (ny, nx) host arrays (None where not
+    requested), e.g. views of pinned memory, to write into instead of new arrays."""
     n = nx * ny
     if device_out is not None:
         r, u, v = device_out
         _check(lib().lbm_read_fields(ctx, which | LBM_FIELD_DEVICE_DST, r, u, v, n), ctx)
         return None
-    rho = np.zeros((ny, nx)) if which & LBM_FIELD_RHO else None
-    ux = np.zeros((ny, nx)) if which & LBM_FIELD_VEL else None
-    uy = np.zeros((ny, nx)) if which & LBM_FIELD_VEL else None
+    if host_out is not None:
+        for a in host_out:
+            if a is not None and not (a.dtype == np.float64 and a.flags.c_contiguous and
+                                      a.size == n):
+                raise ValueError("host_out arrays must be C-contiguous float64 of nx * ny")
+        rho, ux, uy = host_out
+    else:
+        rho = np.zeros((ny, nx)) if which & LBM_FIELD_RHO else None
+        ux = np.zeros((ny, nx)) if which & LBM_FIELD_VEL else None
+        uy = np.zeros((ny, nx)) if which & LBM_FIELD_VEL else None
     ptr = lambda a: a.ctypes.data if a is not None else None
     _check(lib().lbm_read_fields(ctx, which, ptr(rho), ptr(ux), ptr(uy), n), ctx)
     return rho, ux, uy
@@ -351,8 +360,10 @@ class Lattice:
         st, (l, r) = lbm_measure_contact_angle(self.ctx)
         return _angle(l), _angle(r)
 
-    def rho(self):
-        return lbm_read_fields(self.ctx, LBM_FIELD_RHO, self.nx, self.ny)[0]
+    def rho(self, out=None):
+        """Density (ny, nx); out: a caller-owned float64 host array to fill (e.g. pinned)."""
+        return lbm_read_fields(self.ctx, LBM_FIELD_RHO, self.nx, self.ny,
+                               host_out=None if out is None else (out, None, None))[0]
 
     def velocity(self):
         _, ux, uy = lbm_read_fields(self.ctx, LBM_FIELD_VEL, self.nx, self.ny)

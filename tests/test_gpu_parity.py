@@ -149,15 +149,46 @@ def test_small_periodic_domain(lbm, oracle_mod):
 
 
 def test_graph_chunks_equal_single_launches(lbm, oracle_mod):
-    """Steps replayed from the captured graph equal steps launched one by one (bitwise)."""
+    """Steps replayed from the captured graphs (64, 32, ..., 2 steps from either buffer) equal
+    steps launched one by one (bitwise), for step counts that use every graph size and both
+    starting buffers."""
     O = oracle_mod
     cfg = _cfg(O, nx=96, ny=64, cx=48, R=20, drop_x=48, drop_y=34.5, drop_r=14)
     a = gpu_lattice(lbm, cfg)
     b = gpu_lattice(lbm, cfg)
-    a.step(128 + 3)           # two graph chunks + 3 single launches
-    for _ in range(131):
-        b.step(1)
-    assert np.array_equal(a.rho(), b.rho())
+    total = 0
+    for n in (128 + 3, 37, 126, 1, 20, 63):  # 64+64+2+1, 32+4+1, 64+32+16+8+4+2, 1, 16+4, ...
+        a.step(n)
+        total += n
+        for _ in range(n):
+            b.step(1)
+        assert np.array_equal(a.rho(), b.rho()), n
+    assert a.info().steps == b.info().steps == total
+
+
+def test_new_geometry_on_a_used_context(lbm, oracle_mod):
+    """A context that has stepped (and captured its step graphs) and then gets a new geometry,
+    with the same or the interpolated boundary scheme, steps bit for bit like a fresh context
+    given that geometry."""
+    O = oracle_mod
+    first = _cfg(O, nx=96, ny=64, cx=48, R=20, drop_x=48, drop_y=34.5, drop_r=14)
+    second = _cfg(O, nx=96, ny=64, cx=40, R=16, drop_x=40, drop_y=16.5 + 12, drop_r=12)
+    lat = gpu_lattice(lbm, first)
+    lat.step(70)
+    for cfg in (second, first):
+        for interp in (0, 1):
+            cfg.interp_bb = interp
+            lat.set_geometry(circle=(cfg.cx, cfg.cy, cfg.R), mu_circle=cfg.mu_circle,
+                             mu_bottom=cfg.mu_bottom, mu_top=cfg.mu_top,
+                             drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W),
+                             boundary=interp)
+            fresh = gpu_lattice(lbm, cfg)
+            lat.step(75)
+            fresh.step(75)
+            assert np.array_equal(lat.rho(), fresh.rho()), (cfg.cx, interp)
+            fresh.close()
+        cfg.interp_bb = 0
+    lat.close()
 
 
 def _concave_cfg(O):
@@ -399,6 +430,12 @@ def test_stream_from_torch(lbm, oracle_mod):
     lbm.lbm_read_fields(a.ctx, lbm.LBM_FIELD_RHO, 96, 64, device_out=(r.data_ptr(), None, None))
     torch.cuda.synchronize()
     assert np.array_equal(r.cpu().numpy().reshape(64, 96), a.rho())
+    # caller-owned (pinned) host destination
+    pinned = torch.zeros((64, 96), dtype=torch.float64, pin_memory=True).numpy()
+    got = a.rho(out=pinned)
+    assert got is pinned and np.array_equal(pinned, a.rho())
+    with pytest.raises(ValueError):
+        a.rho(out=np.zeros((64, 96), dtype=np.float32))
 
 
 # -------------------------------------------------------------------- other model options
