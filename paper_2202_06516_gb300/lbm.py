@@ -553,6 +553,15 @@ def lbm_sg_inject_timeout():
     _scheck(_sg_sig().lbm_sg_inject_timeout())
 
 
+def _torch_inputs_ready():
+    """The surrogate runs on its own stream: make sure work that torch queued on its current
+    stream (the copies and casts that produced the device inputs) has finished first."""
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+        torch.cuda.current_stream().synchronize()
+
+
 class Surrogate:
     """The warm-start U-Net on an H x W lattice (device inputs are torch tensors' pointers)."""
 
@@ -587,9 +596,11 @@ class Surrogate:
         return w
 
     def forward(self, x_ptr, B, phi_ptr):
+        _torch_inputs_ready()
         _scheck(_sg_sig().lbm_surrogate_forward(self.s, x_ptr, B, phi_ptr), self.s)
 
     def train_step(self, x_ptr, target_ptr, mask_ptr, B, lr) -> float:
+        _torch_inputs_ready()
         loss = C.c_double()
         _scheck(_sg_sig().lbm_surrogate_train_step(self.s, x_ptr, target_ptr, mask_ptr, B,
                                                    float(lr), C.byref(loss)), self.s)

@@ -141,17 +141,16 @@ def train(sur, x, t, m, epochs=20, batch=8, lr=1e-3, seed=0, log=None, schedule=
 
 
 def predict(sur, x, batch=8):
+    """phi for inputs x (n, H, W, 8) float32, `batch` cases per forward call; each chunk goes to
+    the device as FP32 and is converted to BF16 there."""
     import torch
     n = x.shape[0]
-    out = np.zeros((n, x.shape[1], x.shape[2]), dtype=np.float32)
-    xd = torch.tensor(x).to(torch.bfloat16).cuda()
-    phi = torch.zeros((batch, x.shape[1], x.shape[2]), dtype=torch.float32, device="cuda")
+    out = torch.zeros((n, x.shape[1], x.shape[2]), dtype=torch.float32, device="cuda")
     for k in range(0, n, batch):
         bb = min(batch, n - k)
-        xb = xd[k:k + bb].contiguous()
-        sur.forward(xb.data_ptr(), bb, phi.data_ptr())
-        out[k:k + bb] = phi[:bb].cpu().numpy()
-    return out
+        xb = torch.from_numpy(np.ascontiguousarray(x[k:k + bb])).cuda().to(torch.bfloat16)
+        sur.forward(xb.contiguous().data_ptr(), bb, out[k:k + bb].data_ptr())
+    return out.cpu().numpy()
 
 
 def match_mass(phi, mask, target_mass, rho_g, rho_l, rtol=1e-12):
@@ -260,12 +259,16 @@ def evaluate(sur, ws, steps=20000, every=250, log=None, plain=True):
         fluid.append(lbm.lbm_read_geometry(ctx, w.nx, w.ny)[0][2:-2] == 0)
     hc, tc = angle_histories(bc, len(ws), steps, every)
     bc.close()
+    # the warm batch's lattices exist before the clock starts, as the cold batch's did; the
+    # clock covers the prediction, the mass matching and setting the predicted initial states
+    bw, _, _ = make_batch(ws)
     t0 = time.perf_counter()
     phi = predict(sur, x).astype(np.float64)
     phi = np.stack([match_mass(phi[i], fluid[i], masses[i], co["rho_g"], co["rho_l"])
                     for i in range(len(ws))])
     rho0 = co["rho_g"] + phi * (co["rho_l"] - co["rho_g"])
-    bw, _, _ = make_batch(ws, rho0=rho0)
+    for i, w in enumerate(ws):
+        bw.set_geometry(i, **_geometry(w, neutral), rho0=rho0[i])
     t_pred = time.perf_counter() - t0
     hw, tw = angle_histories(bw, len(ws), steps, every)
     bw.close()
