@@ -151,15 +151,32 @@ def _cos(a, b):
 CASES = [(8, 32), (8, 48), (16, 64), (32, 64)]  # base, resolution (48: not a power of two)
 
 
+def _fp32_yardstick(pw, xb, t, m, base):
+    """The oracle's BF16-storage network evaluated in FP32 on the CPU (same BF16 inputs and
+    weights): how far FP32 arithmetic alone moves the gradients from the FP64 evaluation."""
+    import torch
+    from oracle import surrogate as S
+    pt = torch.tensor(pw.astype(np.float32), requires_grad=True)
+    loss, _ = S.loss_fn(pt, torch.tensor(xb.astype(np.float32)), torch.tensor(t),
+                        torch.tensor(m.astype(bool)), base, True, True)
+    loss.backward()
+    return pt.grad.double().numpy()
+
+
 @pytest.mark.parametrize("regime", ["positive", "negative"])
 @pytest.mark.parametrize("base,H", CASES)
 def test_gradients_match_bf16_oracle_per_layer(env, base, H, regime):
-    """Every layer's weight and bias gradient within 1.5e-2 (relative, per layer) of the oracle
-    that stores activations and pre-activation gradients in BF16 as the GPU does, with weights
-    chosen so that every pre-activation keeps one sign with a wide margin (positive: weights
-    x 0.1, biases +1; negative: weights x 0.25, biases -1; margin checked in the oracle). Away
-    from the leaky-ReLU kink the only differences left are FP32 against FP64 accumulation and
-    the BF16 rounding decisions they move (measured worst layer: 1.2e-2); the forward pass then
+    """Every layer's weight and bias gradient against the oracle that stores activations and
+    pre-activation gradients in BF16 as the GPU does, with weights chosen so that every
+    pre-activation keeps one sign with a wide margin (positive: weights x 0.1, biases +1;
+    negative: weights x 0.25, biases -1; margin checked in the oracle). Away from the leaky-ReLU
+    kink the differences left are FP32 against FP64 accumulation and the BF16 rounding decisions
+    they move, amplified through the 17 layers. The same oracle evaluated in FP32 on the CPU
+    shows that amplification: it departs from the FP64 evaluation by up to 1.1e-2 per layer in
+    these regimes, with the same per-layer profile as the GPU. So each layer must be within the
+    1e-2 relative bound for BF16 gradients, or, where FP32 arithmetic itself does not reach that
+    bound, within twice the FP32 evaluation's own departure; 1.5e-2 caps both (measured GPU
+    worst 1.25e-2 with the FP32 evaluation at 1.08e-2 on that layer's case). The forward pass
     agrees to ~1e-7 and the head gradient to 1e-4. The oracle without the gradient rounding is
     farther from the GPU, so that mode is what the GPU computes."""
     torch, _ = env
@@ -180,11 +197,13 @@ def test_gradients_match_bf16_oracle_per_layer(env, base, H, regime):
     assert np.abs(gpu["phi"] - full["phi"]).max() < 5e-4
     assert gpu["loss"] == pytest.approx(full["loss"], rel=1e-5)
     assert _rel(gpu["g"][head], full["g"][head]) < 1e-3
+    g32 = _fp32_yardstick(pw, xb, t, m, base)
     errs = []
     for k, (sw, sb) in enumerate(layers):
         ew, eb = _rel(gpu["g"][sw], full["g"][sw]), _rel(gpu["g"][sb], full["g"][sb])
+        yard = max(_rel(g32[sw], full["g"][sw]), _rel(g32[sb], full["g"][sb]))
         errs.append(max(ew, eb))
-        assert ew < 1.5e-2 and eb < 1.5e-2, (k, ew, eb)
+        assert max(ew, eb) < min(1.5e-2, max(1e-2, 2.0 * yard)), (k, ew, eb, yard)
     act_only = [max(_rel(gpu["g"][sw], ref["act"]["g"][sw]), _rel(gpu["g"][sb], ref["act"]["g"][sb]))
                 for sw, sb in layers]
     assert sum(errs) < sum(act_only)
