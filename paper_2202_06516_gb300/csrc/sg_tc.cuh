@@ -479,6 +479,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                     float bn[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
+                    // destination of row it * 4 + lane / 8; with accumulation all eight old
+                    // values are loaded before the first store, so their latencies overlap
+                    auto dst_of = [&](int it) {
+                        const int m = m0 + warp * 32 + it * 4 + (lane >> 3);
+                        return (g.Cf2 && n >= g.nsplit)
+                                   ? reinterpret_cast<float4*>(g.Cf2 + (size_t)m * g.ldc2 +
+                                                               (n - g.nsplit))
+                                   : reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n);
+                    };
+                    float4 old[8];
+                    if (g.accumulate) {
+#pragma unroll
+                        for (int it = 0; it < 8; ++it) {
+                            const int m = m0 + warp * 32 + it * 4 + (lane >> 3);
+                            old[it] = m < g.M ? *dst_of(it) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
 #pragma unroll
                     for (int it = 0; it < 8; ++it) {
                         const int r = it * 4 + (lane >> 3), m = m0 + warp * 32 + r;
@@ -494,18 +511,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
                             x.z = fmaxf(x.z, 0.1f * x.z);
                             x.w = fmaxf(x.w, 0.1f * x.w);
                         }
-                        float4* dst =
-                            (g.Cf2 && n >= g.nsplit)
-                                ? reinterpret_cast<float4*>(g.Cf2 + (size_t)m * g.ldc2 + (n - g.nsplit))
-                                : reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n);
                         if (g.accumulate) {
-                            const float4 o = *dst;
-                            x.x += o.x;
-                            x.y += o.y;
-                            x.z += o.z;
-                            x.w += o.w;
+                            x.x += old[it].x;
+                            x.y += old[it].y;
+                            x.z += old[it].z;
+                            x.w += old[it].w;
                         }
-                        *dst = x;
+                        *dst_of(it) = x;
                     }
                 }
             } else {
