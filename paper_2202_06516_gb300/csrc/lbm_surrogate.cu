@@ -401,19 +401,23 @@ cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits) {
 // wide tiles keep two stages so that two CTAs share an SM and one's epilogue overlaps the
 // other's MMAs. GA / GAM: A (K-major / MN-major) is the implicit im2col of a.conv; GD: A is the
 // gathered data-gradient operand a.dg.
-template <bool AMN, bool BMN, bool GA = false, bool GD = false, bool GAM = false>
-cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
+int pick_bn(int N) {
     static const int widths[] = {32, 64, 80, 128, 144, 192, 256};
     int best = 256, best_cols = 1 << 30, best_tiles = 1 << 30;
     for (int w : widths) {
-        const int tiles = (a.N + w - 1) / w, cols = tiles * w;
+        const int tiles = (N + w - 1) / w, cols = tiles * w;
         if (cols < best_cols || (cols == best_cols && tiles < best_tiles)) {
             best = w;
             best_cols = cols;
             best_tiles = tiles;
         }
     }
-    switch (best) {
+    return best;
+}
+
+template <bool AMN, bool BMN, bool GA = false, bool GD = false, bool GAM = false>
+cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
+    switch (pick_bn(a.N)) {
         case 32: return launch_tc<32, 3, AMN, BMN, GA, GD, GAM>(st, a, splits);
         case 64: return launch_tc<64, 3, AMN, BMN, GA, GD, GAM>(st, a, splits);
         case 80: return launch_tc<80, 4, AMN, BMN, GA, GD, GAM>(st, a, splits);
@@ -422,6 +426,45 @@ cudaError_t gemm_tc(cudaStream_t st, const GemmArgs& a, int splits = 1) {
         case 192: return launch_tc<192, 2, AMN, BMN, GA, GD, GAM>(st, a, splits);
         default: return launch_tc<256, 2, AMN, BMN, GA, GD, GAM>(st, a, splits);
     }
+}
+
+// The gathering GEMMs (GA: forward convolution, GD: data gradient) with fewer output tiles than
+// about three quarters of the SMs (the coarse levels): K is cut into up to 2 x 152 / tiles ranges
+// of whole 64-wide slices, at least four each, whose FP32 partials k_splitk_finish sums in a
+// fixed order before applying the GEMM's own epilogue (bias, leaky ReLU, BF16 or accumulated
+// FP32 stores). Otherwise one launch as usual.
+template <bool GA, bool GD>
+cudaError_t gemm_tc_split(cudaStream_t st, const GemmArgs& a, float* scratch,
+                          size_t scratch_elems) {
+    const int bn = pick_bn(a.N);
+    const long long tiles =
+        (long long)((a.N + bn - 1) / bn) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
+    const int nkt = (a.K + lbm::sgtc::BK - 1) / lbm::sgtc::BK;
+    long long splits = 1;
+    if (tiles < 114 && a.N % 4 == 0 && !a.tout && !a.kchunk)
+        splits = std::min<long long>(2 * 152 / tiles, nkt / 4);
+    while (splits > 1 && (size_t)splits * a.M * a.N > scratch_elems) --splits;
+    if (splits <= 1) return gemm_tc<false, false, GA, GD>(st, a);
+    const int chunk = (int)((nkt + splits - 1) / splits) * lbm::sgtc::BK;
+    const int nsp = (a.K + chunk - 1) / chunk;
+    GemmArgs p = a;
+    p.Cf = scratch;
+    p.Cb = nullptr;
+    p.Cf2 = nullptr;
+    p.ldc = a.N;
+    p.ldc2 = 0;
+    p.nsplit = 0;
+    p.bias = nullptr;
+    p.relu = 0;
+    p.accumulate = 0;
+    p.kchunk = chunk;
+    p.split_stride = (long long)a.M * a.N;
+    cudaError_t e = gemm_tc<false, false, GA, GD>(st, p, nsp);
+    if (e != cudaSuccess) return e;
+    k_splitk_finish<<<blocks_for((long long)a.M * a.N / 4), kT, 0, st>>>(
+        scratch, nsp, a.M, a.N, a.bias, a.relu, a.Cb, a.Cf, a.ldc, a.Cf2, a.ldc2, a.nsplit,
+        a.accumulate);
+    return cudaGetLastError();
 }
 
 // AK / BK: operand stored K-major (else MN-major)
@@ -448,8 +491,12 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
         t.tout = 1;
         a = t;
     }
-    const int tiles = ((a.N + 255) / 256) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
-    int splits = std::max(1, std::min(128, 2 * 152 / std::max(1, tiles)));
+    // enough K slices for every SM to hold as many CTAs as fit (three of the narrow tiles, two
+    // of the wide ones): each CTA keeps only two K-slices of gathers in flight
+    const int bn = pick_bn(a.N);
+    const int tiles = ((a.N + bn - 1) / bn) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
+    const int occ = bn <= 64 ? 3 : 2;
+    int splits = std::max(1, std::min(128, occ * 152 / std::max(1, tiles)));
     const long long stride = gather ? (long long)a.N * a.ldc : (long long)a.M * a.ldc;
     while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
     if (splits == 1) {
@@ -590,7 +637,7 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         g.ldc = c.Cout;
         g.bias = s->w + c.b_off;
         g.relu = 1;
-        SCUDA(s, (gemm_tc<false, false, true>(s->stream, g)));
+        SCUDA(s, (gemm_tc_split<true, false>(s->stream, g, s->splitk, s->splitk_elems)));
         // a pool whose source is this conv's output runs right after it
         for (const auto& pl : s->pools)
             if (pl.first == c.out) {
@@ -845,7 +892,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
             gd.ldc2 = c.C2;
             gd.nsplit = c.C1;
         }
-        SCUDA(s, (gemm_tc<false, false, false, true>(s->stream, gd)));
+        SCUDA(s, (gemm_tc_split<false, true>(s->stream, gd, s->splitk, s->splitk_elems)));
     }
     if (lr > 0.f) {
         ++s->adam_t;

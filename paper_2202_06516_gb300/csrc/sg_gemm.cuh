@@ -89,5 +89,58 @@ __global__ void k_splitk_sum(const float* part, int splits, long long stride, lo
         out[i] = s;
     }
 }
+
+// Finish a split-K GEMM whose FP32 partials part[z][m][n] (row length N, splits stride M N)
+// were written by the K-ranges z = 0 .. splits - 1: the sum in order z = 0, 1, ..., then the
+// epilogue of the unsplit GEMM (bias, leaky ReLU, BF16 store to Cb, or FP32 store / accumulation
+// to Cf, columns n >= nsplit to Cf2). Four consecutive columns per thread (N % 4 == 0).
+__global__ void k_splitk_finish(const float* part, int splits, int M, int N, const float* bias,
+                                int relu, __nv_bfloat16* Cb, float* Cf, int ldc, float* Cf2,
+                                int ldc2, int nsplit, int accumulate) {
+    const long long stride = (long long)M * N, n4 = stride / 4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long e = 4 * i;
+        const int m = (int)(e / N), n = (int)(e - (long long)m * N);
+        float4 x = reinterpret_cast<const float4*>(part + e)[0];
+        for (int z = 1; z < splits; ++z) {
+            const float4 y = reinterpret_cast<const float4*>(part + (size_t)z * stride + e)[0];
+            x.x += y.x;
+            x.y += y.y;
+            x.z += y.z;
+            x.w += y.w;
+        }
+        if (bias) {
+            x.x += bias[n];
+            x.y += bias[n + 1];
+            x.z += bias[n + 2];
+            x.w += bias[n + 3];
+        }
+        if (relu) {
+            x.x = fmaxf(x.x, 0.1f * x.x);
+            x.y = fmaxf(x.y, 0.1f * x.y);
+            x.z = fmaxf(x.z, 0.1f * x.z);
+            x.w = fmaxf(x.w, 0.1f * x.w);
+        }
+        if (Cb) {
+            __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(Cb + (size_t)m * ldc + n);
+            o[0] = __floats2bfloat162_rn(x.x, x.y);
+            o[1] = __floats2bfloat162_rn(x.z, x.w);
+            continue;
+        }
+        float* o = (Cf2 && n >= nsplit) ? Cf2 + (size_t)m * ldc2 + (n - nsplit)
+                                        : Cf + (size_t)m * ldc + n;
+        if (accumulate) {
+            x.x += o[0];
+            x.y += o[1];
+            x.z += o[2];
+            x.w += o[3];
+        }
+        o[0] = x.x;
+        o[1] = x.y;
+        o[2] = x.z;
+        o[3] = x.w;
+    }
+}
 }  // namespace sg
 }  // namespace lbm
