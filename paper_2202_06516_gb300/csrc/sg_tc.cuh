@@ -17,6 +17,7 @@
 // CTA sets *err, waits (bounded) for the MMAs it issued, frees its tensor memory and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -40,7 +41,7 @@ struct TcShape {
     static constexpr int B_BYTES = BMN ? (BN + 63) / 64 * 64 * BK * 2 : BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     // 1 KB alignment slack for the swizzle atoms, then the stages, mbarriers and the TMEM slot
-    static constexpr int RAW_BYTES = 1024 + STAGES * STAGE_BYTES + 8 * (STAGES + 1) + 16;
+    static constexpr int RAW_BYTES = 1024 + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1) + 16;
     // at least enough shared memory that the CTAs resident on one SM never ask for more than
     // the 512 tensor-memory columns together (an allocation beyond them would wait)
     static constexpr int TMEM_CTAS = 512 / tmem_cols(BN);
@@ -111,6 +112,31 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+// the mbarrier expects `bytes` more transaction bytes (one arrival)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// tiled tensor copies global -> shared, completion counted on an mbarrier; coordinates are
+// innermost first, out-of-range elements are zero-filled
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
 
@@ -272,16 +298,25 @@ __device__ __forceinline__ void load_slice_mn_conv_a(uint8_t* s, const sg::ConvG
 // GA: A is the gathered convolution operand (K-major, rows = output pixels); GD: A is the
 // gathered data-gradient operand; GAM: A is the gathered convolution operand MN-major (K =
 // pixels, M = im2col columns).
+// TMA: (with GA or GD, both operands K-major) thread 0 alone feeds the stages with tiled tensor
+// copies: A as one box of 64 channels x the tile's tbh x tbw pixels of the activation (GA; the
+// tap's offset applied to the box origin, x1 or x2 by channel) or of the output gradient (GD, the
+// offset negated), out-of-image pixels zero-filled by the copy itself; B as a 64 x BN box of the
+// weight matrix. Stage s completes on full[s] (transaction bytes), is released by the MMAs'
+// commit to empty[s], and STAGES slices are in flight.
 template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GD = false,
-          bool GAM = false>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g, int* err) {
+          bool GAM = false, bool TMA = false>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const sg::GemmArgs g, int* err, const __grid_constant__ CUtensorMap tmA1,
+              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB) {
+    static_assert(!TMA || ((GA || GD) && !AMN && !BMN), "TMA feeds the K-major gathers only");
     using S = TcShape<BN, STAGES, BMN>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     // 1 KB-aligned base of the stages (the swizzle pattern follows shared-memory address bits)
     const uint32_t raw = su32(smem_raw);
     uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * S::STAGE_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -297,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s <= STAGES; ++s) mbar_init(su32(bars + s), 1);
+        for (int s = 0; s <= 2 * STAGES; ++s) mbar_init(su32(bars + s), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_ok = 1;
     }
@@ -348,12 +383,77 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
             load_slice<BN>(stage_b(s), g.B, g.ldb, n0, g.N, k0, ke, g.kperiod);
     };
 
+    bool ok = true;
+    if constexpr (TMA) {
+        // tile origin: n, y0, x0 of the first of the 128 pixels (a tbh x tbw block)
+        const int TH = GA ? g.conv.H : g.dg.H, TW = GA ? g.conv.W : g.dg.W;
+        const int img = m0 / (TH * TW), rem = m0 - img * (TH * TW);
+        const int y0 = rem / TW, x0 = rem - (rem / TW) * TW;
+        const int lk = GA ? g.conv.lc : g.dg.lco;
+        auto issue = [&](int st, int k0) {
+            const uint32_t full = su32(bars + st);
+            mbar_expect_tx(full, (uint32_t)(S::A_BYTES + S::B_BYTES));
+            const int tap = k0 >> lk, ch = k0 & ((1 << lk) - 1);
+            const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+            if (GA) {
+                if (ch < g.conv.C1)
+                    tma_load_4d(su32(stage_a(st)), &tmA1, full, ch, x0 + dx, y0 + dy, img);
+                else
+                    tma_load_4d(su32(stage_a(st)), &tmA2, full, ch - g.conv.C1, x0 + dx, y0 + dy,
+                                img);
+            } else {
+                tma_load_4d(su32(stage_a(st)), &tmA1, full, ch, x0 - dx, y0 - dy, img);
+            }
+            tma_load_2d(su32(stage_b(st)), &tmB, full, k0, n0);
+        };
+        if (tid == 0) {
+            int issued = 0, done_mma = 0;
+            bool good = true;
+            for (; issued < STAGES && issued < nk; ++issued) issue(issued, kb + issued * BK);
+            for (int kt = 0; kt < nk; ++kt) {
+                const int st = kt % STAGES;
+                if (!mbar_wait(su32(bars + st), (kt / STAGES) & 1)) {
+                    good = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = su32(stage_a(st)), b0 = su32(stage_b(st));
+#pragma unroll
+                for (int j = 0; j < BK / 16; ++j)
+                    tc_mma(tmem, desc_sw128(a0 + 32 * j), desc_sw128(b0 + 32 * j), IDESC,
+                           (kt > 0 || j > 0) ? 1u : 0u);
+                tc_commit(su32(bars + STAGES + st));
+                done_mma = kt + 1;
+                // refill the stage that slice kt - 1 used once its MMAs have read it
+                if (kt >= 1 && issued < nk) {
+                    const int sp = (kt - 1) % STAGES;
+                    if (!mbar_wait(su32(bars + STAGES + sp), ((kt - 1) / STAGES) & 1)) {
+                        good = false;
+                        break;
+                    }
+                    issue(sp, kb + issued * BK);
+                    ++issued;
+                }
+            }
+            if (!good) {
+                // let the copies still in flight land before the CTA may leave (bounded)
+                for (int j = done_mma; j < issued; ++j)
+                    mbar_wait(su32(bars + j % STAGES), (j / STAGES) & 1);
+            }
+            if (nk > 0) {
+                tc_commit(su32(bars + 2 * STAGES));
+                if (!mbar_wait(su32(bars + 2 * STAGES), 0)) good = false;
+            }
+            if (!good) s_ok = 0;
+        }
+        __syncthreads();
+        ok = s_ok;
+    } else {
 #pragma unroll 1
     for (int p = 0; p < STAGES - 1; ++p) {
         if (p < nk) load(p, kb + p * BK);
         sg::cp_async_commit();
     }
-    bool ok = true;
 #pragma unroll 1
     for (int kt = 0; kt < nk; ++kt) {
         const int s = kt % STAGES;
@@ -391,11 +491,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const sg::GemmArgs g,
     // completion of every MMA issued (the last commit tracks all earlier ones)
     if (nk > 0) {
         if (tid == 0) {
-            tc_commit(su32(bars + STAGES));
-            if (!mbar_wait(su32(bars + STAGES), 0)) s_ok = 0;
+            tc_commit(su32(bars + 2 * STAGES));
+            if (!mbar_wait(su32(bars + 2 * STAGES), 0)) s_ok = 0;
         }
         __syncthreads();
         ok = ok && s_ok;
+    }
     }
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);

@@ -107,11 +107,12 @@ def _gpu_and_oracle(env, x, t, m, p, base, H):
     s = lbm.Surrogate(H, H, base=base, max_batch=2)
     assert s.n == p.size
     s.set_weights(p)
+    nb = x.shape[0]
     xd = torch.tensor(x).to(torch.bfloat16).cuda()
     td = torch.tensor(t).cuda()
     md = torch.tensor(m).cuda()
-    loss = s.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 2, 0.0)
-    gpu = dict(loss=loss, g=s.weights(grads=True).astype(np.float64), phi=s.phi(2))
+    loss = s.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), nb, 0.0)
+    gpu = dict(loss=loss, g=s.weights(grads=True).astype(np.float64), phi=s.phi(nb))
     s.close()
     pw = _bf16(p)
     convs, n = S.layer_specs(base)
@@ -166,6 +167,18 @@ def _fp32_yardstick(pw, xb, t, m, base):
 @pytest.mark.parametrize("regime", ["positive", "negative"])
 @pytest.mark.parametrize("base,H", CASES)
 def test_gradients_match_bf16_oracle_per_layer(env, base, H, regime):
+    _per_layer_check(env, base, H, regime)
+
+
+def test_tma_fed_levels_at_full_resolution(env):
+    """256 x 256, base 32, one image: the 128 x 128 (64 channels), 64 x 64 and 32 x 32 levels
+    feed their forward and data-gradient GEMMs with tensor-map (TMA) boxes, the 128 x 128 level
+    with single-row boxes of 128 pixels; the per-layer check of
+    test_gradients_match_bf16_oracle_per_layer at that size."""
+    _per_layer_check(env, 32, 256, "positive", B=1)
+
+
+def _per_layer_check(env, base, H, regime, B=2):
     """Every layer's weight and bias gradient against the oracle that stores activations and
     pre-activation gradients in BF16 as the GPU does, with weights chosen so that every
     pre-activation keeps one sign with a wide margin (positive: weights x 0.1, biases +1;
@@ -181,7 +194,7 @@ def test_gradients_match_bf16_oracle_per_layer(env, base, H, regime):
     farther from the GPU, so that mode is what the GPU computes."""
     torch, _ = env
     from oracle import surrogate as S
-    x, t, m, p = _case(base=base, H=H, Wd=H)
+    x, t, m, p = _case(base=base, H=H, Wd=H, B=B)
     scale, bias = (0.1, 1.0) if regime == "positive" else (0.25, -1.0)
     p = p.copy()
     layers, head = _layers(base)
