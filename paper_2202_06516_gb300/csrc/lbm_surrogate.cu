@@ -39,6 +39,7 @@ namespace sg {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kReluBlocks = 1024;  // blocks of the fused leaky-ReLU adjoint / bias-sum pass
 
 int blocks_for(long long n) {
     long long b = (n + kT - 1) / kT;
@@ -114,27 +115,37 @@ __global__ void k_avgpool(const bf16* x, bf16* y, int B, int H, int W, int C) {
     }
 }
 
-// adjoint of k_avgpool, accumulated into the full-resolution gradient
-__global__ void k_avgpool_bwd(const float* dy, float* dx, int B, int H, int W, int C) {
-    const long long total = (long long)B * H * W * C;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(t % C);
-        const long long q = t / C;
-        const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((long long)W * H));
-        dx[t] += 0.25f * dy[(((size_t)n * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c];
-    }
-}
-
-// leaky-ReLU adjoint: g = dy * (y > 0 ? 1 : 0.1) (the output has the sign of its input), as
-// BF16 for the gradient GEMMs; eight elements per thread (n8 groups)
-__global__ void k_relu_mask(const float* dy, const bf16* y, bf16* g, long long n8) {
+// The leaky-ReLU adjoint of one convolution's output fused with what feeds it and what reads
+// it: g = (dy + dyp / 4) * (y > 0 ? 1 : 0.1), stored as BF16 for the gradient GEMMs, where dyp
+// (POOL) is the gradient of the 2 x 2 average pool taken of this output, whose adjoint gives a
+// quarter to each of the four source pixels (added after the other consumers' contributions,
+// as a separate pass would); and the per-block column sums of the stored g (the bias gradient's
+// partials). Thread t always covers the eight channels 8 t mod C (8 x threads per block is a
+// multiple of C), so each block adds its threads' sums per channel in thread order into
+// part[block][c] (deterministic). H, W: the output resolution (even when POOL).
+template <bool POOL>
+__global__ void k_relu_bias(const float* dy, const float* dyp, const bf16* y, bf16* g,
+                            long long n8, int C, int H, int W, float* part) {
+    __shared__ float sred[kT * 8];
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n8;
          t += (long long)gridDim.x * blockDim.x) {
         const uint4 yv = reinterpret_cast<const uint4*>(y)[t];
         const float4 a = reinterpret_cast<const float4*>(dy)[2 * t];
         const float4 b = reinterpret_cast<const float4*>(dy)[2 * t + 1];
-        const float d[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        float d[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        if (POOL) {
+            const long long e = 8 * t, p = e / C;
+            const int c = (int)(e - p * C);
+            const long long q = p / W, n = q / H;
+            const int xx = (int)(p - q * W), yy = (int)(q - n * H);
+            const float4* src = reinterpret_cast<const float4*>(
+                dyp + (((n * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c));
+            const float4 pa = src[0], pb = src[1];
+            const float pv[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) d[j] += 0.25f * pv[j];
+        }
         const __nv_bfloat162* yh = reinterpret_cast<const __nv_bfloat162*>(&yv);
         uint4 out;
         __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&out);
@@ -144,28 +155,21 @@ __global__ void k_relu_mask(const float* dy, const bf16* y, bf16* g, long long n
             const float g0 = yf.x > 0.f ? d[2 * i] : 0.1f * d[2 * i];
             const float g1 = yf.y > 0.f ? d[2 * i + 1] : 0.1f * d[2 * i + 1];
             oh[i] = __floats2bfloat162_rn(g0, g1);
+            const float2 r = __bfloat1622float2(oh[i]);
+            acc[2 * i] += r.x;
+            acc[2 * i + 1] += r.y;
         }
         reinterpret_cast<uint4*>(g)[t] = out;
     }
-}
-
-// column sums of g [P x C] (bias gradient), deterministic: with R = blockDim / C rows per pass,
-// thread (r, c) of block b sums rows b R + r, b R + r + gridDim R, ...; the R partial sums of a
-// column are then added in r order. Requires C <= blockDim.
-__global__ void k_colsum_partial(const bf16* g, long long P, int C, float* part) {
-    __shared__ float sm[kT];
-    const int R = blockDim.x / C;
-    const int r = threadIdx.x / C, c = threadIdx.x - r * C;
-    float s = 0.f;
-    if (r < R)
-        for (long long p = (long long)blockIdx.x * R + r; p < P; p += (long long)gridDim.x * R)
-            s += __bfloat162float(g[p * C + c]);
-    sm[threadIdx.x] = s;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sred[threadIdx.x * 8 + j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < C) {
-        float t = 0.f;
-        for (int k = 0; k < R; ++k) t += sm[k * C + threadIdx.x];
-        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+    // channel c: the threads c / 8 + k C / 8 (k = 0, 1, ...), slot c % 8
+    const int groups = C / 8, reps = blockDim.x / groups;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < reps; ++k) s += sred[(c / 8 + k * groups) * 8 + (c & 7)];
+        part[(size_t)blockIdx.x * C + c] = s;
     }
 }
 
@@ -204,11 +208,20 @@ __global__ void k_head(const bf16* x, const float* w, const float* bptr, float* 
          p += (long long)gridDim.x * blockDim.x) {
         float z = b;
         float xv[C];
+        // the pixel's C channels as 16-byte vectors (C is a multiple of 8)
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            xv[c] = __bfloat162float(x[p * C + c]);
-            z += xv[c] * sw[c];
+        for (int v = 0; v < C / 8; ++v) {
+            const uint4 raw = reinterpret_cast<const uint4*>(x + p * C)[v];
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f2 = __bfloat1622float2(h[i]);
+                xv[8 * v + 2 * i] = f2.x;
+                xv[8 * v + 2 * i + 1] = f2.y;
+            }
         }
+#pragma unroll
+        for (int c = 0; c < C; ++c) z += xv[c] * sw[c];
         const float f = 1.f / (1.f + __expf(-z));
         phi[p] = f;
         if (target) {
@@ -218,10 +231,11 @@ __global__ void k_head(const bf16* x, const float* w, const float* bptr, float* 
             acc[C] += m * e * e * inv_n;
             acc[C + 1] += dz;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                acc[c] += dz * xv[c];
-                dx[p * C + c] = dz * sw[c];
-            }
+            for (int c = 0; c < C; ++c) acc[c] += dz * xv[c];
+#pragma unroll
+            for (int c = 0; c < C; c += 4)
+                reinterpret_cast<float4*>(dx + p * C)[c / 4] =
+                    make_float4(dz * sw[c], dz * sw[c + 1], dz * sw[c + 2], dz * sw[c + 3]);
         }
     }
     if (!target) return;
@@ -312,6 +326,7 @@ struct lbm_surrogate {
     float* part = nullptr;  // reduction partials
     float* phi = nullptr;   // head output
     float* hpart = nullptr;
+    float* bpart = nullptr;   // per-block column sums of the bias gradients
     float* splitk = nullptr;  // split-K partials of the weight gradient
     size_t splitk_elems = 0;
     int part_blocks = 256;
@@ -582,7 +597,10 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     cudaError_t e = gather ? gemm_tc<true, true, false, false, true>(st, a, splits)
                            : gemm_tc<true, true>(st, a, splits);
     if (e != cudaSuccess) return e;
-    k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
+    if (stride % 4 == 0 && ((uintptr_t)out & 15) == 0)
+        k_splitk_sum4<<<blocks_for(stride / 4), kT, 0, st>>>(scratch, splits, stride, stride, out);
+    else
+        k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
     return cudaGetLastError();
 }
 
@@ -795,6 +813,8 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->phi, (size_t)max_batch * H * W * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMalloc((void**)&s->hpart, (size_t)s->part_blocks * (base + 2) * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&s->bpart, (size_t)kReluBlocks * 8 * base * sizeof(float));
     size_t wmax = 0;
     for (const Conv& c : s->convs) wmax = std::max(wmax, (size_t)c.Cout * 9 * (c.C1 + c.C2));
     s->splitk_elems = std::min<size_t>(wmax * 128, (size_t)64 << 20);
@@ -920,22 +940,22 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         const Conv& c = s->convs[ci];
         // gradient arriving at this conv's output also includes the pool path (already added,
         // pools run before: a pool's output gradient is complete once every later conv is done)
+        const float* dyp = nullptr;
         for (const auto& pl : s->pools)
-            if (pl.first == c.out) {
-                const Tensor& src = s->t[pl.first];
-                k_avgpool_bwd<<<blocks_for((long long)B * src.H * src.W * src.C), kT, 0,
-                                s->stream>>>(s->t[pl.second].dy, s->t[pl.first].dy, B, src.H,
-                                             src.W, src.C);
-            }
+            if (pl.first == c.out) dyp = s->t[pl.second].dy;
         Tensor& o = s->t[c.out];
         const int Cin = c.C1 + c.C2;
         const long long Pc = (long long)B * c.H * c.W;
         const long long n_out = Pc * c.Cout;
-        k_relu_mask<<<blocks_for(n_out / 8), kT, 0, s->stream>>>(o.dy, o.y, s->gmask, n_out / 8);
-        // bias gradient
-        const int cb = std::min<long long>(s->part_blocks, Pc);
-        k_colsum_partial<<<cb, kT, 0, s->stream>>>(s->gmask, Pc, c.Cout, s->part);
-        k_colsum_final<<<c.Cout, kT, 0, s->stream>>>(s->part, cb, c.Cout, s->g + c.b_off);
+        // leaky-ReLU adjoint (with the pool's), BF16 copy and the bias gradient's partial sums
+        const int rb = (int)std::min<long long>(kReluBlocks, (n_out / 8 + kT - 1) / kT);
+        if (dyp)
+            k_relu_bias<true><<<rb, kT, 0, s->stream>>>(o.dy, dyp, o.y, s->gmask, n_out / 8,
+                                                        c.Cout, c.H, c.W, s->bpart);
+        else
+            k_relu_bias<false><<<rb, kT, 0, s->stream>>>(o.dy, nullptr, o.y, s->gmask, n_out / 8,
+                                                         c.Cout, c.H, c.W, s->bpart);
+        k_colsum_final<<<c.Cout, kT, 0, s->stream>>>(s->bpart, rb, c.Cout, s->g + c.b_off);
         // weight gradient: dW[co][k] = sum_p g[p][co] col[p][k], the im2col columns gathered by
         // the GEMM's loader when the resolution allows (powers of two), else from a buffer
         GemmArgs gw{};
@@ -1082,6 +1102,7 @@ void lbm_surrogate_destroy(lbm_surrogate* s) {
     cudaFree(s->phi);
     cudaFree(s->hpart);
     cudaFree(s->splitk);
+    cudaFree(s->bpart);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -90,6 +90,23 @@ __global__ void k_splitk_sum(const float* part, int splits, long long stride, lo
     }
 }
 
+// the same sum four consecutive outputs per thread (n and stride multiples of 4)
+__global__ void k_splitk_sum4(const float* part, int splits, long long stride, long long n,
+                              float* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int z = 0; z < splits; ++z) {
+            const float4 v = reinterpret_cast<const float4*>(part + (size_t)z * stride)[i];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        reinterpret_cast<float4*>(out)[i] = s;
+    }
+}
+
 // Finish a split-K GEMM whose FP32 partials part[z][m][n] (row length N, splits stride M N)
 // were written by the K-ranges z = 0 .. splits - 1: the sum in order z = 0, 1, ..., then the
 // epilogue of the unsplit GEMM (bias, leaky ReLU, BF16 store to Cb, or FP32 store / accumulation
