@@ -291,9 +291,9 @@ struct Conv {
     int H, W;           // output resolution
     size_t w_off, b_off;  // offsets into the parameter vector
     // tensor maps of the TMA-fed forward (f) and data-gradient (d) GEMMs: A source 1, A source
-    // 2 (concatenation), B; built when the shapes allow it (f_tma, d_tma), else the loaders
-    // gather with cp.async
-    bool f_tma = false, d_tma = false;
+    // 2 (concatenation), B; f_ks, d_ks: the K elements per stage of those maps (64 or 32), 0
+    // when the shapes do not allow it and the loaders gather with cp.async
+    int f_ks = 0, d_ks = 0;
     CUtensorMap fmap[3] = {}, dmap[3] = {};
 };
 
@@ -392,10 +392,10 @@ bool tc_timed_out() {
     return t;
 }
 
-template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GD, bool GAM, bool TMA = false>
+template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GD, bool GAM, int TMA = 0>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits,
                       const CUtensorMap* maps = nullptr) {
-    using TS = lbm::sgtc::TcShape<BN, STAGES, BMN>;
+    using TS = lbm::sgtc::TcShape<BN, STAGES, BMN, TMA ? TMA : lbm::sgtc::BK>;
     // the shared-memory opt-in is per device: one bit per device ordinal that has it (setting it
     // twice from racing host threads is harmless)
     static std::atomic<unsigned long long> configured{0};
@@ -469,45 +469,59 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// Map of an NHWC BF16 tensor [N][H][W][C] (C innermost), box 64 channels x bw x bh pixels x 1
-// image, 128-byte swizzle (the K-major layout the MMAs read), out-of-range elements zero.
-bool map_nhwc(CUtensorMap* m, const void* base, int C, int W, int H, int N, int bw, int bh) {
+// Map of an NHWC BF16 tensor [N][H][W][C] (C innermost), box ks channels x bw x bh pixels x 1
+// image, ks = 64 with 128-byte or ks = 32 with 64-byte swizzle (the K-major layouts the MMAs
+// read), out-of-range elements zero.
+bool map_nhwc(CUtensorMap* m, const void* base, int C, int W, int H, int N, int bw, int bh,
+              int ks) {
     const EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const cuuint64_t dim[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
     const cuuint64_t stride[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2,
                                   (cuuint64_t)H * W * C * 2};
-    const cuuint32_t box[4] = {64, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)ks, (cuuint32_t)bw, (cuuint32_t)bh, 1};
     const cuuint32_t es[4] = {1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dim, stride, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE,
+               ks == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Map of a row-major BF16 matrix [rows][K], box 64 (K) x box_rows, 128-byte swizzle.
-bool map_rows(CUtensorMap* m, const void* base, int K, int rows, int box_rows) {
+// Map of a row-major BF16 matrix [rows][K], box ks (K) x box_rows, swizzled as in map_nhwc.
+bool map_rows(CUtensorMap* m, const void* base, int K, int rows, int box_rows, int ks) {
     const EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const cuuint64_t dim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t stride[1] = {(cuuint64_t)K * 2};
-    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)ks, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dim, stride, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE,
+               ks == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The TMA-fed gathering GEMM (GA or GD with tensor maps, see Conv::fmap / dmap): N tiles of 32,
-// 64, 128 or 256 columns; more stages for the narrow tiles, whose stages are small.
+// The TMA-fed gathering GEMM (GA or GD with tensor maps, see Conv::fmap / dmap), ks elements
+// of K per stage: N tiles of 32, 64, 128 or 256 columns, stages sized for two CTAs per SM.
 template <bool GA, bool GD>
-cudaError_t gemm_tc_tma(cudaStream_t st, const GemmArgs& a, int splits, const CUtensorMap* maps) {
-    switch (pick_bn(a.N)) {
-        case 32: return launch_tc<32, 4, false, false, GA, GD, false, true>(st, a, splits, maps);
-        case 64: return launch_tc<64, 4, false, false, GA, GD, false, true>(st, a, splits, maps);
-        case 128: return launch_tc<128, 3, false, false, GA, GD, false, true>(st, a, splits, maps);
-        case 256: return launch_tc<256, 2, false, false, GA, GD, false, true>(st, a, splits, maps);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t gemm_tc_tma(cudaStream_t st, const GemmArgs& a, int splits, const CUtensorMap* maps,
+                        int ks) {
+    const int bn = pick_bn(a.N);
+    if (ks == 64) switch (bn) {
+            case 32: return launch_tc<32, 4, false, false, GA, GD, false, 64>(st, a, splits, maps);
+            case 64: return launch_tc<64, 4, false, false, GA, GD, false, 64>(st, a, splits, maps);
+            case 128: return launch_tc<128, 3, false, false, GA, GD, false, 64>(st, a, splits, maps);
+            case 256: return launch_tc<256, 2, false, false, GA, GD, false, 64>(st, a, splits, maps);
+            default: break;
+        }
+    if (ks == 32) switch (bn) {
+            case 32: return launch_tc<32, 8, false, false, GA, GD, false, 32>(st, a, splits, maps);
+            case 64: return launch_tc<64, 8, false, false, GA, GD, false, 32>(st, a, splits, maps);
+            case 128: return launch_tc<128, 6, false, false, GA, GD, false, 32>(st, a, splits, maps);
+            case 256: return launch_tc<256, 4, false, false, GA, GD, false, 32>(st, a, splits, maps);
+            default: break;
+        }
+    return cudaErrorInvalidValue;
 }
 
 // The gathering GEMMs (GA: forward convolution, GD: data gradient) with fewer output tiles than
@@ -517,7 +531,7 @@ cudaError_t gemm_tc_tma(cudaStream_t st, const GemmArgs& a, int splits, const CU
 // FP32 stores). Otherwise one launch as usual.
 template <bool GA, bool GD>
 cudaError_t gemm_tc_split(cudaStream_t st, const GemmArgs& a, float* scratch,
-                          size_t scratch_elems, const CUtensorMap* maps = nullptr) {
+                          size_t scratch_elems, const CUtensorMap* maps = nullptr, int ks = 0) {
     const int bn = pick_bn(a.N);
     const long long tiles =
         (long long)((a.N + bn - 1) / bn) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
@@ -527,7 +541,7 @@ cudaError_t gemm_tc_split(cudaStream_t st, const GemmArgs& a, float* scratch,
         splits = std::min<long long>(2 * 152 / tiles, nkt / 4);
     while (splits > 1 && (size_t)splits * a.M * a.N > scratch_elems) --splits;
     if (splits <= 1)
-        return maps ? gemm_tc_tma<GA, GD>(st, a, 1, maps) : gemm_tc<false, false, GA, GD>(st, a);
+        return ks ? gemm_tc_tma<GA, GD>(st, a, 1, maps, ks) : gemm_tc<false, false, GA, GD>(st, a);
     const int chunk = (int)((nkt + splits - 1) / splits) * lbm::sgtc::BK;
     const int nsp = (a.K + chunk - 1) / chunk;
     GemmArgs p = a;
@@ -542,8 +556,8 @@ cudaError_t gemm_tc_split(cudaStream_t st, const GemmArgs& a, float* scratch,
     p.accumulate = 0;
     p.kchunk = chunk;
     p.split_stride = (long long)a.M * a.N;
-    cudaError_t e = maps ? gemm_tc_tma<GA, GD>(st, p, nsp, maps)
-                         : gemm_tc<false, false, GA, GD>(st, p, nsp);
+    cudaError_t e = ks ? gemm_tc_tma<GA, GD>(st, p, nsp, maps, ks)
+                       : gemm_tc<false, false, GA, GD>(st, p, nsp);
     if (e != cudaSuccess) return e;
     k_splitk_finish<<<blocks_for((long long)a.M * a.N / 4), kT, 0, st>>>(
         scratch, nsp, a.M, a.N, a.bias, a.relu, a.Cb, a.Cf, a.ldc, a.Cf2, a.ldc2, a.nsplit,
@@ -724,8 +738,8 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         g.ldc = c.Cout;
         g.bias = s->w + c.b_off;
         g.relu = 1;
-        SCUDA(s, (gemm_tc_split<true, false>(s->stream, g, s->splitk, s->splitk_elems,
-                                              c.f_tma ? c.fmap : nullptr)));
+        SCUDA(s, (gemm_tc_split<true, false>(s->stream, g, s->splitk, s->splitk_elems, c.fmap,
+                                              c.f_ks)));
         // a pool whose source is this conv's output runs right after it
         for (const auto& pl : s->pools)
             if (pl.first == c.out) {
@@ -738,24 +752,29 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
 }
 
 // Tensor maps for the forward and data-gradient GEMMs whose A operand the copy engine can fetch
-// as boxes: no upsampled source, channel counts multiples of 64 (one K-slice = one tap of one
-// source), the 128 rows of a tile a whole block of pixels of one image, and N tiles of 32, 64,
-// 128 or 256 columns. The network input (its pointer changes per call) never qualifies.
+// as boxes: no upsampled source, channel counts multiples of 64 (one K-slice of 64 = one tap of
+// one source) or else of 32 (slices of 32), the 128 rows of a tile a whole block of pixels of
+// one image, and N tiles of 32, 64, 128 or 256 columns. The network input (its pointer changes
+// per call) never qualifies.
 void make_tensor_maps(lbm_surrogate* s) {
     auto tma_width = [](int bn) { return bn == 32 || bn == 64 || bn == 128 || bn == 256; };
+    auto slice = [](int a, int b) { return a % 64 == 0 && b % 64 == 0 ? 64
+                                         : a % 32 == 0 && b % 32 == 0 ? 32 : 0; };
     for (Conv& c : s->convs) {
         const int W = c.W, H = c.H;
         if (!((W % 128 == 0 || 128 % W == 0) && (H * W) % 128 == 0) || c.src1 == 0 || c.up1)
             continue;
         const int bw = std::min(W, 128), bh = 128 / bw, cin = c.C1 + c.C2;
-        if (c.C1 % 64 == 0 && c.C2 % 64 == 0 && tma_width(pick_bn(c.Cout)))
-            c.f_tma = map_nhwc(&c.fmap[0], s->t[c.src1].y, c.C1, W, H, s->maxB, bw, bh) &&
-                      (c.src2 < 0 ||
-                       map_nhwc(&c.fmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, bw, bh)) &&
-                      map_rows(&c.fmap[2], s->wb + c.w_off, 9 * cin, c.Cout, pick_bn(c.Cout));
-        if (c.Cout % 64 == 0 && tma_width(pick_bn(cin)))
-            c.d_tma = map_nhwc(&c.dmap[0], s->gmask, c.Cout, W, H, s->maxB, bw, bh) &&
-                      map_rows(&c.dmap[2], s->wbd + c.w_off, 9 * c.Cout, cin, pick_bn(cin));
+        const int fk = slice(c.C1, c.C2), dk = slice(c.Cout, 0);
+        if (fk && tma_width(pick_bn(c.Cout)) &&
+            map_nhwc(&c.fmap[0], s->t[c.src1].y, c.C1, W, H, s->maxB, bw, bh, fk) &&
+            (c.src2 < 0 || map_nhwc(&c.fmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, bw, bh, fk)) &&
+            map_rows(&c.fmap[2], s->wb + c.w_off, 9 * cin, c.Cout, pick_bn(c.Cout), fk))
+            c.f_ks = fk;
+        if (dk && tma_width(pick_bn(cin)) &&
+            map_nhwc(&c.dmap[0], s->gmask, c.Cout, W, H, s->maxB, bw, bh, dk) &&
+            map_rows(&c.dmap[2], s->wbd + c.w_off, 9 * c.Cout, cin, pick_bn(cin), dk))
+            c.d_ks = dk;
     }
 }
 
@@ -1005,8 +1024,8 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
             gd.ldc2 = c.C2;
             gd.nsplit = c.C1;
         }
-        SCUDA(s, (gemm_tc_split<false, true>(s->stream, gd, s->splitk, s->splitk_elems,
-                                              c.d_tma ? c.dmap : nullptr)));
+        SCUDA(s, (gemm_tc_split<false, true>(s->stream, gd, s->splitk, s->splitk_elems, c.dmap,
+                                              c.d_ks)));
     }
     if (lr > 0.f) {
         ++s->adam_t;

@@ -33,12 +33,13 @@ __host__ __device__ constexpr int tmem_cols(int bn) {
     return bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
 }
 
-template <int BN, int STAGES, bool BMN = false>
+// KS: elements of K per stage (64, or 32 for the 64-byte-swizzled TMA variant)
+template <int BN, int STAGES, bool BMN = false, int KS = BK>
 struct TcShape {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N of kind::f16 at M = 128");
-    static constexpr int A_BYTES = BM * BK * 2;  // 16 KB
+    static constexpr int A_BYTES = BM * KS * 2;  // 16 KB (8 KB when KS = 32)
     // MN-major slices are whole 64-element swizzle atoms wide along M or N
-    static constexpr int B_BYTES = BMN ? (BN + 63) / 64 * 64 * BK * 2 : BN * BK * 2;
+    static constexpr int B_BYTES = BMN ? (BN + 63) / 64 * 64 * KS * 2 : BN * KS * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     // 1 KB alignment slack for the swizzle atoms, then the stages, mbarriers and the TMEM slot
     static constexpr int RAW_BYTES = 1024 + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1) + 16;
@@ -57,6 +58,12 @@ __device__ __forceinline__ uint32_t su32(const void* p) {
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
            ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// the same for 64-byte rows (32 elements of K), 64-byte swizzle, 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
 // shared-memory descriptor: MN-major operand, 128-byte swizzle; atoms of 64 (M or N) x 8 (K)
@@ -298,19 +305,22 @@ __device__ __forceinline__ void load_slice_mn_conv_a(uint8_t* s, const sg::ConvG
 // GA: A is the gathered convolution operand (K-major, rows = output pixels); GD: A is the
 // gathered data-gradient operand; GAM: A is the gathered convolution operand MN-major (K =
 // pixels, M = im2col columns).
-// TMA: (with GA or GD, both operands K-major) thread 0 alone feeds the stages with tiled tensor
-// copies: A as one box of 64 channels x the tile's tbh x tbw pixels of the activation (GA; the
-// tap's offset applied to the box origin, x1 or x2 by channel) or of the output gradient (GD, the
-// offset negated), out-of-image pixels zero-filled by the copy itself; B as a 64 x BN box of the
-// weight matrix. Stage s completes on full[s] (transaction bytes), is released by the MMAs'
-// commit to empty[s], and STAGES slices are in flight.
+// TMA (64 or 32; with GA or GD, both operands K-major): thread 0 alone feeds the stages with
+// tiled tensor copies of TMA elements of K per stage (128- or 64-byte swizzled rows): A as one
+// box of TMA channels x the tile's 128 pixels (a block of whole rows, or 128 pixels of one row)
+// of the activation (GA; the tap's offset applied to the box origin, x1 or x2 by channel) or of
+// the output gradient (GD, the offset negated), out-of-image pixels zero-filled by the copy
+// itself; B as a TMA x BN box of the weight matrix. Stage s completes on full[s] (transaction
+// bytes), is released by the MMAs' commit to empty[s], and STAGES slices are in flight.
 template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GD = false,
-          bool GAM = false, bool TMA = false>
+          bool GAM = false, int TMA = 0>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const sg::GemmArgs g, int* err, const __grid_constant__ CUtensorMap tmA1,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB) {
     static_assert(!TMA || ((GA || GD) && !AMN && !BMN), "TMA feeds the K-major gathers only");
-    using S = TcShape<BN, STAGES, BMN>;
+    static_assert(TMA == 0 || TMA == 64 || TMA == 32, "TMA slice width");
+    constexpr int KS = TMA ? TMA : BK;
+    using S = TcShape<BN, STAGES, BMN, KS>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     // 1 KB-aligned base of the stages (the swizzle pattern follows shared-memory address bits)
     const uint32_t raw = su32(smem_raw);
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kb = g.kchunk ? blockIdx.z * g.kchunk : 0;
     const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
-    const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
+    const int nk = ke > kb ? (ke - kb + KS - 1) / KS : 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -409,7 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (tid == 0) {
             int issued = 0, done_mma = 0;
             bool good = true;
-            for (; issued < STAGES && issued < nk; ++issued) issue(issued, kb + issued * BK);
+            for (; issued < STAGES && issued < nk; ++issued) issue(issued, kb + issued * KS);
             for (int kt = 0; kt < nk; ++kt) {
                 const int st = kt % STAGES;
                 if (!mbar_wait(su32(bars + st), (kt / STAGES) & 1)) {
@@ -419,8 +429,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t a0 = su32(stage_a(st)), b0 = su32(stage_b(st));
 #pragma unroll
-                for (int j = 0; j < BK / 16; ++j)
-                    tc_mma(tmem, desc_sw128(a0 + 32 * j), desc_sw128(b0 + 32 * j), IDESC,
+                for (int j = 0; j < KS / 16; ++j)
+                    tc_mma(tmem, KS == 64 ? desc_sw128(a0 + 32 * j) : desc_sw64(a0 + 32 * j),
+                           KS == 64 ? desc_sw128(b0 + 32 * j) : desc_sw64(b0 + 32 * j), IDESC,
                            (kt > 0 || j > 0) ? 1u : 0u);
                 tc_commit(su32(bars + STAGES + st));
                 done_mma = kt + 1;
@@ -431,7 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         good = false;
                         break;
                     }
-                    issue(sp, kb + issued * BK);
+                    issue(sp, kb + issued * KS);
                     ++issued;
                 }
             }
