@@ -295,6 +295,10 @@ struct Conv {
     // when the shapes do not allow it and the loaders gather with cp.async
     int f_ks = 0, d_ks = 0;
     CUtensorMap fmap[3] = {}, dmap[3] = {};
+    // weight gradient (w): A sources 1 and 2 and the output gradient, boxes of 32 channels x 64
+    // pixels; w_tma false: gathered with cp.async
+    bool w_tma = false;
+    CUtensorMap wmap[3] = {};
 };
 
 struct Tensor {
@@ -395,7 +399,7 @@ bool tc_timed_out() {
 template <int BN, int STAGES, bool AMN, bool BMN, bool GA, bool GD, bool GAM, int TMA = 0>
 cudaError_t launch_tc(cudaStream_t st, const GemmArgs& a, int splits,
                       const CUtensorMap* maps = nullptr) {
-    using TS = lbm::sgtc::TcShape<BN, STAGES, BMN, TMA ? TMA : lbm::sgtc::BK>;
+    using TS = lbm::sgtc::TcShape<BN, STAGES, BMN, lbm::sgtc::slice_k(TMA)>;
     // the shared-memory opt-in is per device: one bit per device ordinal that has it (setting it
     // twice from racing host threads is harmless)
     static std::atomic<unsigned long long> configured{0};
@@ -576,8 +580,20 @@ cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
 // FP32 partials are summed in a fixed order. gather: computed transposed, dW^T = col^T dY with
 // the im2col columns gathered by the loader as the 128-row operand (each thread decodes its tap
 // and channel once) and stored transposed; else from the im2col buffer a.B.
+// The TMA-fed weight gradient (gathered and transposed, maps: Conv::wmap): N tiles of 32, 64,
+// 128 or 256 columns, stages sized for two CTAs per SM.
+cudaError_t gemm_wgrad_tma(cudaStream_t st, const GemmArgs& a, int splits, const CUtensorMap* maps) {
+    switch (pick_bn(a.N)) {
+        case 32: return launch_tc<32, 4, true, true, false, false, true, 1>(st, a, splits, maps);
+        case 64: return launch_tc<64, 4, true, true, false, false, true, 1>(st, a, splits, maps);
+        case 128: return launch_tc<128, 3, true, true, false, false, true, 1>(st, a, splits, maps);
+        case 256: return launch_tc<256, 2, true, true, false, false, true, 1>(st, a, splits, maps);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
-                       float* out, bool gather) {
+                       float* out, bool gather, const CUtensorMap* maps = nullptr) {
     if (gather) {
         // rows: the 9 C_in im2col columns; columns: C_out; a.ldc (= 9 C_in) stays the row
         // length of dW, written at dW[n * ldc + m]
@@ -593,14 +609,15 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     // of the wide ones): each CTA keeps only two K-slices of gathers in flight
     const int bn = pick_bn(a.N);
     const int tiles = ((a.N + bn - 1) / bn) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
-    const int occ = bn <= 64 ? 3 : 2;
+    const int occ = bn <= 64 && !maps ? 3 : 2;
     int splits = std::max(1, std::min(128, occ * 152 / std::max(1, tiles)));
     const long long stride = gather ? (long long)a.N * a.ldc : (long long)a.M * a.ldc;
     while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
     if (splits == 1) {
         a.Cf = out;
-        return gather ? gemm_tc<true, true, false, false, true>(st, a)
-                      : gemm_tc<true, true>(st, a);
+        return maps     ? gemm_wgrad_tma(st, a, 1, maps)
+               : gather ? gemm_tc<true, true, false, false, true>(st, a)
+                        : gemm_tc<true, true>(st, a);
     }
     int chunk = (a.K + splits - 1) / splits;
     chunk = (chunk + lbm::sgtc::BK - 1) / lbm::sgtc::BK * lbm::sgtc::BK;
@@ -608,11 +625,13 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
     a.Cf = scratch;
     a.kchunk = chunk;
     a.split_stride = stride;
-    cudaError_t e = gather ? gemm_tc<true, true, false, false, true>(st, a, splits)
-                           : gemm_tc<true, true>(st, a, splits);
+    cudaError_t e = maps     ? gemm_wgrad_tma(st, a, splits, maps)
+                    : gather ? gemm_tc<true, true, false, false, true>(st, a, splits)
+                             : gemm_tc<true, true>(st, a, splits);
     if (e != cudaSuccess) return e;
     if (stride % 4 == 0 && ((uintptr_t)out & 15) == 0)
-        k_splitk_sum4<<<blocks_for(stride / 4), kT, 0, st>>>(scratch, splits, stride, stride, out);
+        k_splitk_sum4<<<(unsigned)((stride / 4 + 31) / 32), 256, 0, st>>>(scratch, splits, stride,
+                                                                          stride, out);
     else
         k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
     return cudaGetLastError();
@@ -771,6 +790,15 @@ void make_tensor_maps(lbm_surrogate* s) {
             (c.src2 < 0 || map_nhwc(&c.fmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, bw, bh, fk)) &&
             map_rows(&c.fmap[2], s->wb + c.w_off, 9 * cin, c.Cout, pick_bn(c.Cout), fk))
             c.f_ks = fk;
+        if (W % 64 == 0 || 64 % W == 0) {
+            const int ww = std::min(W, 64), wh = 64 / ww;
+            c.w_tma = c.C1 % 32 == 0 && c.C2 % 32 == 0 && c.Cout % 32 == 0 &&
+                      tma_width(pick_bn(c.Cout)) &&
+                      map_nhwc(&c.wmap[0], s->t[c.src1].y, c.C1, W, H, s->maxB, ww, wh, 32) &&
+                      (c.src2 < 0 ||
+                       map_nhwc(&c.wmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, ww, wh, 32)) &&
+                      map_nhwc(&c.wmap[2], s->gmask, c.Cout, W, H, s->maxB, ww, wh, 32);
+        }
         if (dk && tma_width(pick_bn(cin)) &&
             map_nhwc(&c.dmap[0], s->gmask, c.Cout, W, H, s->maxB, bw, bh, dk) &&
             map_rows(&c.dmap[2], s->wbd + c.w_off, 9 * c.Cout, cin, pick_bn(cin), dk))
@@ -998,7 +1026,8 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         gw.lda = c.Cout;
         gw.ldb = 9 * Cin;
         gw.ldc = 9 * Cin;
-        SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off, gather));
+        SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off, gather,
+                            gather && c.w_tma ? c.wmap : nullptr));
         // data gradient (not needed for the input tensor)
         if (c.src1 == 0) continue;
         // implicit GEMM over the source pixels: dX_src[q][ci] += sum over (sub-pixel, tap, co)

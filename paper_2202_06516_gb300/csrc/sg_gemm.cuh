@@ -90,20 +90,35 @@ __global__ void k_splitk_sum(const float* part, int splits, long long stride, lo
     }
 }
 
-// the same sum four consecutive outputs per thread (n and stride multiples of 4)
+// the same sum for four consecutive outputs at a time (n and stride multiples of 4), the splits
+// spread over the eight warps of a 256-thread block: warp w adds splits w, w + 8, ... in order
+// for the 32 float4 outputs of the block, then the eight warp sums are added in warp order
+// (deterministic: the grouping does not depend on the launch).
 __global__ void k_splitk_sum4(const float* part, int splits, long long stride, long long n,
                               float* out) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int z = 0; z < splits; ++z) {
+    __shared__ float4 sm[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long i = blockIdx.x * 32LL + lane, n4 = n / 4;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < n4)
+        for (int z = w; z < splits; z += 8) {
             const float4 v = reinterpret_cast<const float4*>(part + (size_t)z * stride)[i];
             s.x += v.x;
             s.y += v.y;
             s.z += v.z;
             s.w += v.w;
         }
-        reinterpret_cast<float4*>(out)[i] = s;
+    sm[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < n4) {
+        float4 t = sm[0][lane];
+        for (int k = 1; k < 8; ++k) {
+            t.x += sm[k][lane].x;
+            t.y += sm[k][lane].y;
+            t.z += sm[k][lane].z;
+            t.w += sm[k][lane].w;
+        }
+        reinterpret_cast<float4*>(out)[i] = t;
     }
 }
 

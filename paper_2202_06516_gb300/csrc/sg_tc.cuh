@@ -33,7 +33,11 @@ __host__ __device__ constexpr int tmem_cols(int bn) {
     return bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
 }
 
-// KS: elements of K per stage (64, or 32 for the 64-byte-swizzled TMA variant)
+// elements of K per stage of a kernel variant: 64, or 32 for the 64-byte-swizzled K-major TMA
+// variant (TMA = 32); the launch sizes shared memory with the same rule as the kernel
+__host__ __device__ constexpr int slice_k(int tma) { return tma == 64 || tma == 32 ? tma : BK; }
+
+// KS: elements of K per stage (slice_k of the variant)
 template <int BN, int STAGES, bool BMN = false, int KS = BK>
 struct TcShape {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N of kind::f16 at M = 128");
@@ -63,6 +67,14 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 // the same for 64-byte rows (32 elements of K), 64-byte swizzle, 8-row groups 512 B apart
 __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// shared-memory descriptor: MN-major operand, 64-byte swizzle; atoms of 32 (M or N) x 8 (K)
+// elements, the 8-row K-groups of one 32-wide block 512 B apart (stride offset), blocks of 64 K
+// rows 4 KB apart along M or N (leading offset)
+__device__ __forceinline__ uint64_t desc_sw64_mn(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(4096 >> 4) << 16) |
            ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
@@ -312,14 +324,19 @@ __device__ __forceinline__ void load_slice_mn_conv_a(uint8_t* s, const sg::ConvG
 // the output gradient (GD, the offset negated), out-of-image pixels zero-filled by the copy
 // itself; B as a TMA x BN box of the weight matrix. Stage s completes on full[s] (transaction
 // bytes), is released by the MMAs' commit to empty[s], and STAGES slices are in flight.
+// TMA = 1 (with GAM, both operands MN-major): the same feeding for the weight gradient, 64
+// pixels of K per stage in 64-byte-swizzled MN-major blocks of 32: A as four boxes of 32
+// channels x the 64 pixels (a block of whole rows or 64 pixels of one row), each at its tap's
+// offset; B as BN / 32 boxes of 32 output-gradient channels x the same pixels.
 template <int BN, int STAGES, bool AMN = false, bool BMN = false, bool GA = false, bool GD = false,
           bool GAM = false, int TMA = 0>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const sg::GemmArgs g, int* err, const __grid_constant__ CUtensorMap tmA1,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB) {
-    static_assert(!TMA || ((GA || GD) && !AMN && !BMN), "TMA feeds the K-major gathers only");
-    static_assert(TMA == 0 || TMA == 64 || TMA == 32, "TMA slice width");
-    constexpr int KS = TMA ? TMA : BK;
+    static_assert(!TMA || ((GA || GD) && !AMN && !BMN && (TMA == 64 || TMA == 32)) ||
+                      (GAM && AMN && BMN && TMA == 1 && BN % 32 == 0),
+                  "TMA feeds the K-major gathers (64 or 32) or the weight gradient (1)");
+    constexpr int KS = slice_k(TMA);
     using S = TcShape<BN, STAGES, BMN, KS>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     // 1 KB-aligned base of the stages (the swizzle pattern follows shared-memory address bits)
@@ -396,12 +413,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = true;
     if constexpr (TMA) {
         // tile origin: n, y0, x0 of the first of the 128 pixels (a tbh x tbw block)
-        const int TH = GA ? g.conv.H : g.dg.H, TW = GA ? g.conv.W : g.dg.W;
+        const int TH = GA || GAM ? g.conv.H : g.dg.H, TW = GA || GAM ? g.conv.W : g.dg.W;
         const int img = m0 / (TH * TW), rem = m0 - img * (TH * TW);
         const int y0 = rem / TW, x0 = rem - (rem / TW) * TW;
-        const int lk = GA ? g.conv.lc : g.dg.lco;
+        const int lk = GA || GAM ? g.conv.lc : g.dg.lco;
         auto issue = [&](int st, int k0) {
             const uint32_t full = su32(bars + st);
+            if constexpr (GAM) {
+                // K = pixels k0 .. k0 + 63: image, row and column of the first
+                mbar_expect_tx(full, (uint32_t)(BM * 64 * 2 + BN * 64 * 2));
+                const int pn = k0 / (TH * TW), pr = k0 - pn * (TH * TW);
+                const int py = pr / TW, px = pr - (pr / TW) * TW;
+#pragma unroll
+                for (int b = 0; b < BM / 32; ++b) {
+                    const int col = m0 + 32 * b, tap = col >> lk, ci = col & ((1 << lk) - 1);
+                    const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+                    if (ci < g.conv.C1)
+                        tma_load_4d(su32(stage_a(st)) + 4096 * b, &tmA1, full, ci, px + dx,
+                                    py + dy, pn);
+                    else
+                        tma_load_4d(su32(stage_a(st)) + 4096 * b, &tmA2, full, ci - g.conv.C1,
+                                    px + dx, py + dy, pn);
+                }
+#pragma unroll
+                for (int b = 0; b < BN / 32; ++b)
+                    tma_load_4d(su32(stage_b(st)) + 4096 * b, &tmB, full, n0 + 32 * b, px, py, pn);
+                return;
+            }
             mbar_expect_tx(full, (uint32_t)(S::A_BYTES + S::B_BYTES));
             const int tap = k0 >> lk, ch = k0 & ((1 << lk) - 1);
             const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
@@ -429,10 +467,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t a0 = su32(stage_a(st)), b0 = su32(stage_b(st));
 #pragma unroll
-                for (int j = 0; j < KS / 16; ++j)
-                    tc_mma(tmem, KS == 64 ? desc_sw128(a0 + 32 * j) : desc_sw64(a0 + 32 * j),
-                           KS == 64 ? desc_sw128(b0 + 32 * j) : desc_sw64(b0 + 32 * j), IDESC,
-                           (kt > 0 || j > 0) ? 1u : 0u);
+                for (int j = 0; j < KS / 16; ++j) {
+                    // K = 16 per MMA: 32 bytes along a K-major row, or two 512-byte K-groups of
+                    // an MN-major 64-byte-swizzled block
+                    const uint64_t ad = GAM         ? desc_sw64_mn(a0 + 1024 * j)
+                                        : KS == 64 ? desc_sw128(a0 + 32 * j)
+                                                   : desc_sw64(a0 + 32 * j);
+                    const uint64_t bd = GAM         ? desc_sw64_mn(b0 + 1024 * j)
+                                        : KS == 64 ? desc_sw128(b0 + 32 * j)
+                                                   : desc_sw64(b0 + 32 * j);
+                    tc_mma(tmem, ad, bd, IDESC, (kt > 0 || j > 0) ? 1u : 0u);
+                }
                 tc_commit(su32(bars + STAGES + st));
                 done_mma = kt + 1;
                 // refill the stage that slice kt - 1 used once its MMAs have read it
