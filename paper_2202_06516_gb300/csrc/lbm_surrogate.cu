@@ -506,21 +506,22 @@ bool map_rows(CUtensorMap* m, const void* base, int K, int rows, int box_rows, i
 }
 
 // The TMA-fed gathering GEMM (GA or GD with tensor maps, see Conv::fmap / dmap), ks elements
-// of K per stage: N tiles of 32, 64, 128 or 256 columns, stages sized for two CTAs per SM.
+// of K per stage: N tiles of 32, 64, 128 or 256 columns; few stages, so that several CTAs share
+// an SM (each CTA's load latency overlaps the others' MMAs and epilogues).
 template <bool GA, bool GD>
 cudaError_t gemm_tc_tma(cudaStream_t st, const GemmArgs& a, int splits, const CUtensorMap* maps,
                         int ks) {
     const int bn = pick_bn(a.N);
     if (ks == 64) switch (bn) {
-            case 32: return launch_tc<32, 4, false, false, GA, GD, false, 64>(st, a, splits, maps);
-            case 64: return launch_tc<64, 4, false, false, GA, GD, false, 64>(st, a, splits, maps);
+            case 32: return launch_tc<32, 3, false, false, GA, GD, false, 64>(st, a, splits, maps);
+            case 64: return launch_tc<64, 3, false, false, GA, GD, false, 64>(st, a, splits, maps);
             case 128: return launch_tc<128, 3, false, false, GA, GD, false, 64>(st, a, splits, maps);
             case 256: return launch_tc<256, 2, false, false, GA, GD, false, 64>(st, a, splits, maps);
             default: break;
         }
     if (ks == 32) switch (bn) {
-            case 32: return launch_tc<32, 8, false, false, GA, GD, false, 32>(st, a, splits, maps);
-            case 64: return launch_tc<64, 8, false, false, GA, GD, false, 32>(st, a, splits, maps);
+            case 32: return launch_tc<32, 4, false, false, GA, GD, false, 32>(st, a, splits, maps);
+            case 64: return launch_tc<64, 4, false, false, GA, GD, false, 32>(st, a, splits, maps);
             case 128: return launch_tc<128, 6, false, false, GA, GD, false, 32>(st, a, splits, maps);
             case 256: return launch_tc<256, 4, false, false, GA, GD, false, 32>(st, a, splits, maps);
             default: break;
@@ -581,11 +582,11 @@ cudaError_t gemm(cudaStream_t st, const GemmArgs& a) {
 // the im2col columns gathered by the loader as the 128-row operand (each thread decodes its tap
 // and channel once) and stored transposed; else from the im2col buffer a.B.
 // The TMA-fed weight gradient (gathered and transposed, maps: Conv::wmap): N tiles of 32, 64,
-// 128 or 256 columns, stages sized for two CTAs per SM.
+// 128 or 256 columns, few stages as in gemm_tc_tma.
 cudaError_t gemm_wgrad_tma(cudaStream_t st, const GemmArgs& a, int splits, const CUtensorMap* maps) {
     switch (pick_bn(a.N)) {
-        case 32: return launch_tc<32, 4, true, true, false, false, true, 1>(st, a, splits, maps);
-        case 64: return launch_tc<64, 4, true, true, false, false, true, 1>(st, a, splits, maps);
+        case 32: return launch_tc<32, 3, true, true, false, false, true, 1>(st, a, splits, maps);
+        case 64: return launch_tc<64, 3, true, true, false, false, true, 1>(st, a, splits, maps);
         case 128: return launch_tc<128, 3, true, true, false, false, true, 1>(st, a, splits, maps);
         case 256: return launch_tc<256, 2, true, true, false, false, true, 1>(st, a, splits, maps);
         default: return cudaErrorInvalidValue;
