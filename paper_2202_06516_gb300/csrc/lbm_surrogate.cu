@@ -477,14 +477,15 @@ EncodeTiledFn encode_tiled() {
 // image, ks = 64 with 128-byte or ks = 32 with 64-byte swizzle (the K-major layouts the MMAs
 // read), out-of-range elements zero.
 bool map_nhwc(CUtensorMap* m, const void* base, int C, int W, int H, int N, int bw, int bh,
-              int ks) {
+              int ks, int step = 1) {
     const EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const cuuint64_t dim[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
     const cuuint64_t stride[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2,
                                   (cuuint64_t)H * W * C * 2};
-    const cuuint32_t box[4] = {(cuuint32_t)ks, (cuuint32_t)bw, (cuuint32_t)bh, 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
+    // step 2: every second pixel in x and y (the box spans 2 bw x 2 bh pixels, loads bw x bh)
+    const cuuint32_t box[4] = {(cuuint32_t)ks, (cuuint32_t)(bw * step), (cuuint32_t)(bh * step), 1};
+    const cuuint32_t es[4] = {1, (cuuint32_t)step, (cuuint32_t)step, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dim, stride, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE,
                ks == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
@@ -782,7 +783,20 @@ void make_tensor_maps(lbm_surrogate* s) {
                                          : a % 32 == 0 && b % 32 == 0 ? 32 : 0; };
     for (Conv& c : s->convs) {
         const int W = c.W, H = c.H;
-        if (!((W % 128 == 0 || 128 % W == 0) && (H * W) % 128 == 0) || c.src1 == 0 || c.up1)
+        if (c.up1 && c.src1 != 0) {
+            // data gradient of an upsampling convolution: rows are source pixels (half
+            // resolution), the output gradient read every second pixel; B wraps every 9 Cout
+            const int Ws = W / 2, Hs = H / 2, cin = c.C1 + c.C2, dk = slice(c.Cout, 0);
+            if ((Ws % 128 == 0 || 128 % Ws == 0) && (Hs * Ws) % 128 == 0 && dk &&
+                (9 * c.Cout) % dk == 0 && tma_width(pick_bn(cin))) {
+                const int bw = std::min(Ws, 128), bh = 128 / bw;
+                if (map_nhwc(&c.dmap[0], s->gmask, c.Cout, W, H, s->maxB, bw, bh, dk, 2) &&
+                    map_rows(&c.dmap[2], s->wbd + c.w_off, 9 * c.Cout, cin, pick_bn(cin), dk))
+                    c.d_ks = dk;
+            }
+            continue;
+        }
+        if (!((W % 128 == 0 || 128 % W == 0) && (H * W) % 128 == 0) || c.src1 == 0)
             continue;
         const int bw = std::min(W, 128), bh = 128 / bw, cin = c.C1 + c.C2;
         const int fk = slice(c.C1, c.C2), dk = slice(c.Cout, 0);

@@ -412,8 +412,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     bool ok = true;
     if constexpr (TMA) {
-        // tile origin: n, y0, x0 of the first of the 128 pixels (a tbh x tbw block)
-        const int TH = GA || GAM ? g.conv.H : g.dg.H, TW = GA || GAM ? g.conv.W : g.dg.W;
+        // tile origin: n, y0, x0 of the first of the 128 pixels (a tbh x tbw block); the data
+        // gradient of an upsampling convolution has its rows at the source's half resolution
+        const int TH = GA || GAM ? g.conv.H : g.dg.H >> g.dg.up1;
+        const int TW = GA || GAM ? g.conv.W : g.dg.W >> g.dg.up1;
         const int img = m0 / (TH * TW), rem = m0 - img * (TH * TW);
         const int y0 = rem / TW, x0 = rem - (rem / TW) * TW;
         const int lk = GA || GAM ? g.conv.lc : g.dg.lco;
@@ -449,10 +451,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 else
                     tma_load_4d(su32(stage_a(st)), &tmA2, full, ch - g.conv.C1, x0 + dx, y0 + dy,
                                 img);
+            } else if (g.dg.up1) {
+                // K = (sub-pixel s, tap, channel): the output gradient at (2 y + sy - dy,
+                // 2 x + sx - dx), every second pixel in both directions (a strided box)
+                const int sub = tap / 9, t9 = tap - sub * 9;
+                const int uy = t9 / 3 - 1, ux = t9 - (t9 / 3) * 3 - 1;
+                tma_load_4d(su32(stage_a(st)), &tmA1, full, ch, 2 * x0 + (sub & 1) - ux,
+                            2 * y0 + (sub >> 1) - uy, img);
             } else {
                 tma_load_4d(su32(stage_a(st)), &tmA1, full, ch, x0 - dx, y0 - dy, img);
             }
-            tma_load_2d(su32(stage_b(st)), &tmB, full, k0, n0);
+            tma_load_2d(su32(stage_b(st)), &tmB, full, g.kperiod ? k0 % g.kperiod : k0, n0);
         };
         if (tid == 0) {
             int issued = 0, done_mma = 0;
