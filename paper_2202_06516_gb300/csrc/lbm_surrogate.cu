@@ -794,6 +794,12 @@ void make_tensor_maps(lbm_surrogate* s) {
                     map_rows(&c.dmap[2], s->wbd + c.w_off, 9 * c.Cout, cin, pick_bn(cin), dk))
                     c.d_ks = dk;
             }
+            // weight gradient: 32 source pixels x 32 channels per box, and 32 output-gradient
+            // pixels taken every second one
+            if (W % 64 == 0 && c.C2 == 0 && c.C1 % 32 == 0 && c.Cout % 32 == 0 &&
+                tma_width(pick_bn(c.Cout)))
+                c.w_tma = map_nhwc(&c.wmap[0], s->t[c.src1].y, c.C1, Ws, Hs, s->maxB, 32, 1, 32) &&
+                          map_nhwc(&c.wmap[2], s->gmask, c.Cout, W, H, s->maxB, 32, 1, 32, 2);
             continue;
         }
         if (!((W % 128 == 0 || 128 % W == 0) && (H * W) % 128 == 0) || c.src1 == 0)

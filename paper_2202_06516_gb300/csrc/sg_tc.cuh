@@ -426,6 +426,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_expect_tx(full, (uint32_t)(BM * 64 * 2 + BN * 64 * 2));
                 const int pn = k0 / (TH * TW), pr = k0 - pn * (TH * TW);
                 const int py = pr / TW, px = pr - (pr / TW) * TW;
+                if (g.conv.up1) {
+                    // upsampling convolution: the slice's 64 pixels (one row segment) in the
+                    // order even columns, odd columns (K is summed over, the same order for A
+                    // and B); each half reads a run of 32 consecutive source pixels and every
+                    // second output-gradient pixel
+#pragma unroll
+                    for (int b = 0; b < BM / 32; ++b) {
+                        const int col = m0 + 32 * b, tap = col >> lk, ci = col & ((1 << lk) - 1);
+                        const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+                        const int sy = (py + dy) >= 0 ? (py + dy) >> 1 : -1;
+                        const uint32_t dst = su32(stage_a(st)) + 4096 * b;
+                        tma_load_4d(dst, &tmA1, full, ci, (px >> 1) + (dx < 0 ? -1 : 0), sy, pn);
+                        tma_load_4d(dst + 2048, &tmA1, full, ci, (px >> 1) + (dx > 0 ? 1 : 0), sy,
+                                    pn);
+                    }
+#pragma unroll
+                    for (int b = 0; b < BN / 32; ++b) {
+                        const uint32_t dst = su32(stage_b(st)) + 4096 * b;
+                        tma_load_4d(dst, &tmB, full, n0 + 32 * b, px, py, pn);
+                        tma_load_4d(dst + 2048, &tmB, full, n0 + 32 * b, px + 1, py, pn);
+                    }
+                    return;
+                }
 #pragma unroll
                 for (int b = 0; b < BM / 32; ++b) {
                     const int col = m0 + 32 * b, tap = col >> lk, ci = col & ((1 << lk) - 1);
