@@ -122,7 +122,7 @@ __global__ void k_avgpool(const bf16* x, bf16* y, int B, int H, int W, int C) {
 // as a separate pass would); and the per-block column sums of the stored g (the bias gradient's
 // partials). Thread t always covers the eight channels 8 t mod C (8 x threads per block is a
 // multiple of C), so each block adds its threads' sums per channel in thread order into
-// part[block][c] (deterministic). H, W: the output resolution (even when POOL).
+// part[c][block] (deterministic). H, W: the output resolution (even when POOL).
 template <bool POOL>
 __global__ void k_relu_bias(const float* dy, const float* dyp, const bf16* y, bf16* g,
                             long long n8, int C, int H, int W, float* part) {
@@ -169,17 +169,18 @@ __global__ void k_relu_bias(const float* dy, const float* dyp, const bf16* y, bf
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         float s = 0.f;
         for (int k = 0; k < reps; ++k) s += sred[(c / 8 + k * groups) * 8 + (c & 7)];
-        part[(size_t)blockIdx.x * C + c] = s;
+        part[(size_t)c * gridDim.x + blockIdx.x] = s;
     }
 }
 
-// out[c] = sum over b of part[b * C + c]: one block per column, a fixed-shape tree in shared
-// memory (deterministic)
-__global__ void k_colsum_final(const float* part, int nb, int C, float* out) {
+// out[c] = sum over b of the partials of column c: part[b * C + c], or part[c * nb + b] when
+// transposed; one block per column, a fixed-shape tree in shared memory (deterministic)
+__global__ void k_colsum_final(const float* part, int nb, int C, float* out, int transposed = 0) {
     __shared__ float sm[kT];
     const int c = blockIdx.x;
     float s = 0.f;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)b * C + c];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        s += transposed ? part[(size_t)c * nb + b] : part[(size_t)b * C + c];
     sm[threadIdx.x] = s;
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
@@ -253,8 +254,39 @@ __global__ void k_head(const bf16* x, const float* w, const float* bptr, float* 
     }
 }
 
+// Offsets and shapes of the convolution weights in the parameter vector, for the kernels that
+// keep the BF16 copies (the forward/weight-gradient layout w[co][tap][ci] and the data-gradient
+// layout wd[ci][tap][co]).
+struct ConvTable {
+    int n;
+    long long off[24];
+    int cout[24], cin[24];
+};
+
+// BF16 copies of parameter t with FP32 value x: wb[t], and for a convolution weight also its
+// data-gradient position wd[off + (ci 9 + tap) cout + co]
+__device__ __forceinline__ void store_bf16_copies(long long t, float x, bf16* wb, bf16* wd,
+                                                  const ConvTable& tab) {
+    const bf16 h = __float2bfloat16_rn(x);
+    wb[t] = h;
+    for (int k = 0; k < tab.n; ++k) {
+        const long long loc = t - tab.off[k];
+        const long long len = (long long)tab.cout[k] * 9 * tab.cin[k];
+        if (loc >= 0 && loc < len) {
+            const int cin = tab.cin[k], cout = tab.cout[k];
+            const int co = (int)(loc / (9 * cin)), rem = (int)(loc - (long long)co * 9 * cin);
+            const int tap = rem / cin, ci = rem - tap * cin;
+            wd[tab.off[k] + ((long long)ci * 9 + tap) * cout + co] = h;
+            return;
+        }
+    }
+}
+
+// Adam with bias correction (c1, c2 = 1 / (1 - beta^t)), followed by the BF16 copies of the
+// updated parameter
 __global__ void k_adam(float* w, const float* g, float* m, float* v, long long n, float lr,
-                       float b1, float b2, float eps, float c1, float c2) {
+                       float b1, float b2, float eps, float c1, float c2, bf16* wb, bf16* wd,
+                       const ConvTable tab) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
         const float gi = g[t];
@@ -262,27 +294,20 @@ __global__ void k_adam(float* w, const float* g, float* m, float* v, long long n
         const float vi = b2 * v[t] + (1.f - b2) * gi * gi;
         m[t] = mi;
         v[t] = vi;
-        w[t] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        const float wi = w[t] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        w[t] = wi;
+        store_bf16_copies(t, wi, wb, wd, tab);
     }
 }
 
-__global__ void k_to_bf16(const float* x, bf16* y, long long n) {
+// the BF16 copies of every parameter (after the FP32 masters were set)
+__global__ void k_bf16_copies(const float* w, long long n, bf16* wb, bf16* wd,
+                              const ConvTable tab) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
-        y[t] = __float2bfloat16_rn(x[t]);
+        store_bf16_copies(t, w[t], wb, wd, tab);
 }
 
-// Data-gradient weights of one convolution: wd[ci][tap][co] = w[co][tap][ci], i.e. for each
-// input channel the 9 C_out weights it contributes to, (tap, co) contiguous.
-__global__ void k_dgrad_weights(const bf16* w, bf16* wd, int cout, int cin) {
-    const long long n = (long long)cin * 9 * cout;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int ci = (int)(i / (9 * cout)), rem = (int)(i - (long long)ci * 9 * cout);
-        const int tap = rem / cout, co = rem - tap * cout;
-        wd[i] = w[(size_t)co * 9 * cin + tap * cin + ci];
-    }
-}
 
 struct Conv {
     int src1, C1, up1;  // source tensor index, channels, stored at half resolution
@@ -334,6 +359,7 @@ struct lbm_surrogate {
     float* splitk = nullptr;  // split-K partials of the weight gradient
     size_t splitk_elems = 0;
     int part_blocks = 256;
+    ConvTable tab{};  // convolution weight shapes for the BF16 copies
     long long adam_t = 0;
     std::string err;
 };
@@ -642,13 +668,8 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
 // BF16 copies of the weights (after the FP32 masters changed): W for the forward pass and the
 // weight gradient, the rearranged copy for the data gradient
 cudaError_t refresh_bf16_weights(lbm_surrogate* s) {
-    k_to_bf16<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(s->w, s->wb,
-                                                                       (long long)s->nparams);
-    for (const Conv& c : s->convs) {
-        const int cin = c.C1 + c.C2;
-        k_dgrad_weights<<<blocks_for((long long)c.Cout * 9 * cin), kT, 0, s->stream>>>(
-            s->wb + c.w_off, s->wbd + c.w_off, c.Cout, cin);
-    }
+    k_bf16_copies<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(
+        s->w, (long long)s->nparams, s->wb, s->wbd, s->tab);
     return cudaGetLastError();
 }
 
@@ -850,6 +871,12 @@ lbm_status lbm_surrogate_create(int32_t H, int32_t W, int32_t base, int32_t max_
     s->maxB = max_batch;
     s->device = device;
     build(s);
+    s->tab.n = std::min<int>(24, (int)s->convs.size());  // 17 convolutions
+    for (int k = 0; k < s->tab.n; ++k) {
+        s->tab.off[k] = (long long)s->convs[k].w_off;
+        s->tab.cout[k] = s->convs[k].Cout;
+        s->tab.cin[k] = s->convs[k].C1 + s->convs[k].C2;
+    }
     auto cleanup = [&](const char* e) {
         lbm_surrogate_destroy(s);
         return sfail(nullptr, LBM_ERR_CUDA, std::string("lbm_surrogate_create: ") + e);
@@ -1023,7 +1050,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         else
             k_relu_bias<false><<<rb, kT, 0, s->stream>>>(o.dy, nullptr, o.y, s->gmask, n_out / 8,
                                                          c.Cout, c.H, c.W, s->bpart);
-        k_colsum_final<<<c.Cout, kT, 0, s->stream>>>(s->bpart, rb, c.Cout, s->g + c.b_off);
+        k_colsum_final<<<c.Cout, kT, 0, s->stream>>>(s->bpart, rb, c.Cout, s->g + c.b_off, 1);
         // weight gradient: dW[co][k] = sum_p g[p][co] col[p][k], the im2col columns gathered by
         // the GEMM's loader when the resolution allows (powers of two), else from a buffer
         GemmArgs gw{};
@@ -1083,8 +1110,8 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         const float c1 = 1.f / (1.f - powf(b1, (float)s->adam_t));
         const float c2 = 1.f / (1.f - powf(b2, (float)s->adam_t));
         k_adam<<<blocks_for((long long)s->nparams), kT, 0, s->stream>>>(
-            s->w, s->g, s->m, s->v, (long long)s->nparams, lr, b1, b2, 1e-8f, c1, c2);
-        SCUDA(s, refresh_bf16_weights(s));
+            s->w, s->g, s->m, s->v, (long long)s->nparams, lr, b1, b2, 1e-8f, c1, c2, s->wb, s->wbd,
+            s->tab);
     }
     SCUDA(s, cudaGetLastError());
     SCUDA(s, cudaStreamSynchronize(s->stream));
