@@ -569,7 +569,7 @@ cudaError_t gemm_tc_split(cudaStream_t st, const GemmArgs& a, float* scratch,
         (long long)((a.N + bn - 1) / bn) * ((a.M + lbm::sgtc::BM - 1) / lbm::sgtc::BM);
     const int nkt = (a.K + lbm::sgtc::BK - 1) / lbm::sgtc::BK;
     long long splits = 1;
-    if (tiles < 114 && a.N % 4 == 0 && !a.tout && !a.kchunk)
+    if (tiles < 114 && a.N % 4 == 0 && !a.tout && !a.kchunk && !a.rperm)
         splits = std::min<long long>(2 * 152 / tiles, nkt / 4);
     while (splits > 1 && (size_t)splits * a.M * a.N > scratch_elems) --splits;
     if (splits <= 1)
@@ -780,6 +780,7 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         g.ldc = c.Cout;
         g.bias = s->w + c.b_off;
         g.relu = 1;
+        if (c.up1 && c.f_ks) g.rperm = std::min(c.W, 128) / 2;
         SCUDA(s, (gemm_tc_split<true, false>(s->stream, g, s->splitk, s->splitk_elems, c.fmap,
                                               c.f_ks)));
         // a pool whose source is this conv's output runs right after it
@@ -805,6 +806,15 @@ void make_tensor_maps(lbm_surrogate* s) {
     for (Conv& c : s->convs) {
         const int W = c.W, H = c.H;
         if (c.up1 && c.src1 != 0) {
+            // forward of an upsampling convolution: tile rows in runs of even, then odd output
+            // columns, each run a box of half a tile row of source pixels
+            const int fk = slice(c.C1, c.C2);
+            if ((W % 128 == 0 || 128 % W == 0) && (H * W) % 128 == 0 && W >= 16 && fk &&
+                c.C2 == 0 && tma_width(pick_bn(c.Cout)) &&
+                map_nhwc(&c.fmap[0], s->t[c.src1].y, c.C1, W / 2, H / 2, s->maxB,
+                         std::min(W, 128) / 2, 1, fk) &&
+                map_rows(&c.fmap[2], s->wb + c.w_off, 9 * c.C1, c.Cout, pick_bn(c.Cout), fk))
+                c.f_ks = fk;
             // data gradient of an upsampling convolution: rows are source pixels (half
             // resolution), the output gradient read every second pixel; B wraps every 9 Cout
             const int Ws = W / 2, Hs = H / 2, cin = c.C1 + c.C2, dk = slice(c.Cout, 0);

@@ -57,7 +57,16 @@ struct GemmArgs {
     float* Cf2;        // FP32 output columns n >= nsplit go to Cf2[m * ldc2 + n - nsplit]
     int ldc2, nsplit;
     int tout;          // FP32 output stored transposed: Cf[n * ldc + m] (no bias / ReLU)
+    int rperm;         // h > 0: the rows of a tile come in runs of 2 h pixels, each run's even
+                       // columns first, then its odd columns (row_pixel); 0: in pixel order
 };
+
+// pixel offset within its tile of tile row r (see GemmArgs::rperm)
+__host__ __device__ __forceinline__ int row_pixel(int r, int h) {
+    if (h == 0) return r;
+    const int w2 = 2 * h, i = r / w2, j = r - i * w2;
+    return i * w2 + (j < h ? 2 * j : 2 * (j - h) + 1);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);

@@ -468,7 +468,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_expect_tx(full, (uint32_t)(S::A_BYTES + S::B_BYTES));
             const int tap = k0 >> lk, ch = k0 & ((1 << lk) - 1);
             const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
-            if (GA) {
+            if (GA && g.conv.up1) {
+                // upsampling layer: the tile's rows come as runs of even, then odd output
+                // columns (rperm = half a tile row); each run reads consecutive source pixels of
+                // the half-resolution source row floor((y + dy) / 2)
+                const int h = g.rperm, tbh = BM / (2 * h);
+                for (int i = 0; i < tbh; ++i) {
+                    const int yo = y0 + i + dy, sy = yo >= 0 ? yo >> 1 : -1;
+                    const uint32_t row = su32(stage_a(st)) + (uint32_t)(i * 2 * h * KS * 2);
+                    tma_load_4d(row, &tmA1, full, ch, (x0 >> 1) + (dx < 0 ? -1 : 0), sy, img);
+                    tma_load_4d(row + (uint32_t)(h * KS * 2), &tmA1, full, ch,
+                                (x0 >> 1) + (dx > 0 ? 1 : 0), sy, img);
+                }
+            } else if (GA) {
                 if (ch < g.conv.C1)
                     tma_load_4d(su32(stage_a(st)), &tmA1, full, ch, x0 + dx, y0 + dy, img);
                 else
@@ -644,7 +656,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int j = 0; j < 8; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
 #pragma unroll
                     for (int it = 0; it < 4; ++it) {
-                        const int r = it * 8 + (lane >> 2), m = m0 + warp * 32 + r;
+                        const int r = it * 8 + (lane >> 2);
+                        const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
                         if (m >= g.M) continue;
                         const float4 x0 = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
                         const float4 x1 = *reinterpret_cast<const float4*>(ep + r * 36 + cc + 4);
@@ -671,7 +684,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // destination of row it * 4 + lane / 8; with accumulation all eight old
                     // values are loaded before the first store, so their latencies overlap
                     auto dst_of = [&](int it) {
-                        const int m = m0 + warp * 32 + it * 4 + (lane >> 3);
+                        const int m = m0 + sg::row_pixel(warp * 32 + it * 4 + (lane >> 3), g.rperm);
                         return (g.Cf2 && n >= g.nsplit)
                                    ? reinterpret_cast<float4*>(g.Cf2 + (size_t)m * g.ldc2 +
                                                                (n - g.nsplit))
@@ -681,13 +694,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (g.accumulate) {
 #pragma unroll
                         for (int it = 0; it < 8; ++it) {
-                            const int m = m0 + warp * 32 + it * 4 + (lane >> 3);
+                            const int m = m0 + sg::row_pixel(warp * 32 + it * 4 + (lane >> 3), g.rperm);
                             old[it] = m < g.M ? *dst_of(it) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
                     }
 #pragma unroll
                     for (int it = 0; it < 8; ++it) {
-                        const int r = it * 4 + (lane >> 3), m = m0 + warp * 32 + r;
+                        const int r = it * 4 + (lane >> 3);
+                        const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
                         if (m >= g.M) continue;
                         float4 x = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
                         x.x += bn[0];
@@ -715,7 +729,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const float bn = (col_ok && g.bias) ? g.bias[n] : 0.f;
 #pragma unroll 4
                 for (int r = 0; r < 32; ++r) {
-                    const int m = m0 + warp * 32 + r;
+                    const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
                     if (!col_ok || m >= g.M) continue;
                     float x = ep[r * 36 + lane] + bn;
                     if (g.relu) x = fmaxf(x, 0.1f * x);
