@@ -157,7 +157,8 @@ lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
 
 /* Build the geometry on the device (classification, wetting layers, wall chemical potential,
  * boundary-link masks) and set the initial state; resets the step counter. Copies g->rho0 from
- * the host when given. Synchronous. */
+ * the host when given. When every wall field (all but the drop and rho0) equals the current
+ * geometry's, the walls already on the device are kept and only the state is set. Synchronous. */
 lbm_status lbm_set_geometry(lbm_ctx *ctx, const lbm_geometry *g);
 
 /* Advance nsteps time steps (Eq. 1-4 with Eq. 7, 12-14): one fused kernel per step, replayed

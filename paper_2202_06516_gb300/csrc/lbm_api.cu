@@ -402,6 +402,15 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
         return fail(c, LBM_ERR_ARG, "lbm_set_geometry: boundary must be LBM_BB_HALFWAY or "
                                     "LBM_BB_INTERP");
     DeviceGuard dg(c->device);
+    // the walls (classes, wetting layers, wall potentials, links) depend on these fields only;
+    // the drop and rho0 set the initial state
+    const lbm_geometry& o = c->geom;
+    const bool same_walls = c->has_geometry && o.has_circle == g->has_circle &&
+                            o.stripes == g->stripes && o.cx == g->cx && o.cy == g->cy &&
+                            o.R == g->R && o.mu_circle == g->mu_circle &&
+                            o.stripe_arc == g->stripe_arc && o.mu_stripe_b == g->mu_stripe_b &&
+                            o.mu_bottom == g->mu_bottom && o.mu_top == g->mu_top &&
+                            o.concave == g->concave && o.boundary == g->boundary;
     lbm::GeomArgs a{};
     a.nx = c->nx;
     a.ny = c->ny;
@@ -421,16 +430,19 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
     a.mu_stripe_b = g->mu_stripe_b;
     a.mu_bottom = g->mu_bottom;
     a.mu_top = g->mu_top;
-    LBM_CUDA(c, cudaMemsetAsync(c->flags, lbm::kSolid, c->plane, c->stream));
-    LBM_CUDA(c, cudaMemsetAsync(c->muw, 0, c->plane * c->esz, c->stream));
-    LBM_CUDA(c, cudaMemsetAsync(c->linkmask, 0, c->plane, c->stream));
-    LBM_CUDA(c, lbm::launch_geometry(c, a));
+    if (!same_walls) {
+        c->has_geometry = false;  // until the new walls are complete
+        LBM_CUDA(c, cudaMemsetAsync(c->flags, lbm::kSolid, c->plane, c->stream));
+        LBM_CUDA(c, cudaMemsetAsync(c->muw, 0, c->plane * c->esz, c->stream));
+        LBM_CUDA(c, cudaMemsetAsync(c->linkmask, 0, c->plane, c->stream));
+        LBM_CUDA(c, lbm::launch_geometry(c, a));
+    }
     // captured step graphs stay valid across geometries (the kernels read the same buffers);
     // they hold the boundary scheme and the variant, so a change of either drops them
     const bool ibb = g->boundary == LBM_BB_INTERP;
     if (ibb != c->ibb) destroy_graphs(c);
     c->ibb = ibb;
-    if (c->ibb) {
+    if (c->ibb && !same_walls) {
         if (!c->dlt) {
             destroy_graphs(c);
             LBM_CUDA(c, cudaMalloc(&c->dlt, 8 * c->plane * c->esz));
@@ -455,7 +467,6 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const lbm_geometry* g) {
             return fail(c, LBM_ERR_CUDA, std::string("lbm_set_geometry: ") + cudaGetErrorString(e));
     } else {
         LBM_CUDA(c, lbm::launch_init_state(c, *g, nullptr));
-        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     c->geom = *g;
     c->geom.rho0 = nullptr;

@@ -191,6 +191,51 @@ def test_new_geometry_on_a_used_context(lbm, oracle_mod):
     lat.close()
 
 
+@pytest.mark.parametrize("interp", [0, 1])
+def test_same_walls_new_state_on_a_used_context(lbm, oracle_mod, interp):
+    """lbm_set_geometry with the walls unchanged (only the drop, or a host rho0) keeps the walls
+    on the device and resets the state: the context then steps bit for bit like a fresh one given
+    that geometry and start, and its node classes and wall potentials are unchanged; a change of
+    one wall field (the wall potential) afterwards rebuilds the walls."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=96, ny=64, cx=48, R=20, drop_x=48, drop_y=34.5, drop_r=14)
+    cfg.interp_bb = interp
+    walls = dict(circle=(cfg.cx, cfg.cy, cfg.R), mu_circle=cfg.mu_circle, mu_bottom=cfg.mu_bottom,
+                 mu_top=cfg.mu_top, boundary=interp)
+    lat = gpu_lattice(lbm, cfg)
+    lat.step(60)
+    flags0, muw0, _ = lat.geometry()
+    # a new drop on the same walls
+    cfg.drop_x, cfg.drop_r = 40.0, 12.0
+    lat.set_geometry(**walls, drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W))
+    flags1, muw1, _ = lat.geometry()
+    assert np.array_equal(flags0, flags1) and np.array_equal(muw0, muw1)
+    fresh = gpu_lattice(lbm, cfg)
+    lat.step(75)
+    fresh.step(75)
+    assert np.array_equal(lat.rho(), fresh.rho())
+    # a host density field on the same walls
+    rho0 = fresh.rho()
+    lat.set_geometry(**walls, drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W), rho0=rho0)
+    fresh.set_geometry(**walls, drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W), rho0=rho0)
+    lat.step(40)
+    fresh.step(40)
+    assert np.array_equal(lat.rho(), fresh.rho())
+    fresh.close()
+    # one wall field changed: the walls are rebuilt
+    cfg.mu_circle = cfg.mu_circle + 0.02
+    walls["mu_circle"] = cfg.mu_circle
+    lat.set_geometry(**walls, drop=(cfg.drop_x, cfg.drop_y, cfg.drop_r, cfg.drop_W))
+    fresh = gpu_lattice(lbm, cfg)
+    assert not np.array_equal(lat.geometry()[1], muw0)
+    assert np.array_equal(lat.geometry()[1], fresh.geometry()[1])
+    lat.step(50)
+    fresh.step(50)
+    assert np.array_equal(lat.rho(), fresh.rho())
+    fresh.close()
+    lat.close()
+
+
 def _concave_cfg(O):
     """Drop started as a near-hemispherical cap at the bottom of a circular cavity (Fig. 2b) of
     radius 60 in a 160 x 100 domain (cut by the top wall), on a hydrophilic wall."""
