@@ -324,6 +324,10 @@ struct Conv {
     // pixels; w_tma false: gathered with cp.async
     bool w_tma = false;
     CUtensorMap wmap[3] = {};
+    // weight gradient from one staged input window per slice (k_gemm_wwin): C_in / 32 when it
+    // applies (1 or 2), else 0; maps: sources 1 and 2 (32 channels x 72 pixels x 3 rows), dY
+    int ww_cb = 0;
+    CUtensorMap wwmap[3] = {};
 };
 
 struct Tensor {
@@ -620,8 +624,62 @@ cudaError_t gemm_wgrad_tma(cudaStream_t st, const GemmArgs& a, int splits, const
     }
 }
 
+// Launch of k_gemm_wwin over `splits` K ranges (one CTA each).
+template <int BN, int CB>
+cudaError_t launch_wwin(cudaStream_t st, const GemmArgs& a, int splits, const CUtensorMap* maps) {
+    constexpr int STAGES = 4;
+    constexpr int STAGE = CB * 4 * 72 * 64 + BN * 128;
+    constexpr int RAW = 1024 + STAGES * STAGE + 8 * (2 * STAGES + 1) + 16;
+    constexpr int CTAS = 512 / (int)lbm::sgtc::tmem_pow2(3 * CB * BN);
+    constexpr int MINB = 233472 / (CTAS + 1) + 1;
+    constexpr int SMEM = RAW > MINB ? RAW : MINB;
+    auto* kern = lbm::sgtc::k_gemm_wwin<BN, CB, STAGES>;
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        configured.fetch_or(bit);
+    }
+    int* flag = tc_flag().dev;
+    if (!flag) return cudaErrorMemoryAllocation;
+    kern<<<splits, lbm::sgtc::TC_THREADS, SMEM, st>>>(a, flag, maps[0], maps[1], maps[2]);
+    return cudaGetLastError();
+}
+
+// The weight gradient through k_gemm_wwin (a: the transposed, gathered form of gemm_wgrad):
+// K ranges of at least 16 slices, at most two per SM, their partials summed in order.
+cudaError_t gemm_wgrad_window(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
+                              float* out, int cb, const CUtensorMap* maps) {
+    const long long stride = (long long)a.N * a.ldc;
+    const int slices = a.K / 64;
+    int splits = std::max(1, std::min(304, slices / 16));
+    while (splits > 1 && (size_t)splits * stride > scratch_elems) splits /= 2;
+    const int chunk = (slices + splits - 1) / splits * 64;
+    splits = (a.K + chunk - 1) / chunk;
+    a.kchunk = chunk;
+    a.split_stride = splits > 1 ? stride : 0;
+    a.Cf = splits > 1 ? scratch : out;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (a.N == 32 && cb == 1) e = launch_wwin<32, 1>(st, a, splits, maps);
+    if (a.N == 32 && cb == 2) e = launch_wwin<32, 2>(st, a, splits, maps);
+    if (a.N == 64 && cb == 1) e = launch_wwin<64, 1>(st, a, splits, maps);
+    if (a.N == 64 && cb == 2) e = launch_wwin<64, 2>(st, a, splits, maps);
+    if (e != cudaSuccess || splits == 1) return e;
+    if (stride % 4 == 0 && ((uintptr_t)out & 15) == 0)
+        k_splitk_sum4<<<(unsigned)((stride / 4 + 31) / 32), 256, 0, st>>>(scratch, splits, stride,
+                                                                          stride, out);
+    else
+        k_splitk_sum<<<blocks_for(stride), kT, 0, st>>>(scratch, splits, stride, stride, out);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
-                       float* out, bool gather, const CUtensorMap* maps = nullptr) {
+                       float* out, bool gather, const CUtensorMap* maps = nullptr,
+                       int ww_cb = 0, const CUtensorMap* wwmaps = nullptr) {
     if (gather) {
         // rows: the 9 C_in im2col columns; columns: C_out; a.ldc (= 9 C_in) stays the row
         // length of dW, written at dW[n * ldc + m]
@@ -632,6 +690,7 @@ cudaError_t gemm_wgrad(cudaStream_t st, GemmArgs a, float* scratch, size_t scrat
         t.ldb = a.lda;
         t.tout = 1;
         a = t;
+        if (ww_cb) return gemm_wgrad_window(st, a, scratch, scratch_elems, out, ww_cb, wwmaps);
     }
     // enough K slices for every SM to hold as many CTAs as fit (three of the narrow tiles, two
     // of the wide ones): each CTA keeps only two K-slices of gathers in flight
@@ -842,6 +901,15 @@ void make_tensor_maps(lbm_surrogate* s) {
             (c.src2 < 0 || map_nhwc(&c.fmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, bw, bh, fk)) &&
             map_rows(&c.fmap[2], s->wb + c.w_off, 9 * cin, c.Cout, pick_bn(c.Cout), fk))
             c.f_ks = fk;
+        if (W % 64 == 0 && c.C1 % 32 == 0 && c.C2 % 32 == 0 && (cin == 32 || cin == 64) &&
+            (c.Cout == 32 || c.Cout == 64)) {
+            const int wc = cin / 32;
+            if (map_nhwc(&c.wwmap[0], s->t[c.src1].y, c.C1, W, H, s->maxB, 72, 3, 32) &&
+                (c.src2 < 0 ||
+                 map_nhwc(&c.wwmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, 72, 3, 32)) &&
+                map_nhwc(&c.wwmap[2], s->gmask, c.Cout, W, H, s->maxB, 64, 1, 32))
+                c.ww_cb = wc;
+        }
         if (W % 64 == 0 || 64 % W == 0) {
             const int ww = std::min(W, 64), wh = 64 / ww;
             c.w_tma = c.C1 % 32 == 0 && c.C2 % 32 == 0 && c.Cout % 32 == 0 &&
@@ -1085,7 +1153,7 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
         gw.ldb = 9 * Cin;
         gw.ldc = 9 * Cin;
         SCUDA(s, gemm_wgrad(s->stream, gw, s->splitk, s->splitk_elems, s->g + c.w_off, gather,
-                            gather && c.w_tma ? c.wmap : nullptr));
+                            gather && c.w_tma ? c.wmap : nullptr, gather ? c.ww_cb : 0, c.wwmap));
         // data gradient (not needed for the input tensor)
         if (c.src1 == 0) continue;
         // implicit GEMM over the source pixels: dX_src[q][ci] += sum over (sub-pixel, tap, co)

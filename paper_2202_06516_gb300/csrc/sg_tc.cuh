@@ -762,5 +762,160 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// shared-memory descriptor of an MN-major, 64-byte-swizzled operand whose 32-wide blocks are
+// lbo bytes apart (K-groups of 8 rows 512 B apart); the start may lie on any 64-byte row, the
+// swizzle follows the absolute shared-memory address
+__device__ __forceinline__ uint64_t desc_sw64_mn_lbo(uint32_t saddr, uint32_t lbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+__host__ __device__ constexpr uint32_t tmem_pow2(int cols) {
+    return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+}
+
+// Weight gradient of a 3 x 3 convolution with C_in = 32 CB input channels from one staged input
+// window per K slice: dW^T[(tap, ci)][co] = sum over pixels p of x(p + off(tap))[ci] dY(p)[co]
+// (K = pixels of one image row segment, 64 per slice; each CTA one split-K range, grid = splits).
+// Per slice thread 0 loads with TMA, for each 32-channel block, the input rows y - 1 .. y + 1 of
+// pixels x - 4 .. x + 67 (64-byte-swizzled rows of 32 channels: the MN-major layout with K =
+// pixels), and the 32-channel blocks of dY for the 64 pixels. The nine taps are then MN-major A
+// operands that start a whole number of rows into that window (dx) with the three dy rows as their
+// first three 32-wide M blocks (4,608 B apart; the fourth block reads a row that is not loaded and
+// its outputs are dropped): accumulator tile (block cb, dx) in tensor-memory columns
+// (3 cb + dx + 1) BN. Every input element is read once per slice instead of once per tap. The
+// epilogue writes the split's FP32 partial transposed, dW^T row tap C_in + ci.
+template <int BN, int CB, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_wwin(const sg::GemmArgs g, int* err, const __grid_constant__ CUtensorMap tmX1,
+                const __grid_constant__ CUtensorMap tmX2, const __grid_constant__ CUtensorMap tmDY) {
+    static_assert(BN % 32 == 0 && 3 * CB * BN <= 512, "accumulators must fit tensor memory");
+    constexpr int T = 3 * CB, WROW = 72, WIN = 4 * WROW * 64;
+    constexpr int A_B = CB * WIN, B_B = BN * 128, STAGE = A_B + B_B;
+    constexpr uint32_t TX = (uint32_t)(CB * 3 * WROW * 64 + B_B);
+    constexpr uint32_t COLS = tmem_pow2(T * BN);
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kb = blockIdx.x * g.kchunk, ke = min(g.K, kb + g.kchunk);
+    const int nk = ke > kb ? (ke - kb) / 64 : 0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         su32(tmem_slot)),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i <= 2 * STAGES; ++i) mbar_init(su32(bars + i), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_ok = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t IDESC = idesc_bf16(BM, BN, 1, 1);
+    const int H = g.conv.H, W = g.conv.W;
+    auto win = [&](int st, int cb) { return su32(base + st * STAGE + cb * WIN); };
+    auto dyb = [&](int st) { return su32(base + st * STAGE + A_B); };
+    auto issue = [&](int st, int k0) {
+        const uint32_t full = su32(bars + st);
+        mbar_expect_tx(full, TX);
+        const int pn = k0 / (H * W), pr = k0 - pn * (H * W);
+        const int py = pr / W, px = pr - (pr / W) * W;
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) {
+            const int ci = 32 * cb;
+            if (ci < g.conv.C1)
+                tma_load_4d(win(st, cb), &tmX1, full, ci, px - 4, py - 1, pn);
+            else
+                tma_load_4d(win(st, cb), &tmX2, full, ci - g.conv.C1, px - 4, py - 1, pn);
+        }
+#pragma unroll
+        for (int b = 0; b < BN / 32; ++b) tma_load_4d(dyb(st) + 4096 * b, &tmDY, full, 32 * b, px, py, pn);
+    };
+    if (tid == 0) {
+        int issued = 0, done_mma = 0;
+        bool good = true;
+        for (; issued < STAGES && issued < nk; ++issued) issue(issued, kb + issued * 64);
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % STAGES;
+            if (!mbar_wait(su32(bars + st), (kt / STAGES) & 1)) {
+                good = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int cb = t / 3, dxi = t - 3 * (t / 3);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t ad =
+                        desc_sw64_mn_lbo(win(st, cb) + (uint32_t)((3 + dxi) * 64 + 1024 * j), WROW * 64);
+                    const uint64_t bd = desc_sw64_mn(dyb(st) + 1024 * j);
+                    tc_mma(tmem + (uint32_t)(t * BN), ad, bd, IDESC, (kt > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            tc_commit(su32(bars + STAGES + st));
+            done_mma = kt + 1;
+            if (kt >= 1 && issued < nk) {
+                const int sp = (kt - 1) % STAGES;
+                if (!mbar_wait(su32(bars + STAGES + sp), ((kt - 1) / STAGES) & 1)) {
+                    good = false;
+                    break;
+                }
+                issue(sp, kb + issued * 64);
+                ++issued;
+            }
+        }
+        if (!good)
+            for (int j = done_mma; j < issued; ++j) mbar_wait(su32(bars + j % STAGES), (j / STAGES) & 1);
+        if (nk > 0) {
+            tc_commit(su32(bars + 2 * STAGES));
+            if (!mbar_wait(su32(bars + 2 * STAGES), 0)) good = false;
+        }
+        if (!good) s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else if (warp < 3) {
+        // warp w holds M block w: dy = w - 1, lane = channel within the block
+        tc_fence_after();
+        const size_t zoff = (size_t)blockIdx.x * g.split_stride;
+        const int cin = 32 * CB;
+#pragma unroll 1
+        for (int t = 0; t < T; ++t) {
+            const int cb = t / 3, dxi = t - 3 * (t / 3);
+            const int m = (warp * 3 + dxi) * cin + 32 * cb + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                float v[32];
+                if (nk == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                } else {
+                    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * BN + c0), v);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < g.N) g.Cf[(size_t)(c0 + j) * g.ldc + m + zoff] = v[j];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace sgtc
 }  // namespace lbm
