@@ -10,9 +10,12 @@
 //   head      1x1 conv to one channel, sigmoid: phi = (rho - rho_g) / (rho_l - rho_g)
 // Activations BF16 NHWC, weights FP32 masters with BF16 copies, all contractions on the tcgen05
 // tensor cores with FP32 accumulation in tensor memory (sg_tc.cuh), as implicit GEMMs whose
-// loaders gather the 3 x 3 neighbourhoods from the activations: the forward convolution, the
+// operands are the 3 x 3 neighbourhoods of the activations: the forward convolution, the
 // weight gradient (pixels as K; an im2col buffer only when the resolution is not a power of two)
-// and the data gradient (output gradients gathered around each source pixel).
+// and the data gradient (output gradients around each source pixel). Where the shapes allow,
+// the operands arrive as tensor-map (TMA) boxes built once per network (make_tensor_maps): the
+// tap's offset moves the box, the image border is zero-filled, upsampling layers order their
+// rows or K even/odd or read every second pixel; elsewhere the loaders gather with cp.async.
 // Loss: masked mean squared error on phi. Optimiser: Adam.
 #include <math.h>
 

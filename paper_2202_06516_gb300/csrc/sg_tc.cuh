@@ -4,14 +4,17 @@
 // weight copy, the data gradient dY W (both K-major), and the weight gradient dY^T Xcol (both
 // MN-major, K = pixels).
 //
-// One CTA of 128 threads computes a 128 x BN tile. All threads stage K-slices of 64 elements
-// into shared memory with cp.async, in the 128-byte-swizzled K-major layout the tensor core
-// reads (8-row atoms of 1 KB; the 16-byte chunk c of row r stored at chunk c ^ (r % 8)); STAGES
-// slices are in flight. Thread 0 issues four 128 x BN x 16 MMAs per slice (kind::f16, BF16 in,
+// One CTA of 128 threads computes a 128 x BN tile. Its K-slices reach shared memory either as
+// cp.async gathers by all threads (TMA = 0), in the 128-byte-swizzled K-major layout the tensor
+// core reads (8-row atoms of 1 KB; the 16-byte chunk c of row r stored at chunk c ^ (r % 8)), or
+// as tensor-map (TMA) boxes issued by thread 0 (TMA = 64 / 32: K-major slices of 64 or 32
+// elements, 128- or 64-byte swizzle; TMA = 1: the weight gradient's MN-major blocks), STAGES
+// slices in flight. Thread 0 issues the 128 x BN x 16 MMAs of each slice (kind::f16, BF16 in,
 // FP32 accumulate into BN tensor-memory columns) and commits them to the slice's mbarrier,
 // which frees the slice for the next load. The epilogue reads the accumulator lanes back with
 // tcgen05.ld (warp w owns rows 32 w .. 32 w + 31), adds the bias, applies the leaky ReLU and
-// stores FP32 or BF16.
+// stores FP32 or BF16. k_gemm_wwin computes the weight gradient of the 32/64-channel levels from
+// one staged input window per slice.
 //
 // Every wait on an mbarrier is polled by one thread with an iteration limit; on expiry the
 // CTA sets *err, waits (bounded) for the MMAs it issued, frees its tensor memory and returns.
