@@ -325,11 +325,12 @@ def run_reference(args):
     steps = max(1, min(args.steps, 200))
     warm = max(0, min(args.warmup, 3))
     cb = cpu_baseline(steps)
-    return {"metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": 0,
+    return {"metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": cb["seconds"] * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name.rsplit("-s", 1)[0], "nx": w.nx, "ny": w.ny},
+            "config": {"workload": w.name.rsplit("-s", 1)[0], "nx": w.nx, "ny": w.ny,
+                       "device": "host cores (FP64 oracle), rank 0 only"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
