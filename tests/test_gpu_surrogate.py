@@ -96,7 +96,7 @@ def _bf16(a):
     return torch.tensor(a).to(torch.bfloat16).double().numpy()
 
 
-def _gpu_and_oracle(env, x, t, m, p, base, H):
+def _gpu_and_oracle(env, x, t, m, p, base, H, Wd=None):
     """One GPU training step without update (gradients only) and the oracle on the same BF16
     inputs and weights the GPU used (convolution weights rounded to BF16; biases and the head
     stay FP32, as in the GPU epilogue and head), in three modes: FP64 throughout, BF16
@@ -104,7 +104,7 @@ def _gpu_and_oracle(env, x, t, m, p, base, H):
     GPU stores in BF16)."""
     torch, lbm = env
     from oracle import surrogate as S
-    s = lbm.Surrogate(H, H, base=base, max_batch=2)
+    s = lbm.Surrogate(H, Wd or H, base=base, max_batch=2)
     assert s.n == p.size
     s.set_weights(p)
     nb = x.shape[0]
@@ -178,7 +178,15 @@ def test_tma_fed_levels_at_full_resolution(env):
     _per_layer_check(env, 32, 256, "positive", B=1)
 
 
-def _per_layer_check(env, base, H, regime, B=2):
+def test_tma_fed_levels_on_a_rectangular_lattice(env):
+    """128 rows x 256 columns, base 32, one image: tiles of whole rows (or half rows) of a
+    non-square image through every tensor-map path (forward, data and weight gradients, the
+    upsampling layers' even/odd orders, the staged-window weight gradient); the per-layer check
+    of test_gradients_match_bf16_oracle_per_layer."""
+    _per_layer_check(env, 32, 128, "positive", B=1, Wd=256)
+
+
+def _per_layer_check(env, base, H, regime, B=2, Wd=None):
     """Every layer's weight and bias gradient against the oracle that stores activations and
     pre-activation gradients in BF16 as the GPU does, with weights chosen so that every
     pre-activation keeps one sign with a wide margin (positive: weights x 0.1, biases +1;
@@ -194,14 +202,14 @@ def _per_layer_check(env, base, H, regime, B=2):
     farther from the GPU, so that mode is what the GPU computes."""
     torch, _ = env
     from oracle import surrogate as S
-    x, t, m, p = _case(base=base, H=H, Wd=H, B=B)
+    x, t, m, p = _case(base=base, H=H, Wd=Wd or H, B=B)
     scale, bias = (0.1, 1.0) if regime == "positive" else (0.25, -1.0)
     p = p.copy()
     layers, head = _layers(base)
     for sw, sb in layers:
         p[sw] *= scale
         p[sb] = bias
-    gpu, ref, pw, xb = _gpu_and_oracle(env, x, t, m, p, base, H)
+    gpu, ref, pw, xb = _gpu_and_oracle(env, x, t, m, p, base, H, Wd)
     rec = []
     S.forward(torch.tensor(pw), torch.tensor(xb), base, bf16_activations=True, record=rec)
     margin = min(float(z.abs().min()) for z in rec)
