@@ -331,6 +331,12 @@ struct Conv {
     // applies (1 or 2), else 0; maps: sources 1 and 2 (32 channels x 72 pixels x 3 rows), dY
     int ww_cb = 0;
     CUtensorMap wwmap[3] = {};
+    // forward (fw) and data gradient (dw) from one staged window per tile of 128 pixels of one
+    // row (k_gemm_fwin): 32-channel blocks of the window operand (1 where it applies, else 0)
+    // and the N tile; maps: source 1 (dY for dw) as boxes of 32 channels x 136 pixels x 3 rows,
+    // source 2 likewise, and the weights as 32 x N-tile blocks
+    int fw_cb = 0, fw_bn = 0, dw_cb = 0, dw_bn = 0;
+    CUtensorMap fwmap[3] = {}, dwmap[3] = {};
 };
 
 struct Tensor {
@@ -653,6 +659,38 @@ cudaError_t launch_wwin(cudaStream_t st, const GemmArgs& a, int splits, const CU
     return cudaGetLastError();
 }
 
+// Launch of k_gemm_fwin: one CTA per tile of 128 pixels x BN columns.
+template <int BN, int CB, bool GD>
+cudaError_t launch_fwin(cudaStream_t st, const GemmArgs& a, const CUtensorMap* maps) {
+    constexpr int SMEM = 1024 + CB * 3 * 136 * 64 + 9 * CB * BN * 64 + 32;
+    auto* kern = lbm::sgtc::k_gemm_fwin<BN, CB, GD>;
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        configured.fetch_or(bit);
+    }
+    int* flag = tc_flag().dev;
+    if (!flag) return cudaErrorMemoryAllocation;
+    dim3 grid(a.N / BN, a.M / lbm::sgtc::BM);
+    kern<<<grid, lbm::sgtc::TC_THREADS, SMEM, st>>>(a, flag, maps[0], maps[1], maps[2]);
+    return cudaGetLastError();
+}
+
+// The window-fed forward (GD false) or data gradient of a convolution that qualifies (see
+// Conv::fw_cb / dw_cb): a.M a multiple of 128, a.N of bn.
+template <bool GD>
+cudaError_t gemm_fwin(cudaStream_t st, const GemmArgs& a, int cb, int bn, const CUtensorMap* maps) {
+    if (a.M % lbm::sgtc::BM || a.N % bn) return cudaErrorInvalidValue;
+    if (cb == 1 && bn == 32) return launch_fwin<32, 1, GD>(st, a, maps);
+    if (cb == 1 && bn == 64) return launch_fwin<64, 1, GD>(st, a, maps);
+    return cudaErrorInvalidValue;
+}
+
 // The weight gradient through k_gemm_wwin (a: the transposed, gathered form of gemm_wgrad):
 // K ranges of at least 16 slices, at most two per SM, their partials summed in order.
 cudaError_t gemm_wgrad_window(cudaStream_t st, GemmArgs a, float* scratch, size_t scratch_elems,
@@ -843,8 +881,11 @@ lbm_status forward(lbm_surrogate* s, const bf16* x, int B) {
         g.bias = s->w + c.b_off;
         g.relu = 1;
         if (c.up1 && c.f_ks) g.rperm = std::min(c.W, 128) / 2;
-        SCUDA(s, (gemm_tc_split<true, false>(s->stream, g, s->splitk, s->splitk_elems, c.fmap,
-                                              c.f_ks)));
+        if (c.fw_cb)
+            SCUDA(s, gemm_fwin<false>(s->stream, g, c.fw_cb, c.fw_bn, c.fwmap));
+        else
+            SCUDA(s, (gemm_tc_split<true, false>(s->stream, g, s->splitk, s->splitk_elems, c.fmap,
+                                                  c.f_ks)));
         // a pool whose source is this conv's output runs right after it
         for (const auto& pl : s->pools)
             if (pl.first == c.out) {
@@ -904,6 +945,25 @@ void make_tensor_maps(lbm_surrogate* s) {
             (c.src2 < 0 || map_nhwc(&c.fmap[1], s->t[c.src2].y, c.C2, W, H, s->maxB, bw, bh, fk)) &&
             map_rows(&c.fmap[2], s->wb + c.w_off, 9 * cin, c.Cout, pick_bn(c.Cout), fk))
             c.f_ks = fk;
+        // window-fed forward and data gradient: 128-pixel row segments, a window operand of 32
+        // channels (the input for the forward, dY for the data gradient) and 32 or 64 output
+        // columns (at most 64 KB of shared memory, three or four CTAs per SM). With 64 window
+        // channels (90 KB and two CTAs per SM, each loading, multiplying and storing in turn,
+        // or one CTA per SM at N = 64) the pipelined TMA path is faster, so those keep it.
+        if (W % 128 == 0 && (long long)s->maxB * H * W / 128 <= 65535) {
+            if (cin == 32 && c.C2 == 0 && (c.Cout == 32 || c.Cout == 64) &&
+                map_nhwc(&c.fwmap[0], s->t[c.src1].y, c.C1, W, H, s->maxB, 136, 3, 32) &&
+                map_rows(&c.fwmap[2], s->wb + c.w_off, 9 * cin, c.Cout, c.Cout, 32)) {
+                c.fw_cb = 1;
+                c.fw_bn = c.Cout;
+            }
+            if (c.Cout == 32 && c.C1 % 32 == 0 && c.C2 % 32 == 0 && (cin == 32 || cin == 64) &&
+                map_nhwc(&c.dwmap[0], s->gmask, c.Cout, W, H, s->maxB, 136, 3, 32) &&
+                map_rows(&c.dwmap[2], s->wbd + c.w_off, 9 * c.Cout, cin, cin, 32)) {
+                c.dw_cb = 1;
+                c.dw_bn = cin;
+            }
+        }
         if (W % 64 == 0 && c.C1 % 32 == 0 && c.C2 % 32 == 0 && (cin == 32 || cin == 64) &&
             (c.Cout == 32 || c.Cout == 64)) {
             const int wc = cin / 32;
@@ -1182,8 +1242,11 @@ lbm_status lbm_surrogate_train_step(lbm_surrogate* s, const void* xin, const flo
             gd.ldc2 = c.C2;
             gd.nsplit = c.C1;
         }
-        SCUDA(s, (gemm_tc_split<false, true>(s->stream, gd, s->splitk, s->splitk_elems, c.dmap,
-                                              c.d_ks)));
+        if (c.dw_cb)
+            SCUDA(s, gemm_fwin<true>(s->stream, gd, c.dw_cb, c.dw_bn, c.dwmap));
+        else
+            SCUDA(s, (gemm_tc_split<false, true>(s->stream, gd, s->splitk, s->splitk_elems,
+                                                  c.dmap, c.d_ks)));
     }
     if (lr > 0.f) {
         ++s->adam_t;

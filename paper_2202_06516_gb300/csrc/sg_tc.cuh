@@ -317,6 +317,163 @@ __device__ __forceinline__ void load_slice_mn_conv_a(uint8_t* s, const sg::ConvG
     }
 }
 
+// Epilogue of one 128 x BN output tile whose FP32 accumulator sits in tensor-memory columns
+// tacc .. tacc + BN - 1 (zero: no K slices, the result is 0). Warp `warp` (0 .. 3) reads
+// accumulator lanes 32 warp .. 32 warp + 31 (rows m0 + 32 warp ..) and passes them through its
+// own 32 x 32 staging block ep (rows 144 B apart), so that stores write whole row segments:
+// 16-byte vectors when the output allows (no accumulation or split, aligned rows), else one
+// column per lane; bias, leaky ReLU, BF16 or FP32 (accumulated, split at nsplit, or transposed)
+// as the arguments say. zoff: the split-K partial's offset.
+template <int BN>
+__device__ __forceinline__ void epilogue_tile(const sg::GemmArgs& g, uint32_t tacc, float* ep,
+                                              int warp, int lane, int m0, int n0, bool zero,
+                                              size_t zoff) {
+    // FP32 outputs may accumulate and may be split at column nsplit into two tensors; the
+    // vector path then takes a 32-column chunk that lies on one side of the split
+    const bool vec = !g.kchunk &&
+                     (g.Cb ? (!g.accumulate && g.ldc % 8 == 0 && ((uintptr_t)g.Cb & 15) == 0)
+                           : (g.ldc % 4 == 0 && ((uintptr_t)g.Cf & 15) == 0 &&
+                              (!g.Cf2 || (g.ldc2 % 4 == 0 && g.nsplit % 4 == 0 &&
+                                          ((uintptr_t)g.Cf2 & 15) == 0))));
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= g.N) break;
+        const int w = BN - c0 >= 32 ? 32 : 16;
+        float v[32];
+        const uint32_t ta = tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        if (zero) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        } else if (w == 32) {
+            tc_ld32(ta, v);
+        } else {
+            tc_ld16(ta, v);
+        }
+        if (g.tout) {
+            // transposed FP32 store: for each column, the warp's 32 rows are consecutive
+            const int m = m0 + warp * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + c0 + j;
+                if (j >= w || n >= g.N || m >= g.M) continue;
+                float* o = g.Cf + (size_t)n * g.ldc + m + zoff;
+                *o = g.accumulate ? *o + v[j] : v[j];
+            }
+            continue;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+            if (j < w)
+                *reinterpret_cast<float4*>(ep + lane * 36 + j) =
+                    make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        __syncwarp();
+        const bool one_side = !g.Cf2 || n0 + c0 + 32 <= g.nsplit || n0 + c0 >= g.nsplit;
+        if (vec && w == 32 && n0 + c0 + 32 <= g.N && one_side) {
+            if (g.Cb) {
+                // lane: row it * 8 + lane / 4, columns 8 (lane % 4) .. + 7
+                const int cc = 8 * (lane & 3), n = n0 + c0 + cc;
+                float bn[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int r = it * 8 + (lane >> 2);
+                    const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
+                    if (m >= g.M) continue;
+                    const float4 x0 = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
+                    const float4 x1 = *reinterpret_cast<const float4*>(ep + r * 36 + cc + 4);
+                    float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                    uint4 o;
+                    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) {
+                        float a0 = x[j] + bn[j], a1 = x[j + 1] + bn[j + 1];
+                        if (g.relu) {
+                            a0 = fmaxf(a0, 0.1f * a0);
+                            a1 = fmaxf(a1, 0.1f * a1);
+                        }
+                        oh[j / 2] = __floats2bfloat162_rn(a0, a1);
+                    }
+                    *reinterpret_cast<uint4*>(g.Cb + (size_t)m * g.ldc + n) = o;
+                }
+            } else {
+                // lane: row it * 4 + lane / 8, columns 4 (lane % 8) .. + 3
+                const int cc = 4 * (lane & 7), n = n0 + c0 + cc;
+                float bn[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
+                // destination of row it * 4 + lane / 8; with accumulation all eight old
+                // values are loaded before the first store, so their latencies overlap
+                auto dst_of = [&](int it) {
+                    const int m = m0 + sg::row_pixel(warp * 32 + it * 4 + (lane >> 3), g.rperm);
+                    return (g.Cf2 && n >= g.nsplit)
+                               ? reinterpret_cast<float4*>(g.Cf2 + (size_t)m * g.ldc2 +
+                                                           (n - g.nsplit))
+                               : reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n);
+                };
+                float4 old[8];
+                if (g.accumulate) {
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int m = m0 + sg::row_pixel(warp * 32 + it * 4 + (lane >> 3), g.rperm);
+                        old[it] = m < g.M ? *dst_of(it) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int r = it * 4 + (lane >> 3);
+                    const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
+                    if (m >= g.M) continue;
+                    float4 x = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
+                    x.x += bn[0];
+                    x.y += bn[1];
+                    x.z += bn[2];
+                    x.w += bn[3];
+                    if (g.relu) {
+                        x.x = fmaxf(x.x, 0.1f * x.x);
+                        x.y = fmaxf(x.y, 0.1f * x.y);
+                        x.z = fmaxf(x.z, 0.1f * x.z);
+                        x.w = fmaxf(x.w, 0.1f * x.w);
+                    }
+                    if (g.accumulate) {
+                        x.x += old[it].x;
+                        x.y += old[it].y;
+                        x.z += old[it].z;
+                        x.w += old[it].w;
+                    }
+                    *dst_of(it) = x;
+                }
+            }
+        } else {
+            const int n = n0 + c0 + lane;
+            const bool col_ok = lane < w && n < g.N;
+            const float bn = (col_ok && g.bias) ? g.bias[n] : 0.f;
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+                const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
+                if (!col_ok || m >= g.M) continue;
+                float x = ep[r * 36 + lane] + bn;
+                if (g.relu) x = fmaxf(x, 0.1f * x);
+                float* cf = g.Cf;
+                size_t o = (size_t)m * g.ldc + n + zoff;
+                if (g.Cf2 && n >= g.nsplit) {
+                    cf = g.Cf2;
+                    o = (size_t)m * g.ldc2 + (n - g.nsplit);
+                }
+                if (cf) {
+                    if (g.accumulate)
+                        cf[o] += x;
+                    else
+                        cf[o] = x;
+                } else {
+                    g.Cb[o] = __float2bfloat16_rn(x);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // GA: A is the gathered convolution operand (K-major, rows = output pixels); GD: A is the
 // gathered data-gradient operand; GAM: A is the gathered convolution operand MN-major (K =
 // pixels, M = im2col columns).
@@ -605,155 +762,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (tid == 0) atomicExch(err, 1);
     } else {
         tc_fence_after();
-        // accumulator rows go through a per-warp 32 x 32 staging block (rows 144 B apart) in the
-        // now idle stage buffers, so that stores write whole row segments: 16-byte vectors when
-        // the output allows (no accumulation or split, aligned rows), else one column per lane
-        float* ep = reinterpret_cast<float*>(base) + warp * (32 * 36);
-        const size_t zoff = g.kchunk ? (size_t)blockIdx.z * g.split_stride : 0;
-        // FP32 outputs may accumulate and may be split at column nsplit into two tensors; the
-        // vector path then takes a 32-column chunk that lies on one side of the split
-        const bool vec = !g.kchunk &&
-                         (g.Cb ? (!g.accumulate && g.ldc % 8 == 0 && ((uintptr_t)g.Cb & 15) == 0)
-                               : (g.ldc % 4 == 0 && ((uintptr_t)g.Cf & 15) == 0 &&
-                                  (!g.Cf2 || (g.ldc2 % 4 == 0 && g.nsplit % 4 == 0 &&
-                                              ((uintptr_t)g.Cf2 & 15) == 0))));
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            if (n0 + c0 >= g.N) break;
-            const int w = BN - c0 >= 32 ? 32 : 16;
-            float v[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            if (nk == 0) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.f;
-            } else if (w == 32) {
-                tc_ld32(ta, v);
-            } else {
-                tc_ld16(ta, v);
-            }
-            if (g.tout) {
-                // transposed FP32 store: for each column, the warp's 32 rows are consecutive
-                const int m = m0 + warp * 32 + lane;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (j >= w || n >= g.N || m >= g.M) continue;
-                    float* o = g.Cf + (size_t)n * g.ldc + m + zoff;
-                    *o = g.accumulate ? *o + v[j] : v[j];
-                }
-                continue;
-            }
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-                if (j < w)
-                    *reinterpret_cast<float4*>(ep + lane * 36 + j) =
-                        make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            __syncwarp();
-            const bool one_side = !g.Cf2 || n0 + c0 + 32 <= g.nsplit || n0 + c0 >= g.nsplit;
-            if (vec && w == 32 && n0 + c0 + 32 <= g.N && one_side) {
-                if (g.Cb) {
-                    // lane: row it * 8 + lane / 4, columns 8 (lane % 4) .. + 7
-                    const int cc = 8 * (lane & 3), n = n0 + c0 + cc;
-                    float bn[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
-#pragma unroll
-                    for (int it = 0; it < 4; ++it) {
-                        const int r = it * 8 + (lane >> 2);
-                        const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
-                        if (m >= g.M) continue;
-                        const float4 x0 = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
-                        const float4 x1 = *reinterpret_cast<const float4*>(ep + r * 36 + cc + 4);
-                        float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                        uint4 o;
-                        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-                        for (int j = 0; j < 8; j += 2) {
-                            float a0 = x[j] + bn[j], a1 = x[j + 1] + bn[j + 1];
-                            if (g.relu) {
-                                a0 = fmaxf(a0, 0.1f * a0);
-                                a1 = fmaxf(a1, 0.1f * a1);
-                            }
-                            oh[j / 2] = __floats2bfloat162_rn(a0, a1);
-                        }
-                        *reinterpret_cast<uint4*>(g.Cb + (size_t)m * g.ldc + n) = o;
-                    }
-                } else {
-                    // lane: row it * 4 + lane / 8, columns 4 (lane % 8) .. + 3
-                    const int cc = 4 * (lane & 7), n = n0 + c0 + cc;
-                    float bn[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) bn[j] = g.bias ? g.bias[n + j] : 0.f;
-                    // destination of row it * 4 + lane / 8; with accumulation all eight old
-                    // values are loaded before the first store, so their latencies overlap
-                    auto dst_of = [&](int it) {
-                        const int m = m0 + sg::row_pixel(warp * 32 + it * 4 + (lane >> 3), g.rperm);
-                        return (g.Cf2 && n >= g.nsplit)
-                                   ? reinterpret_cast<float4*>(g.Cf2 + (size_t)m * g.ldc2 +
-                                                               (n - g.nsplit))
-                                   : reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldc + n);
-                    };
-                    float4 old[8];
-                    if (g.accumulate) {
-#pragma unroll
-                        for (int it = 0; it < 8; ++it) {
-                            const int m = m0 + sg::row_pixel(warp * 32 + it * 4 + (lane >> 3), g.rperm);
-                            old[it] = m < g.M ? *dst_of(it) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-                    }
-#pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int r = it * 4 + (lane >> 3);
-                        const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
-                        if (m >= g.M) continue;
-                        float4 x = *reinterpret_cast<const float4*>(ep + r * 36 + cc);
-                        x.x += bn[0];
-                        x.y += bn[1];
-                        x.z += bn[2];
-                        x.w += bn[3];
-                        if (g.relu) {
-                            x.x = fmaxf(x.x, 0.1f * x.x);
-                            x.y = fmaxf(x.y, 0.1f * x.y);
-                            x.z = fmaxf(x.z, 0.1f * x.z);
-                            x.w = fmaxf(x.w, 0.1f * x.w);
-                        }
-                        if (g.accumulate) {
-                            x.x += old[it].x;
-                            x.y += old[it].y;
-                            x.z += old[it].z;
-                            x.w += old[it].w;
-                        }
-                        *dst_of(it) = x;
-                    }
-                }
-            } else {
-                const int n = n0 + c0 + lane;
-                const bool col_ok = lane < w && n < g.N;
-                const float bn = (col_ok && g.bias) ? g.bias[n] : 0.f;
-#pragma unroll 4
-                for (int r = 0; r < 32; ++r) {
-                    const int m = m0 + sg::row_pixel(warp * 32 + r, g.rperm);
-                    if (!col_ok || m >= g.M) continue;
-                    float x = ep[r * 36 + lane] + bn;
-                    if (g.relu) x = fmaxf(x, 0.1f * x);
-                    float* cf = g.Cf;
-                    size_t o = (size_t)m * g.ldc + n + zoff;
-                    if (g.Cf2 && n >= g.nsplit) {
-                        cf = g.Cf2;
-                        o = (size_t)m * g.ldc2 + (n - g.nsplit);
-                    }
-                    if (cf) {
-                        if (g.accumulate)
-                            cf[o] += x;
-                        else
-                            cf[o] = x;
-                    } else {
-                        g.Cb[o] = __float2bfloat16_rn(x);
-                    }
-                }
-            }
-            __syncwarp();
-        }
+        // the staging blocks lie in the now idle stage buffers
+        epilogue_tile<BN>(g, tmem, reinterpret_cast<float*>(base) + warp * (32 * 36), warp, lane,
+                          m0, n0, nk == 0, g.kchunk ? (size_t)blockIdx.z * g.split_stride : 0);
     }
     tc_fence_before();
     __syncthreads();
@@ -916,6 +927,113 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(COLS)
+                     : "memory");
+    }
+}
+
+// Forward convolution (GA) or data gradient (GD) of a 3 x 3 convolution for a tile of 128
+// output pixels of one image row, from one staged window: with C = 32 CB channels of the operand
+// (the input for GA, concatenated sources by channel; the output gradient for GD), thread 0
+// loads with TMA, per 32-channel block, the rows y - 1 .. y + 1 of pixels x - 4 .. x + 131
+// (K-major rows of 32 channels, 64-byte swizzle) and the tile's 32 x BN weight blocks of all
+// nine taps (output columns BN blockIdx.x ..), all on one mbarrier. Each tap (dy, dx) is then a K-major A operand that starts whole rows into
+// the window (GA: row dy + 1, column 4 + dx; GD: the offsets negated), two 16-deep MMAs per
+// (tap, block) into one accumulator. Every operand element is read once per tile instead of once
+// per tap. The epilogue is the GEMM's own (bias and leaky ReLU with BF16 output, or the
+// accumulating, possibly split FP32 output of the data gradient).
+template <int BN, int CB, bool GD>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_fwin(const sg::GemmArgs g, int* err, const __grid_constant__ CUtensorMap tmA1,
+                const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB) {
+    static_assert((BN == 32 || BN == 64) && (CB == 1 || CB == 2), "32 or 64 columns and channels");
+    constexpr int WROW = 136, WINB = 3 * WROW * 64;  // one 32-channel block of the window
+    constexpr int A_B = CB * WINB, BSUB = BN * 64, B_B = 9 * CB * BSUB;
+    constexpr uint32_t TX = (uint32_t)(A_B + B_B);
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + A_B + B_B);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         su32(tmem_slot)),
+                     "r"(tmem_cols(BN))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(su32(bars), 1);
+        mbar_init(su32(bars + 1), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_ok = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t IDESC = idesc_bf16(BM, BN, 0, 0);
+    const int H = GD ? g.dg.H : g.conv.H, W = GD ? g.dg.W : g.conv.W;
+    const int img = m0 / (H * W), rem = m0 - img * (H * W);
+    const int y0 = rem / W, x0 = rem - (rem / W) * W;
+    const uint32_t A = su32(base), B = su32(base + A_B);
+    if (tid == 0) {
+        bool good = true;
+        const uint32_t full = su32(bars);
+        mbar_expect_tx(full, TX);
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) {
+            const int ci = 32 * cb;
+            if (GD || ci < g.conv.C1)
+                tma_load_4d(A + cb * WINB, &tmA1, full, ci, x0 - 4, y0 - 1, img);
+            else
+                tma_load_4d(A + cb * WINB, &tmA2, full, ci - g.conv.C1, x0 - 4, y0 - 1, img);
+        }
+        for (int t = 0; t < 9; ++t)
+#pragma unroll
+            for (int cb = 0; cb < CB; ++cb)
+                tma_load_2d(B + (t * CB + cb) * BSUB, &tmB, full, (t * CB + cb) * 32, n0);
+        if (!mbar_wait(full, 0)) {
+            good = false;
+            mbar_wait(full, 0);  // let the copies in flight land before the CTA may leave (bounded)
+        }
+        if (good) {
+            tc_fence_after();
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3 - 1, dx = t - (t / 3) * 3 - 1;
+                const int wr = GD ? 1 - dy : 1 + dy, wc = GD ? 4 - dx : 4 + dx;
+#pragma unroll
+                for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t a = A + cb * WINB + (uint32_t)((wr * WROW + wc) * 64 + 32 * j);
+                        const uint32_t b = B + (t * CB + cb) * BSUB + 32 * j;
+                        tc_mma(tmem, desc_sw64(a), desc_sw64(b), IDESC,
+                               (t > 0 || cb > 0 || j > 0) ? 1u : 0u);
+                    }
+            }
+            tc_commit(su32(bars + 1));
+            if (!mbar_wait(su32(bars + 1), 0)) good = false;
+        }
+        if (!good) s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        tc_fence_after();
+        // the staging blocks lie in the window, no longer read
+        epilogue_tile<BN>(g, tmem, reinterpret_cast<float*>(base) + warp * (32 * 36), warp, lane,
+                          m0, n0, false, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(tmem_cols(BN))
                      : "memory");
     }
 }
