@@ -15,7 +15,8 @@
 // and the data gradient (output gradients around each source pixel). Where the shapes allow,
 // the operands arrive as tensor-map (TMA) boxes built once per network (make_tensor_maps): the
 // tap's offset moves the box, the image border is zero-filled, upsampling layers order their
-// rows or K even/odd or read every second pixel; elsewhere the loaders gather with cp.async.
+// rows or K even/odd or read every second pixel; the 32/64-channel levels stage one window per
+// slice or tile and take the nine taps from it; elsewhere the loaders gather with cp.async.
 // Loss: masked mean squared error on phi. Optimiser: Adam.
 #include <math.h>
 

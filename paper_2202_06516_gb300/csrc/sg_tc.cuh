@@ -14,7 +14,9 @@
 // which frees the slice for the next load. The epilogue reads the accumulator lanes back with
 // tcgen05.ld (warp w owns rows 32 w .. 32 w + 31), adds the bias, applies the leaky ReLU and
 // stores FP32 or BF16. k_gemm_wwin computes the weight gradient of the 32/64-channel levels from
-// one staged input window per slice.
+// one staged input window per slice, and k_gemm_fwin the forward convolution or data gradient of
+// a layer whose window operand has 32 channels from one staged window per 128-pixel tile (the
+// nine taps as operands shifted by whole rows inside the window).
 //
 // Every wait on an mbarrier is polled by one thread with an iteration limit; on expiry the
 // CTA sets *err, waits (bounded) for the MMAs it issued, frees its tensor memory and returns.
