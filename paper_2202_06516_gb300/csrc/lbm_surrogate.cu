@@ -663,7 +663,9 @@ cudaError_t launch_wwin(cudaStream_t st, const GemmArgs& a, int splits, const CU
 // Launch of k_gemm_fwin: one CTA per tile of 128 pixels x BN columns.
 template <int BN, int CB, bool GD>
 cudaError_t launch_fwin(cudaStream_t st, const GemmArgs& a, const CUtensorMap* maps) {
-    constexpr int SMEM = 1024 + CB * 3 * 136 * 64 + 9 * CB * BN * 64 + 32;
+    // 512-byte alignment slack (the 64-byte swizzle repeats every 512 bytes): 45,088 bytes at
+    // BN = 32, five CTAs per SM
+    constexpr int SMEM = 512 + CB * 3 * 136 * 64 + 9 * CB * BN * 64 + 32;
     auto* kern = lbm::sgtc::k_gemm_fwin<BN, CB, GD>;
     static std::atomic<unsigned long long> configured{0};
     int dev = 0;

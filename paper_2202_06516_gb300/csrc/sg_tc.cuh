@@ -953,7 +953,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t TX = (uint32_t)(A_B + B_B);
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
-    uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    // 512-byte-aligned base: the 64-byte swizzle repeats every 512 bytes of shared memory
+    uint8_t* base = smem_raw + ((512u - (raw & 511u)) & 511u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + A_B + B_B);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
     __shared__ int s_ok;
