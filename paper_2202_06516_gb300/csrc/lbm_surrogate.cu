@@ -950,7 +950,7 @@ void make_tensor_maps(lbm_surrogate* s) {
             c.f_ks = fk;
         // window-fed forward and data gradient: 128-pixel row segments, a window operand of 32
         // channels (the input for the forward, dY for the data gradient) and 32 or 64 output
-        // columns (at most 64 KB of shared memory, three or four CTAs per SM). With 64 window
+        // columns (at most 64 KB of shared memory, five or three CTAs per SM). With 64 window
         // channels (90 KB and two CTAs per SM, each loading, multiplying and storing in turn,
         // or one CTA per SM at N = 64) the pipelined TMA path is faster, so those keep it.
         if (W % 128 == 0 && (long long)s->maxB * H * W / 128 <= 65535) {
