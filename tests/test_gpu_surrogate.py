@@ -178,12 +178,15 @@ def test_tma_fed_levels_at_full_resolution(env):
     _per_layer_check(env, 32, 256, "positive", B=1)
 
 
-def test_tma_fed_levels_on_a_rectangular_lattice(env):
-    """128 rows x 256 columns, base 32, one image: tiles of whole rows (or half rows) of a
-    non-square image through every tensor-map path (forward, data and weight gradients, the
-    upsampling layers' even/odd orders, the staged-window weight gradient); the per-layer check
-    of test_gradients_match_bf16_oracle_per_layer."""
-    _per_layer_check(env, 32, 128, "positive", B=1, Wd=256)
+@pytest.mark.parametrize("B", [1, 2])
+def test_tma_fed_levels_on_a_rectangular_lattice(env, B):
+    """128 rows x 256 columns, base 32, one or two images: tiles of whole rows (or half rows) of
+    a non-square image through every tensor-map path (forward, data and weight gradients, the
+    upsampling layers' even/odd orders, the staged windows of the weight gradient and of the
+    32-channel forward and data gradient); with two images the fourth (image) coordinate of
+    the boxes and the zero fill at each image's top and bottom rows; the per-layer check of
+    test_gradients_match_bf16_oracle_per_layer."""
+    _per_layer_check(env, 32, 128, "positive", B=B, Wd=256)
 
 
 def _per_layer_check(env, base, H, regime, B=2, Wd=None):
