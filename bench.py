@@ -293,9 +293,9 @@ def run_cuda(args, rank, world, dist):
     return line
 
 
-def cpu_baseline(steps: int = 400):
-    """The oracle as it stands on the host cores: the same 2048 x 1024 workload, `steps` time
-    steps (a bounded sample of the 50k-step run)."""
+def cpu_baseline(steps: int = 400, warmup: int = 2):
+    """The oracle as it stands on the host cores: the same 2048 x 1024 workload, `warmup`
+    untimed steps, then `steps` timed time steps (a bounded sample of the 50k-step run)."""
     import oracle as O
     from paper_2202_06516_gb300 import workloads as W
     w = W.plain_large(0)
@@ -309,7 +309,8 @@ def cpu_baseline(steps: int = 400):
                    mu_circle=neutral + w.mu_rel_circle, mu_bottom=neutral, mu_top=neutral,
                    drop_x=w.drop[0], drop_y=w.drop[1], drop_r=w.drop[2], drop_W=w.drop[3])
     s = O.Sim(cfg)
-    s.step(2)
+    if warmup > 0:
+        s.step(warmup)
     t = time.perf_counter()
     s.step(steps)
     dt = time.perf_counter() - t
@@ -324,7 +325,7 @@ def run_reference(args):
     w = W.plain_large(0)
     steps = max(1, min(args.steps, 200))
     warm = max(0, min(args.warmup, 3))
-    cb = cpu_baseline(steps)
+    cb = cpu_baseline(steps, warm)
     return {"metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": cb["seconds"] * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
