@@ -1,7 +1,8 @@
 """The bench's reference arm (the FP64 oracle on the host cores) keeps the JSON-line contract:
 one line from rank 0 with the metric, the timing fields, the warm-up it actually ran, a
 `cpu_baseline` that describes the run and an `e2e` object without host-device copies; any other
-rank prints nothing and exits 0. Runs on the CPU (the reference arm launches no GPU work)."""
+rank prints nothing and exits 0. Also the clocks record that every GPU line carries, from
+nvidia-smi rows given as text. Runs on the CPU (the reference arm launches no GPU work)."""
 import json
 import os
 import subprocess
@@ -46,3 +47,28 @@ def test_reference_other_ranks_are_silent(oracle_mod):
     r = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--steps", "2", "--warmup", "3")
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_clock_summary_from_nvidia_smi_rows():
+    """The clocks record of a bench line from nvidia-smi's CSV rows (sm, max sm, then the four
+    throttle reasons): the median SM clock, the maximum, and each reason seen Active at least
+    once; malformed rows are skipped, and no rows at all read as unsampled."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.out = "\n".join([
+        "2070, 2070, Not Active, Not Active, Not Active, Not Active",
+        "1980, 2070, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "[N/A], 2070, Not Active, Not Active, Not Active, Not Active",
+    ])
+    s = c.summary()
+    assert s["samples"] == 4 and s["sm_max_mhz"] == 2070.0
+    assert s["sm_mhz"] == 2070.0            # median of 2070, 1980, 2070 (N/A skipped)
+    assert s["reasons"] == ["sw_power_cap"]
+    c.out = "1500, 2070, Active, Not Active, Active, Not Active"
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.out = ""
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                           "samples": 0}
